@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of the micropolar elastoplastic FFT solver on one GB300.
+
+Workload: the 256^3 periodic Voronoi cell with 200 seeded grains (per-grain
+moduli and yield stresses +-20 % around the matrix values), uniaxial E11 to
+1 % in 20 load increments, tolerance 1e-6 (local error measure), FP32 fields
+and FFTs with the radial return's scalar solve, the error norms and the
+homogenized averages in FP64.  One bench "step" is one load increment of that
+path: predictor, fixed-point iterations to convergence, commit (every step of
+the hot path).  The metric is voxel-iterations per second:
+sum over timed increments of (voxels x fixed-point iterations) / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica on its own GPU ("replicas
+only": one cell does not shard), the timed region is bracketed by a barrier and
+cudaDeviceSynchronize, and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "voxel-iters/s at 256^3 and batched RVE solves/s vs plain FP64; serving p50/p99"
+UNIT = "voxel-iters/s"
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_CLASSES = ("fft_y_fwd", "green_z", "fft_y_inv", "pass_a", "reduce", "start", "commit")
+
+
+# ---------------------------------------------------------------- algorithmic bytes
+
+def algorithmic_bytes(n, precision=1):
+    """Bytes one launch of each iteration kernel must move (inputs + outputs),
+    for an N1 x N2 x N3 cell: the half spectrum holds 18 complex values per
+    (N1 / 2) N2 N3 points; pass A also reads the history (h_t, h_m, p, q, phase)
+    and reads + writes the previous iterate (e, gamma, f_t, f_m)."""
+    r = 8 if precision == 0 else 4
+    nvox = n[0] * n[1] * n[2]
+    nspec = max(n[0] // 2, 1) * n[1] * n[2]
+    spec = nspec * 18 * 2 * r
+    return {
+        "fft_y_fwd": 2 * spec,
+        "green_z": 2 * spec,
+        "fft_y_inv": 2 * spec,
+        "pass_a": 2 * spec + nvox * (2 * 20 * r + 18 * r + 16 + 2),
+    }
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2409_10774_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if data.get("source_hash") != _source_hash():
+        return None
+    return data.get("bytes_per_launch", {}).get(kernel)
+
+
+def _peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return out
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = set()
+        for _, _, flags in rows:
+            for nm, f in zip(names, flags):
+                if f.lower().startswith("active"):
+                    reasons.add(nm)
+        out.update(sm_mhz=statistics.median(r[0] for r in rows), sm_max_mhz=max(r[1] for r in rows),
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+# ---------------------------------------------------------------- oracle legs (CPU)
+
+ORACLE_N = 64  # the 64^3 regeneration of the 256^3 Voronoi cell (same seeds / 4)
+
+
+def oracle_sample(budget_s=15.0, max_iters=None, warmup_iters=1):
+    """Times the FP64 oracle's fixed-point iterations of the first load
+    increment of the 64^3 regeneration of the Voronoi workload; returns
+    (voxel-iters/s, iterations timed, seconds)."""
+    import numpy as np  # noqa: F401
+    import workloads as W
+    from oracle import solver
+
+    prob = W.workload_voronoi(n=ORACLE_N)
+    nvox = ORACLE_N ** 3
+    stamps = []
+
+    class _Stop(Exception):
+        pass
+
+    def t_start():
+        return stamps[warmup_iters - 1] if warmup_iters >= 1 else start
+
+    def cb(step, it, err):
+        stamps.append(time.perf_counter())
+        timed = len(stamps) - warmup_iters
+        if timed <= 0:
+            return
+        if max_iters is not None and timed >= max_iters:
+            raise _Stop()
+        if max_iters is None and stamps[-1] - t_start() > budget_s:
+            raise _Stop()
+
+    start = time.perf_counter()
+    try:
+        solver.solve(prob, callback=cb)
+    except _Stop:
+        pass
+    iters = len(stamps) - warmup_iters
+    if iters <= 0:
+        raise RuntimeError("oracle sample ended before the timed iterations")
+    secs = stamps[-1] - t_start()
+    return nvox * iters / secs, iters, secs
+
+
+def _oracle_subprocess(args):
+    """Run an oracle leg in a fresh single-threaded process (spawned before any
+    CUDA use in this process)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "r = bench.oracle_sample(**%r); print(json.dumps(r))" % (ROOT, args))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_block():
+    value, iters, secs = _oracle_subprocess({"budget_s": 15.0})
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, {iters} fixed-point iterations ({secs:.1f} s) of the first "
+                      f"load increment of the {ORACLE_N}^3 regeneration of the Voronoi cell "
+                      f"(same seeds scaled by 1/4), after 1 untimed iteration"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    value, iters, secs = _oracle_subprocess({"max_iters": args.steps, "warmup_iters": args.warmup})
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(iters, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step = one FP64 oracle fixed-point iteration of the first "
+                                       f"load increment of the {ORACLE_N}^3 regeneration of the Voronoi "
+                                       f"cell; {args.warmup} untimed, {iters} timed"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+
+def _config(args):
+    return {"workload": f"voronoi{args.cells}-{args.n}^3", "n": args.n, "cells": args.cells,
+            "increments": 20, "load": "E11 to 1%", "tol": 1e-6, "err": "local",
+            "ref_medium": "mean", "fields": "fp32", "scalars": "fp64",
+            "l2": "no flush: the cell's device state (~5.3 GB) exceeds L2",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    cpu_block = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_block = cpu_baseline_block()  # before the first CUDA call of this process
+
+    import paper_2409_10774_gb300 as M
+    import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    prob = W.workload_voronoi(n=args.n, n_cells=args.cells)
+    n = prob["n"]
+    nvox = n[0] * n[1] * n[2]
+    n_steps = len(prob["time"]) - 1
+    ctx = M.Context(local_rank)
+
+    # ---------------- device-resident timed run (value)
+    rve = M.Rve(ctx, prob, precision=1, stream=stream)
+
+    def advance(k):
+        done = 0
+        while done < k:
+            if rve.steps_done >= n_steps:
+                rve.reset(stream=stream)  # wrap around the 20-increment path
+            st = rve.run(1, stream=stream)
+            if st != 0:
+                raise RuntimeError(f"increment failed: {M.binding.last_error(ctx.ptr)}")
+            done += 1
+
+    advance(args.warmup)
+    torch.cuda.synchronize(dev)
+    rve.profile(True)
+    rve.profile_read(reset=True)
+    it0 = rve.iterations
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    advance(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    iters = rve.iterations - it0
+    prof = rve.profile_read(reset=True)
+    rve.profile(False)
+    rve.close()
+
+    local = torch.tensor([ms, float(iters) * nvox], dtype=torch.float64)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot = torch.tensor([float(iters) * nvox], dtype=torch.float64)
+        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.SUM)
+        ms_max, vox_it = float(t[0]), float(tot[0])
+    else:
+        ms_max, vox_it = float(local[0]), float(local[1])
+    value = vox_it / (ms_max / 1e3)
+
+    # ---------------- roofline of the dominant kernel (events on the run's stream)
+    abytes = algorithmic_bytes(n, precision=1)
+    timed = {k: prof[k] for k in abytes if prof[k][1] > 0}
+    dom = max(timed, key=lambda k: timed[k][0])
+    dom_ms = timed[dom][0] / timed[dom][1]
+    achieved = abytes[dom] / (dom_ms / 1e3) / 1e9
+    peak, peak_src = _peaks()
+    kernels = {k: {"ms_per_launch": prof[k][0] / prof[k][1] if prof[k][1] else None,
+                   "launches": prof[k][1],
+                   "gbs": (abytes[k] / (prof[k][0] / prof[k][1] / 1e3) / 1e9)
+                   if (k in abytes and prof[k][1] and prof[k][0] > 0) else None}
+               for k in KERNEL_CLASSES}
+    launches = int(sum(v[1] for v in prof.values()))
+
+    # ---------------- plain FP64 GPU solver on the same workload (speed-up base)
+    fp64 = None
+    if not args.no_fp64:
+        r64 = M.Rve(ctx, prob, precision=0, stream=stream)
+        r64.run(args.warmup, stream=stream)
+        torch.cuda.synchronize(dev)
+        i0 = r64.iterations
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        k64 = max(1, min(args.steps, args.fp64_steps))
+        e0.record(stream)
+        r64.run(k64, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        v64 = (r64.iterations - i0) * nvox / (e0.elapsed_time(e1) / 1e3)
+        r64.close()
+        fp64 = {"value": v64, "unit": UNIT, "increments": k64,
+                "note": f"plain FP64 GPU solver, increments {args.warmup + 1}..{args.warmup + k64}"}
+
+    # ---------------- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.empty(nvox, dtype=torch.int16, pin_memory=True)
+        pin_np = pinned.numpy().view(np.uint16)
+        pin_np[:] = prob["phase"].reshape(-1)
+        prob_pinned = dict(prob, phase=pin_np)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = M.Rve(ctx, prob_pinned, precision=1, stream=stream)     # H2D: phase map, tables, path
+        k_e2e = min(args.steps, n_steps)
+        r.run(k_e2e, stream=stream)
+        res = r.results(fields=False, stream=stream)                  # D2H: homogenized results
+        iters_e2e = r.iterations
+        r.close()
+        torch.cuda.synchronize(dev)
+        secs = time.perf_counter() - t0
+        h2d = nvox * 2 + len(prob["phases"]) * 104 + (n_steps + 1) * 19 * 8
+        d2h = k_e2e * (40 * 8) + iters_e2e * 5 * 8
+        e2e = {"value": iters_e2e * nvox / secs, "unit": UNIT, "h2d_bytes_per_step": h2d // k_e2e,
+               "d2h_bytes_per_step": d2h // k_e2e,
+               "note": f"Rve create (uploads) + {k_e2e} increments from the zero state + results + destroy; "
+                       f"T11 after increment {k_e2e}: {res['T'][-1][0, 0]:.6e}"}
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config(args),
+        "iterations_timed": iters,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": _traffic(dom), "algorithmic_bytes_per_launch": abytes[dom]},
+        "kernels": kernels,
+        "fp64_gpu": fp64,
+        "speedup_vs_fp64_gpu": (value / world / fp64["value"]) if fp64 else None,
+        "clocks": clocks,
+        "cpu_baseline": cpu_block,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--cells", type=int, default=200)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("gloo")
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,218 @@
+/*
+ * micropolar.h - C ABI of the GB300 micropolar elastoplastic FFT solver.
+ *
+ * The library solves the periodic micropolar elastoplastic cell problem of
+ * Francis, Lebensohn, Pourahmadian, Dingreville (2024) by the FFT-based
+ * basic scheme with time stepping (their Algorithm 2), applying the
+ * closed-form micropolar radial return (their Algorithm 1) at every voxel.
+ * All compute runs in hand-written CUDA kernels for sm_103a; there is no CPU
+ * fallback: every entry point that computes returns MP_E_CUDA / MP_E_NO_DEVICE
+ * when no GPU is usable.
+ *
+ * Conventions shared by every entry point
+ *   - Grid n[0] = N1 (x1, fastest), n[1] = N2 (x2), n[2] = N3 (x3); voxel
+ *     index v = x1 + N1 * (x2 + N2 * x3); voxel size h (cell side N_j h).
+ *     Each N_j must be 1 or an even number <= 512 whose prime factors are 2
+ *     and 3, else MP_E_UNSUPPORTED_SIZE.
+ *   - A second-order tensor is 9 numbers V_kl stored row-major (3k + l),
+ *     k, l = 0..2 standing for the paper's 1..3.  e_kl, gamma_kl, t_kl, m_kl
+ *     follow the paper's index order (eq. strains, eq. elast_constitutive_aniso).
+ *   - Field arrays are voxel-major: value (v, kl) at [9 v + 3 k + l].
+ *   - precision 0 = plain FP64 (fields, FFTs, Green operator, radial return);
+ *     precision 1 = FP32 fields / FFTs / Green operator with the scalar part
+ *     of the radial return (equivalent stresses' square roots, p, q, scale
+ *     factors), the error norm reductions and the homogenized averages in FP64.
+ *   - Status codes only; nothing throws or aborts across this boundary.  The
+ *     message of the last failure is available from mp_last_error().
+ *   - Host pointers are read during the call and not retained.  Output host
+ *     buffers are caller-allocated; a NULL output pointer skips that output.
+ *   - Device memory is obtained through the mp_alloc callbacks given to
+ *     mp_create (e.g. a framework's caching allocator), else cudaMalloc.
+ */
+#ifndef MICROPOLAR_GB300_H
+#define MICROPOLAR_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MP_ABI_VERSION 1
+
+typedef enum mp_status {
+  MP_OK = 0,
+  MP_E_INVALID_ARG = 1,      /* malformed input (NULL, non-positive sizes, t_Y <= 0, ...)   */
+  MP_E_INADMISSIBLE = 2,     /* moduli violate eq. energetic_bounds (gamma - beta >= 0 read) */
+  MP_E_UNSUPPORTED_SIZE = 3, /* a grid size outside {1} U {even 2^a 3^b <= 512}              */
+  MP_E_NOT_CONVERGED = 4,    /* max_iter fixed-point iterations without err <= tol          */
+  MP_E_DIVERGED = 5,         /* err non-finite or above div_limit                          */
+  MP_E_OOM = 6,              /* device allocation failed                                    */
+  MP_E_CUDA = 7,             /* a CUDA runtime call failed                                  */
+  MP_E_TIMEOUT = 8,          /* a bounded wait expired                                      */
+  MP_E_CANCELLED = 9,        /* request cancelled                                           */
+  MP_E_NO_DEVICE = 10        /* no usable CUDA device                                       */
+} mp_status;
+
+/* Per-phase isotropic micropolar moduli (eq. stiffnesses_iso) and the
+ * yield / hardening parameters of eq. yield_function_f ... radius_2
+ * (Tables 1-5 list them in this order).  elastic != 0 marks a phase with
+ * infinite yield stresses (it never yields; tY..mH ignored). */
+typedef struct mp_phase {
+  double lambda, mu, kappa, alpha, beta, gamma;
+  double tY, tH, mY, mH, a1, b1;
+  int32_t elastic;
+  int32_t reserved;
+} mp_phase;
+
+/* Error measure of eq. err: 0 = local (eq. err_local), 1 = average (eq. err_average). */
+#define MP_ERR_LOCAL 0
+#define MP_ERR_AVERAGE 1
+/* Reference medium: 0 = phase-volume average <A>, <B> (Algorithm 2),
+ * 1 = midrange (min + max) / 2 of each modulus over the phases present,
+ * 2 = explicit ref_moduli[6] = (lambda0, mu0, kappa0, alpha0, beta0, gamma0). */
+#define MP_REF_MEAN 0
+#define MP_REF_MIDRANGE 1
+#define MP_REF_EXPLICIT 2
+
+/* The cell problem (Algorithm 2 inputs). */
+typedef struct mp_problem {
+  int32_t n[3];
+  double h;
+  const uint16_t* phase;        /* host, N1*N2*N3 phase ids < n_phases                    */
+  int32_t n_phases;
+  const mp_phase* phases;       /* host, n_phases                                         */
+  int32_t n_steps;              /* load increments; the zero initial state is index 0    */
+  const double* time;           /* host, n_steps + 1, strictly increasing                 */
+  const double* E;              /* host, (n_steps + 1) * 9 prescribed <e> per time        */
+  const double* G;              /* host, (n_steps + 1) * 9 prescribed <gamma> per time    */
+  double tol;                   /* equilibrium tolerance epsilon (> 0)                    */
+  int32_t err_kind;             /* MP_ERR_*                                               */
+  int32_t max_iter;             /* per step; <= 0 means 10000                             */
+  int32_t ref_kind;             /* MP_REF_*                                               */
+  const double* ref_moduli;     /* 6 values when ref_kind == MP_REF_EXPLICIT             */
+  int32_t precision;            /* 0 = FP64, 1 = FP32 fields with FP64 scalars            */
+  const int32_t* lockstep_iters;/* optional host n_steps: run exactly these iterations    */
+  double div_limit;             /* err above this => MP_E_DIVERGED; <= 0 means 1e6        */
+} mp_problem;
+
+/* Results (caller-allocated host buffers; any pointer may be NULL).
+ * Per step s = 1..n_steps (stored at index s - 1): homogenized stress
+ * T = <t>, couple stress M = <m>, <e>, <gamma> (9 each), P = <p>, Q = <q>,
+ * T_eq = <t_eq(t)>, M_eq = <m_eq(m)>, the last error and the number of
+ * fixed-point iterations.  Final-step fields: e, g (gamma), t, m as
+ * N1*N2*N3*9 and p, q as N1*N2*N3, all FP64. */
+typedef struct mp_result {
+  double *T, *M, *Eavg, *Gavg;
+  double *P, *Q, *Teq, *Meq, *err;
+  int32_t* iters;
+  double *e, *g, *t, *m, *p, *q;
+  int32_t steps_done;           /* out: steps committed                                   */
+  int32_t failed_step;          /* out: 1-based step that failed, 0 if none               */
+  double ref_moduli_used[6];    /* out: reference medium actually used                    */
+} mp_result;
+
+/* Device-memory callbacks (both may be NULL for cudaMalloc / cudaFree). */
+typedef struct mp_alloc {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, size_t bytes, void* user);
+  void* user;
+} mp_alloc;
+
+typedef struct mp_ctx mp_ctx;
+typedef struct mp_rve mp_rve;
+
+/* Library / context ---------------------------------------------------- */
+
+int32_t mp_abi_version(void);
+
+/* Create a context bound to CUDA device `device`.  `alloc` may be NULL.
+ * Returns MP_E_NO_DEVICE when the device cannot be used. */
+mp_status mp_create(mp_ctx** ctx, int32_t device, const mp_alloc* alloc);
+void mp_destroy(mp_ctx* ctx);
+/* Message describing the last failure on `ctx` (or a global one for NULL). */
+const char* mp_last_error(const mp_ctx* ctx);
+
+/* Validation only (no GPU work): checks sizes, eq. energetic_bounds with the
+ * gamma - beta >= 0 reading, yield parameters, load path and reference
+ * medium.  Usable without a GPU. */
+mp_status mp_validate(const mp_problem* problem, char* message, size_t message_len);
+
+/* Whole solve (Algorithm 2) ---------------------------------------------
+ * Copies the problem to the device, runs every load increment (predictor,
+ * fixed-point iterations to err <= tol, commit) and copies the requested
+ * results back to the host.  `stream` is a cudaStream_t (NULL = default). */
+mp_status mp_solve(mp_ctx* ctx, const mp_problem* problem, mp_result* result, void* stream);
+
+/* Device-resident solve in stages (the same computation as mp_solve):
+ *   mp_rve_create   validate, allocate the cell's device state, upload
+ *                   phase map, phase table and load path;
+ *   mp_rve_run      advance up to `n_steps` load increments on the device
+ *                   (returns after they completed; the error of each
+ *                   fixed-point iteration is read back to decide the loop);
+ *   mp_rve_results  copy per-step homogenized results (and the fields of the
+ *                   last committed step, if requested) to host buffers;
+ *   mp_rve_destroy  release the device state.
+ * mp_rve_run returns MP_E_NOT_CONVERGED / MP_E_DIVERGED when a step fails;
+ * the state then stays at the failed step. */
+mp_status mp_rve_create(mp_ctx* ctx, const mp_problem* problem, mp_rve** rve, void* stream);
+mp_status mp_rve_run(mp_rve* rve, int32_t n_steps, void* stream);
+mp_status mp_rve_results(mp_rve* rve, mp_result* result, void* stream);
+/* Reset to the zero initial state (time index 0) without reallocating. */
+mp_status mp_rve_reset(mp_rve* rve, void* stream);
+int32_t mp_rve_steps_done(const mp_rve* rve);
+/* Total fixed-point iterations run so far (sum over committed and current steps). */
+int64_t mp_rve_iterations(const mp_rve* rve);
+void mp_rve_destroy(mp_rve* rve);
+
+/* Kernel classes of the per-increment work, for launch counts and timings. */
+#define MP_KC_FFT_Y_FWD 0 /* y-direction forward transform pass                        */
+#define MP_KC_GREEN_Z 1   /* z forward + Green operator + z inverse pass                */
+#define MP_KC_FFT_Y_INV 2 /* y-direction inverse transform pass                         */
+#define MP_KC_PASS_A 3    /* x inverse, Algorithm 1, error partials, polarization, x fwd */
+#define MP_KC_REDUCE 4    /* iteration error reduction                                   */
+#define MP_KC_START 5     /* increment start: initial state, predictor pass              */
+#define MP_KC_COMMIT 6    /* commit of a converged increment and homogenized averages    */
+#define MP_KC_COUNT 7
+
+/* Enable / disable per-kernel CUDA-event timing of mp_rve_run's fixed-point
+ * loop (events recorded on the run's stream around every launch of classes
+ * 0-4).  Launch counts are kept for every class regardless. */
+mp_status mp_rve_profile(mp_rve* rve, int32_t enable);
+/* Accumulated milliseconds (classes 0-4, while enabled) and launch counts
+ * per class, MP_KC_COUNT entries each (either pointer may be NULL);
+ * reset != 0 zeroes both afterwards. */
+mp_status mp_rve_profile_read(const mp_rve* rve, double* ms, int64_t* launches, int32_t reset);
+
+/* Hot-path components on device buffers -----------------------------------
+ * Real type of tensor buffers: double for precision 0, float for 1.
+ *
+ * mp_radial_return: Algorithm 1 at `count` material points.  Inputs e, g
+ * (gamma), e_n, g_n, t_n, m_n are count*9 tensors, p_n, q_n count doubles,
+ * phase count uint16 ids into `phases` (host table).  Outputs t, m
+ * (count*9) and p, q (count doubles).  All pointers are device pointers and
+ * must not alias outputs with inputs. */
+mp_status mp_radial_return(mp_ctx* ctx, int32_t precision, int64_t count, const uint16_t* phase,
+                           int32_t n_phases, const mp_phase* phases, const void* e, const void* g,
+                           const void* e_n, const void* g_n, const void* t_n, const void* m_n,
+                           const double* p_n, const double* q_n, void* t, void* m, double* p,
+                           double* q, void* stream);
+
+/* mp_green_apply: one Lippmann-Schwinger update without the mean, i.e. the
+ * Fourier transform of the polarizations (tau, mu), the reference medium's
+ * Green operator (eq. micropolar_LippmannSchwinger_iteration) and the
+ * inverse transform: outputs the strain and curvature fluctuations e~, g~
+ * (zero mean; zero at the Nyquist frequencies).  tau, mu, e_out, g_out are
+ * N1*N2*N3*9 device tensors of the precision's real type; ref_moduli[6] on
+ * the host.  Uses a device work buffer of 18 complex values per half-
+ * spectrum point, obtained from the context's allocator. */
+mp_status mp_green_apply(mp_ctx* ctx, int32_t precision, const int32_t n[3], double h,
+                         const double ref_moduli[6], const void* tau, const void* mu, void* e_out,
+                         void* g_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MICROPOLAR_GB300_H */

@@ -1,0 +1,422 @@
+"""ctypes binding of the C ABI declared in include/micropolar.h.
+
+Argument marshalling only: every step of the solver runs in the CUDA kernels
+of ``libmicropolar_gb300.so``.  Functions keep the C names (``mp_solve``,
+``mp_rve_create``, ...) and take / return numpy arrays (host data) or torch
+CUDA tensors (device data).  PyTorch supplies device memory (through the
+library's allocator callbacks) and streams.  There is no CPU fallback: if the
+library cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+LIB_PATH = _build.LIB_PATH
+
+# status codes (mp_status)
+MP_OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "inadmissible", 3: "unsupported_size",
+                4: "not_converged", 5: "diverged", 6: "oom", 7: "cuda", 8: "timeout",
+                9: "cancelled", 10: "no_device"}
+ERR_KIND = {"local": 0, "average": 1}
+REF_KIND = {"mean": 0, "midrange": 1, "explicit": 2}
+
+EXPORTED = ("mp_abi_version", "mp_create", "mp_destroy", "mp_last_error", "mp_validate",
+            "mp_solve", "mp_rve_create", "mp_rve_run", "mp_rve_results", "mp_rve_reset",
+            "mp_rve_steps_done", "mp_rve_iterations", "mp_rve_destroy", "mp_rve_profile",
+            "mp_rve_profile_read", "mp_radial_return", "mp_green_apply")
+KERNEL_CLASSES = ("fft_y_fwd", "green_z", "fft_y_inv", "pass_a", "reduce", "start", "commit")
+
+
+class MicropolarError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class mp_phase(C.Structure):
+    _fields_ = [(f, C.c_double) for f in ("lambda_", "mu", "kappa", "alpha", "beta", "gamma",
+                                          "tY", "tH", "mY", "mH", "a1", "b1")] + \
+               [("elastic", C.c_int32), ("reserved", C.c_int32)]
+
+
+class mp_problem(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("h", C.c_double), ("phase", C.POINTER(C.c_uint16)),
+                ("n_phases", C.c_int32), ("phases", C.POINTER(mp_phase)), ("n_steps", C.c_int32),
+                ("time", C.POINTER(C.c_double)), ("E", C.POINTER(C.c_double)),
+                ("G", C.POINTER(C.c_double)), ("tol", C.c_double), ("err_kind", C.c_int32),
+                ("max_iter", C.c_int32), ("ref_kind", C.c_int32),
+                ("ref_moduli", C.POINTER(C.c_double)), ("precision", C.c_int32),
+                ("lockstep_iters", C.POINTER(C.c_int32)), ("div_limit", C.c_double)]
+
+
+_DP = C.POINTER(C.c_double)
+
+
+class mp_result(C.Structure):
+    _fields_ = [("T", _DP), ("M", _DP), ("Eavg", _DP), ("Gavg", _DP), ("P", _DP), ("Q", _DP),
+                ("Teq", _DP), ("Meq", _DP), ("err", _DP), ("iters", C.POINTER(C.c_int32)),
+                ("e", _DP), ("g", _DP), ("t", _DP), ("m", _DP), ("p", _DP), ("q", _DP),
+                ("steps_done", C.c_int32), ("failed_step", C.c_int32),
+                ("ref_moduli_used", C.c_double * 6)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class mp_alloc(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "(nvcc, sm_103a); there is no CPU fallback")
+    lib = C.CDLL(LIB_PATH)
+    V, P = C.c_void_p, C.POINTER
+    sig = {
+        "mp_abi_version": (C.c_int32, []),
+        "mp_create": (C.c_int, [P(V), C.c_int32, P(mp_alloc)]),
+        "mp_destroy": (None, [V]),
+        "mp_last_error": (C.c_char_p, [V]),
+        "mp_validate": (C.c_int, [P(mp_problem), C.c_char_p, C.c_size_t]),
+        "mp_solve": (C.c_int, [V, P(mp_problem), P(mp_result), V]),
+        "mp_rve_create": (C.c_int, [V, P(mp_problem), P(V), V]),
+        "mp_rve_run": (C.c_int, [V, C.c_int32, V]),
+        "mp_rve_results": (C.c_int, [V, P(mp_result), V]),
+        "mp_rve_reset": (C.c_int, [V, V]),
+        "mp_rve_steps_done": (C.c_int32, [V]),
+        "mp_rve_iterations": (C.c_int64, [V]),
+        "mp_rve_destroy": (None, [V]),
+        "mp_rve_profile": (C.c_int, [V, C.c_int32]),
+        "mp_rve_profile_read": (C.c_int, [V, P(C.c_double), P(C.c_int64), C.c_int32]),
+        "mp_radial_return": (C.c_int, [V, C.c_int32, C.c_int64, V, C.c_int32, P(mp_phase)] + [V] * 6
+                             + [V, V, V, V, V, V, V]),
+        "mp_green_apply": (C.c_int, [V, C.c_int32, P(C.c_int32), C.c_double, P(C.c_double), V, V, V, V, V]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+def last_error(ctx=None) -> str:
+    msg = LIB.mp_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+# ---------------------------------------------------------------- marshalling helpers
+
+def phase_table(phases) -> "C.Array":
+    """numpy structured phase table (workloads.PHASE_FIELDS) -> mp_phase[]."""
+    arr = (mp_phase * len(phases))()
+    for i, r in enumerate(phases):
+        arr[i] = mp_phase(float(r["lambda"]), float(r["mu"]), float(r["kappa"]), float(r["alpha"]),
+                          float(r["beta"]), float(r["gamma"]), float(r["tY"]), float(r["tH"]),
+                          float(r["mY"]), float(r["mH"]), float(r["a1"]), float(r["b1"]),
+                          int(r["elastic"]), 0)
+    return arr
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_DP)
+
+
+class _Problem:
+    """Keeps the host arrays of an mp_problem alive while it is in use."""
+
+    def __init__(self, problem, precision=None, lockstep_iters=None, div_limit=0.0):
+        p = problem
+        n = tuple(int(v) for v in p["n"])
+        self.phase = np.ascontiguousarray(p["phase"], dtype=np.uint16).reshape(-1)
+        if self.phase.size != n[0] * n[1] * n[2]:
+            raise ValueError("phase map size does not match n")
+        self.phases = phase_table(p["phases"])
+        self.time = np.ascontiguousarray(p["time"], dtype=np.float64)
+        n_steps = self.time.size - 1
+        self.E = np.ascontiguousarray(np.asarray(p["E"], dtype=np.float64).reshape(n_steps + 1, 9))
+        self.G = np.ascontiguousarray(np.asarray(p["G"], dtype=np.float64).reshape(n_steps + 1, 9))
+        self.ref = None
+        if p.get("ref_moduli") is not None:
+            self.ref = np.ascontiguousarray(p["ref_moduli"], dtype=np.float64)
+        self.lock = None
+        if lockstep_iters is not None:
+            self.lock = np.ascontiguousarray(lockstep_iters, dtype=np.int32)
+        prec = p.get("precision", 1) if precision is None else precision
+        self.st = mp_problem()
+        self.st.n = (C.c_int32 * 3)(*n)
+        self.st.h = float(p["h"])
+        self.st.phase = self.phase.ctypes.data_as(C.POINTER(C.c_uint16))
+        self.st.n_phases = len(p["phases"])
+        self.st.phases = self.phases
+        self.st.n_steps = n_steps
+        self.st.time = _dptr(self.time)
+        self.st.E = _dptr(self.E)
+        self.st.G = _dptr(self.G)
+        self.st.tol = float(p["tol"])
+        self.st.err_kind = ERR_KIND[p.get("err_kind", "local")]
+        self.st.max_iter = int(p.get("max_iter", 10000))
+        self.st.ref_kind = REF_KIND[p.get("ref_kind", "mean")]
+        self.st.ref_moduli = _dptr(self.ref) if self.ref is not None else None
+        self.st.precision = int(prec)
+        self.st.lockstep_iters = self.lock.ctypes.data_as(C.POINTER(C.c_int32)) if self.lock is not None else None
+        self.st.div_limit = float(div_limit)
+        self.n = n
+        self.n_steps = n_steps
+
+
+class _Result:
+    def __init__(self, n, n_steps, fields):
+        ns = max(n_steps, 1)
+        nv = n[0] * n[1] * n[2]
+        self.arrs = {k: np.zeros((ns, 9)) for k in ("T", "M", "Eavg", "Gavg")}
+        self.arrs.update({k: np.zeros(ns) for k in ("P", "Q", "Teq", "Meq", "err")})
+        self.iters = np.zeros(ns, dtype=np.int32)
+        self.fields = {}
+        if fields:
+            self.fields = {k: np.zeros((nv, 9)) for k in ("e", "g", "t", "m")}
+            self.fields.update({k: np.zeros(nv) for k in ("p", "q")})
+        self.st = mp_result()
+        for k, a in self.arrs.items():
+            setattr(self.st, k, _dptr(a))
+        self.st.iters = self.iters.ctypes.data_as(C.POINTER(C.c_int32))
+        for k, a in self.fields.items():
+            setattr(self.st, k, _dptr(a))
+        self.n = n
+
+    def to_dict(self, status):
+        ns = self.st.steps_done
+        out = {k: v[:ns].copy() for k, v in self.arrs.items()}
+        for k in ("T", "M", "Eavg", "Gavg"):
+            out[k] = out[k].reshape(ns, 3, 3)
+        out["iters"] = self.iters[:ns].astype(np.int64)
+        out["steps_done"] = ns
+        out["failed_step"] = self.st.failed_step
+        out["ref_moduli"] = tuple(self.st.ref_moduli_used)
+        out["status"] = STATUS_NAMES.get(status, str(status))
+        n = self.n
+        if self.fields and ns > 0:
+            fin = {}
+            for k in ("e", "g", "t", "m"):
+                fin[k] = self.fields[k].reshape(n[2], n[1], n[0], 3, 3)
+            for k in ("p", "q"):
+                fin[k] = self.fields[k].reshape(n[2], n[1], n[0])
+            out["final"] = fin
+        return out
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+# ---------------------------------------------------------------- context
+
+class Context:
+    """mp_create / mp_destroy with PyTorch's caching allocator as device memory."""
+
+    def __init__(self, device=0, use_torch_allocator=True):
+        self.device = int(device)
+        self._alloc = None
+        ptr = C.c_void_p()
+        alloc_p = None
+        if use_torch_allocator:
+            import torch
+
+            dev = self.device
+
+            def _a(nbytes, user):
+                try:
+                    return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev))
+                except RuntimeError:
+                    return 0
+
+            def _f(p, nbytes, user):
+                torch.cuda.caching_allocator_delete(int(p))
+
+            self._afn = ALLOC_FN(_a)
+            self._ffn = FREE_FN(_f)
+            self._alloc = mp_alloc(self._afn, self._ffn, None)
+            alloc_p = C.byref(self._alloc)
+        st = LIB.mp_create(C.byref(ptr), self.device, alloc_p)
+        if st != MP_OK:
+            raise MicropolarError(st, last_error(None))
+        self.ptr = ptr
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            LIB.mp_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def error(self):
+        return last_error(self.ptr)
+
+
+# ---------------------------------------------------------------- entry points
+
+def mp_abi_version():
+    return LIB.mp_abi_version()
+
+
+def mp_validate(problem, precision=None):
+    pr = _Problem(problem, precision)
+    buf = C.create_string_buffer(512)
+    st = LIB.mp_validate(C.byref(pr.st), buf, 512)
+    return st, buf.value.decode()
+
+
+_HARD_ERRORS = (1, 2, 3, 6, 7, 8, 9, 10)
+
+
+def mp_solve(ctx, problem, precision=None, fields=False, lockstep_iters=None, div_limit=0.0,
+             stream=None):
+    """Whole solve; returns a dict shaped like the oracle's result (per-step
+    arrays, 'final' fields when requested, 'status')."""
+    pr = _Problem(problem, precision, lockstep_iters, div_limit)
+    rs = _Result(pr.n, pr.n_steps, fields)
+    st = LIB.mp_solve(ctx.ptr, C.byref(pr.st), C.byref(rs.st), _stream_handle(stream))
+    if st in _HARD_ERRORS:
+        raise MicropolarError(st, ctx.error())
+    return rs.to_dict(st)
+
+
+class Rve:
+    """Device-resident cell: mp_rve_create / run / results / reset / destroy."""
+
+    def __init__(self, ctx, problem, precision=None, lockstep_iters=None, div_limit=0.0, stream=None):
+        self.ctx = ctx
+        self._pr = _Problem(problem, precision, lockstep_iters, div_limit)
+        self.ptr = C.c_void_p()
+        st = LIB.mp_rve_create(ctx.ptr, C.byref(self._pr.st), C.byref(self.ptr), _stream_handle(stream))
+        if st != MP_OK:
+            raise MicropolarError(st, ctx.error())
+
+    def run(self, n_steps, stream=None):
+        st = LIB.mp_rve_run(self.ptr, int(n_steps), _stream_handle(stream))
+        if st in _HARD_ERRORS:
+            raise MicropolarError(st, self.ctx.error())
+        return st
+
+    def results(self, fields=False, stream=None):
+        rs = _Result(self._pr.n, self._pr.n_steps, fields)
+        st = LIB.mp_rve_results(self.ptr, C.byref(rs.st), _stream_handle(stream))
+        if st != MP_OK:
+            raise MicropolarError(st, self.ctx.error())
+        return rs.to_dict(MP_OK if rs.st.failed_step == 0 else 5)
+
+    def reset(self, stream=None):
+        LIB.mp_rve_reset(self.ptr, _stream_handle(stream))
+
+    def profile(self, enable=True):
+        st = LIB.mp_rve_profile(self.ptr, 1 if enable else 0)
+        if st != MP_OK:
+            raise MicropolarError(st, self.ctx.error())
+
+    def profile_read(self, reset=False):
+        """{kernel class: (milliseconds, launches)}."""
+        k = len(KERNEL_CLASSES)
+        ms = (C.c_double * k)()
+        ln = (C.c_int64 * k)()
+        LIB.mp_rve_profile_read(self.ptr, ms, ln, 1 if reset else 0)
+        return {name: (ms[i], ln[i]) for i, name in enumerate(KERNEL_CLASSES)}
+
+    @property
+    def steps_done(self):
+        return LIB.mp_rve_steps_done(self.ptr)
+
+    @property
+    def iterations(self):
+        return LIB.mp_rve_iterations(self.ptr)
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            LIB.mp_rve_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mp_rve_create(ctx, problem, precision=None, lockstep_iters=None, div_limit=0.0, stream=None):
+    return Rve(ctx, problem, precision, lockstep_iters, div_limit, stream)
+
+
+def _real(precision):
+    import torch
+    return torch.float64 if precision == 0 else torch.float32
+
+
+def _check_dev(t, dtype, shape_last=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous CUDA tensor of {dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def mp_radial_return(ctx, precision, phase, phases, e, g, e_n, g_n, t_n, m_n, p_n, q_n, stream=None):
+    """Algorithm 1 on device tensors (count, 3, 3) of the precision's real type;
+    phase: uint16-valued int32/int16 CUDA tensor is converted to a uint16 view
+    when given as torch.int16; p_n, q_n float64.  Returns (t, m, p, q)."""
+    import torch
+    R = _real(precision)
+    count = e.shape[0]
+    t = torch.empty_like(e)
+    m = torch.empty_like(g)
+    p = torch.empty(count, dtype=torch.float64, device=e.device)
+    q = torch.empty(count, dtype=torch.float64, device=e.device)
+    ph = phase_table(phases)
+    args = [_check_dev(x, R) for x in (e, g, e_n, g_n, t_n, m_n)]
+    st = LIB.mp_radial_return(ctx.ptr, int(precision), int(count), C.c_void_p(phase.data_ptr()),
+                              len(phases), ph, *args, _check_dev(p_n, torch.float64),
+                              _check_dev(q_n, torch.float64), C.c_void_p(t.data_ptr()),
+                              C.c_void_p(m.data_ptr()), C.c_void_p(p.data_ptr()),
+                              C.c_void_p(q.data_ptr()), _stream_handle(stream))
+    if st != MP_OK:
+        raise MicropolarError(st, ctx.error())
+    return t, m, p, q
+
+
+def mp_green_apply(ctx, precision, n, h, ref_moduli, tau, mu, stream=None):
+    """Fluctuations (e~, gamma~) of the polarization fields tau, mu: device
+    tensors (N3, N2, N1, 3, 3) of the precision's real type."""
+    import torch
+    R = _real(precision)
+    e = torch.empty_like(tau)
+    g = torch.empty_like(mu)
+    nn = (C.c_int32 * 3)(*[int(v) for v in n])
+    ref = (C.c_double * 6)(*[float(v) for v in ref_moduli])
+    st = LIB.mp_green_apply(ctx.ptr, int(precision), nn, float(h), ref, _check_dev(tau, R),
+                            _check_dev(mu, R), C.c_void_p(e.data_ptr()), C.c_void_p(g.data_ptr()),
+                            _stream_handle(stream))
+    if st != MP_OK:
+        raise MicropolarError(st, ctx.error())
+    return e, g

@@ -1,0 +1,871 @@
+// C ABI of the micropolar FFT solver: validation, device state, and the
+// host-side load-step / fixed-point loop of Algorithm 2 around the kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/micropolar.h"
+#include "mp_kernels.cuh"
+
+using namespace mp;
+
+struct mp_ctx {
+  int device = 0;
+  int nsm = 1;
+  mp_alloc alloc{};
+  bool has_alloc = false;
+  std::string last_error;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mp_status set_error(mp_ctx* ctx, mp_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->last_error = buf;
+  g_last_error = buf;
+  return st;
+}
+
+#define MP_CK(ctx, call)                                                                      \
+  do {                                                                                        \
+    cudaError_t _e = (call);                                                                  \
+    if (_e != cudaSuccess)                                                                    \
+      return set_error((ctx), _e == cudaErrorMemoryAllocation ? MP_E_OOM : MP_E_CUDA,          \
+                       "%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__, __LINE__); \
+  } while (0)
+
+// ------------------------------------------------------------------ device memory
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+mp_status dalloc(mp_ctx* ctx, DevBuf& b, size_t bytes) {
+  b.bytes = bytes;
+  b.ptr = nullptr;
+  if (bytes == 0) return MP_OK;
+  if (ctx->has_alloc && ctx->alloc.alloc) {
+    b.ptr = ctx->alloc.alloc(bytes, ctx->alloc.user);
+    if (!b.ptr) return set_error(ctx, MP_E_OOM, "device allocation of %zu bytes failed", bytes);
+    return MP_OK;
+  }
+  cudaError_t e = cudaMalloc(&b.ptr, bytes);
+  if (e != cudaSuccess) {
+    b.ptr = nullptr;
+    return set_error(ctx, MP_E_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  return MP_OK;
+}
+
+void dfree(mp_ctx* ctx, DevBuf& b) {
+  if (!b.ptr) return;
+  if (ctx->has_alloc && ctx->alloc.free) ctx->alloc.free(b.ptr, b.bytes, ctx->alloc.user);
+  else if (!ctx->has_alloc) cudaFree(b.ptr);
+  b.ptr = nullptr;
+  b.bytes = 0;
+}
+
+// ------------------------------------------------------------------ validation
+bool size_ok(int n) {
+  if (n == 1) return true;
+  if (n < 2 || n > 512 || (n % 2) != 0) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+bool finite(double v) { return std::isfinite(v); }
+
+mp_status check_phase(const mp_phase& ph, int idx, std::string& msg) {
+  const double v[12] = {ph.lambda, ph.mu, ph.kappa, ph.alpha, ph.beta, ph.gamma,
+                        ph.tY, ph.tH, ph.mY, ph.mH, ph.a1, ph.b1};
+  for (double x : v)
+    if (!finite(x)) {
+      msg = "phase " + std::to_string(idx) + ": non-finite parameter";
+      return MP_E_INVALID_ARG;
+    }
+  // eq. energetic_bounds, with gamma - beta >= 0 (equality: the skew couple stress vanishes)
+  if (!(3 * ph.lambda + 2 * ph.mu > 0) || !(ph.mu > 0) || !(ph.kappa > 0) ||
+      !(3 * ph.alpha + ph.beta + ph.gamma > 0) || !(ph.gamma + ph.beta > 0) || !(ph.gamma - ph.beta >= 0)) {
+    msg = "phase " + std::to_string(idx) + ": moduli violate the energetic bounds";
+    return MP_E_INADMISSIBLE;
+  }
+  if (!ph.elastic) {
+    if (!(ph.tY > 0) || !(ph.mY > 0) || !(ph.tH >= 0) || !(ph.mH >= 0) || !(ph.a1 > 0) || !(ph.b1 > 0)) {
+      msg = "phase " + std::to_string(idx) + ": need tY, mY, a1, b1 > 0 and tH, mH >= 0";
+      return MP_E_INVALID_ARG;
+    }
+  } else if (!(ph.a1 > 0) || !(ph.b1 > 0)) {
+    msg = "phase " + std::to_string(idx) + ": need a1, b1 > 0";
+    return MP_E_INVALID_ARG;
+  }
+  return MP_OK;
+}
+
+// Reference medium (6 moduli) over the phases present in the map.
+mp_status reference_moduli(const mp_problem* p, const std::vector<long long>& counts, long long nvox,
+                           double ref[6], std::string& msg) {
+  if (p->ref_kind == MP_REF_EXPLICIT) {
+    if (!p->ref_moduli) {
+      msg = "ref_moduli required for MP_REF_EXPLICIT";
+      return MP_E_INVALID_ARG;
+    }
+    for (int i = 0; i < 6; ++i) ref[i] = p->ref_moduli[i];
+  } else {
+    for (int i = 0; i < 6; ++i) ref[i] = (p->ref_kind == MP_REF_MEAN) ? 0.0 : NAN;
+    double lo[6], hi[6];
+    for (int i = 0; i < 6; ++i) {
+      lo[i] = INFINITY;
+      hi[i] = -INFINITY;
+    }
+    for (int k = 0; k < p->n_phases; ++k) {
+      if (counts[k] == 0) continue;
+      const mp_phase& ph = p->phases[k];
+      const double m[6] = {ph.lambda, ph.mu, ph.kappa, ph.alpha, ph.beta, ph.gamma};
+      for (int i = 0; i < 6; ++i) {
+        if (p->ref_kind == MP_REF_MEAN) ref[i] += m[i] * (double)counts[k];
+        lo[i] = std::fmin(lo[i], m[i]);
+        hi[i] = std::fmax(hi[i], m[i]);
+      }
+    }
+    for (int i = 0; i < 6; ++i)
+      ref[i] = (p->ref_kind == MP_REF_MEAN) ? ref[i] / (double)nvox : 0.5 * (lo[i] + hi[i]);
+  }
+  for (int i = 0; i < 6; ++i)
+    if (!finite(ref[i])) {
+      msg = "reference moduli not finite";
+      return MP_E_INVALID_ARG;
+    }
+  // the Green operator needs lam0 + 2 mu0, mu0, kappa0 > 0 and gamma0, alpha0 + beta0 + gamma0 >= 0
+  if (!(ref[0] + 2 * ref[1] > 0) || !(ref[1] > 0) || !(ref[2] > 0) || !(ref[5] >= 0) ||
+      !(ref[3] + ref[4] + ref[5] >= 0)) {
+    msg = "reference medium not admissible for the Green operator";
+    return MP_E_INADMISSIBLE;
+  }
+  return MP_OK;
+}
+
+mp_status validate_problem(const mp_problem* p, std::vector<long long>* counts_out, double ref[6],
+                           std::string& msg) {
+  if (!p) {
+    msg = "problem is NULL";
+    return MP_E_INVALID_ARG;
+  }
+  for (int j = 0; j < 3; ++j)
+    if (p->n[j] < 1) {
+      msg = "grid sizes must be >= 1";
+      return MP_E_INVALID_ARG;
+    }
+  for (int j = 0; j < 3; ++j)
+    if (!size_ok(p->n[j])) {
+      msg = "grid size " + std::to_string(p->n[j]) + " unsupported (1 or even 2^a 3^b <= 512)";
+      return MP_E_UNSUPPORTED_SIZE;
+    }
+  if (!(p->h > 0) || !finite(p->h)) {
+    msg = "voxel size h must be positive";
+    return MP_E_INVALID_ARG;
+  }
+  if (!p->phase || !p->phases || p->n_phases < 1 || p->n_phases > 65536) {
+    msg = "phase map / phase table missing";
+    return MP_E_INVALID_ARG;
+  }
+  for (int k = 0; k < p->n_phases; ++k) {
+    mp_status st = check_phase(p->phases[k], k, msg);
+    if (st != MP_OK) return st;
+  }
+  if (p->n_steps < 1 || !p->time || !p->E || !p->G) {
+    msg = "load path missing";
+    return MP_E_INVALID_ARG;
+  }
+  for (int s = 0; s <= p->n_steps; ++s) {
+    if (!finite(p->time[s])) {
+      msg = "time not finite";
+      return MP_E_INVALID_ARG;
+    }
+    if (s > 0 && !(p->time[s] > p->time[s - 1])) {
+      msg = "time must be strictly increasing";
+      return MP_E_INVALID_ARG;
+    }
+    for (int q = 0; q < 9; ++q)
+      if (!finite(p->E[9 * s + q]) || !finite(p->G[9 * s + q])) {
+        msg = "load path not finite";
+        return MP_E_INVALID_ARG;
+      }
+  }
+  if (!(p->tol > 0) || !finite(p->tol)) {
+    msg = "tol must be positive";
+    return MP_E_INVALID_ARG;
+  }
+  if (p->err_kind != MP_ERR_LOCAL && p->err_kind != MP_ERR_AVERAGE) {
+    msg = "err_kind must be 0 or 1";
+    return MP_E_INVALID_ARG;
+  }
+  if (p->ref_kind < 0 || p->ref_kind > 2) {
+    msg = "ref_kind must be 0, 1 or 2";
+    return MP_E_INVALID_ARG;
+  }
+  if (p->precision != 0 && p->precision != 1) {
+    msg = "precision must be 0 or 1";
+    return MP_E_INVALID_ARG;
+  }
+  if (p->lockstep_iters)
+    for (int s = 0; s < p->n_steps; ++s)
+      if (p->lockstep_iters[s] < 1) {
+        msg = "lockstep iteration counts must be >= 1";
+        return MP_E_INVALID_ARG;
+      }
+  const long long nvox = (long long)p->n[0] * p->n[1] * p->n[2];
+  std::vector<long long> counts(p->n_phases, 0);
+  for (long long v = 0; v < nvox; ++v) {
+    const int id = p->phase[v];
+    if (id >= p->n_phases) {
+      msg = "phase id " + std::to_string(id) + " out of range";
+      return MP_E_INVALID_ARG;
+    }
+    counts[id]++;
+  }
+  mp_status st = reference_moduli(p, counts, nvox, ref, msg);
+  if (st != MP_OK) return st;
+  if (counts_out) *counts_out = std::move(counts);
+  return MP_OK;
+}
+
+// ------------------------------------------------------------------ plans and tables
+void radix_plan(int m, int* radix, int& nst) {
+  nst = 0;
+  int k2 = 0;
+  while (m % 2 == 0) {
+    m /= 2;
+    ++k2;
+  }
+  int k3 = 0;
+  while (m % 3 == 0) {
+    m /= 3;
+    ++k3;
+  }
+  while (k2 >= 3 && k2 - 3 != 1) {
+    radix[nst++] = 8;
+    k2 -= 3;
+  }
+  if (k2 == 4) {
+    radix[nst++] = 4;
+    radix[nst++] = 4;
+  } else if (k2 == 2) {
+    radix[nst++] = 4;
+  } else if (k2 == 1) {
+    radix[nst++] = 2;
+  }
+  for (int i = 0; i < k3; ++i) radix[nst++] = 3;
+}
+
+template <class R>
+mp_status make_axis(mp_ctx* ctx, int n, bool packed, AxisPlan<R>& p, DevBuf& tw, cudaStream_t st,
+                    std::vector<cpx<R>>& host_tw) {
+  p.n = n;
+  p.m = packed ? (n > 1 ? n / 2 : 1) : n;
+  p.tstride = packed ? 2 : 1;
+  radix_plan(p.m, p.radix, p.nstages);
+  host_tw.resize(n);
+  for (int k = 0; k < n; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)n;
+    host_tw[k].x = (R)std::cos(a);
+    host_tw[k].y = (R)(-std::sin(a));
+  }
+  mp_status s = dalloc(ctx, tw, sizeof(cpx<R>) * n);
+  if (s != MP_OK) return s;
+  MP_CK(ctx, cudaMemcpyAsync(tw.ptr, host_tw.data(), sizeof(cpx<R>) * n, cudaMemcpyHostToDevice, st));
+  p.tw = reinterpret_cast<const cpx<R>*>(tw.ptr);
+  return MP_OK;
+}
+
+template <class R>
+PhaseDev<R> phase_dev(const mp_phase& ph) {
+  PhaseDev<R> d{};
+  d.lam = (R)ph.lambda;
+  d.mu = (R)ph.mu;
+  d.kap = (R)ph.kappa;
+  d.alpha = (R)ph.alpha;
+  d.beta = (R)ph.beta;
+  d.gamma = (R)ph.gamma;
+  d.a1 = (R)ph.a1;
+  d.a2 = (R)(ph.a1 * ph.mu / ph.kappa);               // Alg. 1: a2 = a1 mu / kappa
+  d.b1 = (R)ph.b1;
+  d.skew_m = ph.gamma > ph.beta ? 1 : 0;
+  d.b2 = d.skew_m ? (R)(ph.b1 * (ph.gamma + ph.beta) / (ph.gamma - ph.beta)) : (R)0;
+  d.elastic = ph.elastic ? 1 : 0;
+  d.tY = ph.elastic ? INFINITY : ph.tY;
+  d.tH = ph.tH;
+  d.mY = ph.elastic ? INFINITY : ph.mY;
+  d.mH = ph.mH;
+  d.ct = 2.0 * ph.a1 * ph.mu;
+  d.cm = ph.b1 * (ph.gamma + ph.beta);
+  d.inv_t = 1.0 / (ph.tH + d.ct);
+  d.inv_m = 1.0 / (ph.mH + d.cm);
+  return d;
+}
+
+template <class R>
+RefDev<R> ref_dev(const double ref[6]) {
+  RefDev<R> r;
+  r.lam = (R)ref[0];
+  r.mu = (R)ref[1];
+  r.kap = (R)ref[2];
+  r.alpha = (R)ref[3];
+  r.beta = (R)ref[4];
+  r.gamma = (R)ref[5];
+  return r;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ cell state
+struct mp_rve {
+  mp_ctx* ctx = nullptr;
+  int precision = 1;
+  int n[3] = {1, 1, 1};
+  long long nvox = 0, nspec = 0;
+  double h = 1.0;
+  int n_steps = 0;
+  std::vector<double> time, E, G;
+  double tol = 1e-6;
+  int err_kind = 0, max_iter = 10000;
+  std::vector<int> lockstep;
+  double div_limit = 1e6;
+  double ref[6] = {0, 0, 0, 0, 0, 0};
+  DevBuf spec, prev, hist, pq, elast, phase, phases, twx, twy, twz, partials, avgpart, errout, steprows;
+  CellDev<float> cf{};
+  CellDev<double> cd{};
+  LaunchCfg L;
+  int steps_done = 0;
+  bool predicted = false;
+  long long total_iters = 0;
+  int failed_step = 0;
+  std::vector<double> err_steps;
+  std::vector<int> iters_steps;
+  double* err_host = nullptr;  // pinned, 8 doubles
+  // per-kernel-class launch counters and (when profiling) CUDA-event timings
+  long long launches[MP_KC_COUNT] = {0};
+  double kernel_ms[MP_KC_COUNT] = {0};
+  bool profiling = false;
+  cudaEvent_t ev[2 * MP_KC_COUNT] = {};
+};
+
+namespace {
+
+template <class R>
+CellDev<R>& cell_of(mp_rve* r);
+template <>
+CellDev<float>& cell_of<float>(mp_rve* r) { return r->cf; }
+template <>
+CellDev<double>& cell_of<double>(mp_rve* r) { return r->cd; }
+
+template <class R>
+mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
+  mp_ctx* ctx = r->ctx;
+  CellDev<R>& c = cell_of<R>(r);
+  c = CellDev<R>{};
+  c.n1 = p->n[0];
+  c.n2 = p->n[1];
+  c.n3 = p->n[2];
+  c.kx = (c.n1 > 1) ? c.n1 / 2 : 1;
+  c.nvox = r->nvox;
+  c.nspec = (long long)c.kx * c.n2 * c.n3;
+  r->nspec = c.nspec;
+  c.h = p->h;
+  c.inv_nvox = 1.0 / (double)r->nvox;
+  for (int j = 0; j < 3; ++j) c.two_pi_over_L[j] = (R)(2.0 * M_PI / ((double)p->n[j] * p->h));
+  mp_status s;
+  if ((s = dalloc(ctx, r->spec, sizeof(cpx<R>) * 18 * (size_t)c.nspec)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->prev, sizeof(R) * 20 * (size_t)c.nvox)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->hist, sizeof(R) * 18 * (size_t)c.nvox)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->pq, sizeof(double) * 2 * (size_t)c.nvox)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->elast, sizeof(R) * 18 * (size_t)c.nvox)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->phase, sizeof(uint16_t) * (size_t)c.nvox)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->phases, sizeof(PhaseDev<R>) * (size_t)p->n_phases)) != MP_OK) return s;
+  c.spec = reinterpret_cast<cpx<R>*>(r->spec.ptr);
+  c.prev = reinterpret_cast<R*>(r->prev.ptr);
+  c.hist = reinterpret_cast<R*>(r->hist.ptr);
+  c.pq = reinterpret_cast<double*>(r->pq.ptr);
+  c.elast = reinterpret_cast<R*>(r->elast.ptr);
+  c.phase = reinterpret_cast<const uint16_t*>(r->phase.ptr);
+  c.phases = reinterpret_cast<const PhaseDev<R>*>(r->phases.ptr);
+  c.ref = ref_dev<R>(r->ref);
+  std::vector<PhaseDev<R>> ph(p->n_phases);
+  for (int k = 0; k < p->n_phases; ++k) ph[k] = phase_dev<R>(p->phases[k]);
+  std::vector<cpx<R>> t1, t2, t3;
+  if ((s = make_axis<R>(ctx, c.n1, true, c.px, r->twx, st, t1)) != MP_OK) return s;
+  if ((s = make_axis<R>(ctx, c.n2, false, c.py, r->twy, st, t2)) != MP_OK) return s;
+  if ((s = make_axis<R>(ctx, c.n3, false, c.pz, r->twz, st, t3)) != MP_OK) return s;
+  MP_CK(ctx, cudaMemcpyAsync(r->phase.ptr, p->phase, sizeof(uint16_t) * (size_t)c.nvox,
+                             cudaMemcpyHostToDevice, st));
+  MP_CK(ctx, cudaMemcpyAsync(r->phases.ptr, ph.data(), sizeof(PhaseDev<R>) * ph.size(),
+                             cudaMemcpyHostToDevice, st));
+  r->L = make_launch_cfg<R>(c, ctx->nsm);
+  if ((s = dalloc(ctx, r->partials, sizeof(double) * kErrPartials * (size_t)r->L.grid_a)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->avgpart, sizeof(double) * kAvgPartials * (size_t)r->L.grid_v)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->errout, sizeof(double) * 8)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->steprows, sizeof(double) * kAvgPartials * (size_t)r->n_steps)) != MP_OK) return s;
+  MP_CK(ctx, cudaMemsetAsync(r->steprows.ptr, 0, r->steprows.bytes, st));
+  // host tables are stack-local: finish the uploads before returning
+  MP_CK(ctx, cudaStreamSynchronize(st));
+  return MP_OK;
+}
+
+template <class R>
+void set_load(CellDev<R>& c, const mp_rve* r, int s) {
+  for (int q = 0; q < 9; ++q) {
+    c.E[q] = (R)r->E[9 * s + q];
+    c.G[q] = (R)r->G[9 * s + q];
+  }
+}
+
+// One load increment s (1-based): predictor, fixed-point loop, commit.
+template <class R>
+mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
+  mp_ctx* ctx = r->ctx;
+  CellDev<R>& c = cell_of<R>(r);
+  set_load(c, r, s);
+  MP_CK(ctx, launch_start<R>(r->L, c, s == 1 ? 1 : 0, st));
+  r->launches[MP_KC_START] += (s == 1) ? 2 : 1;
+  double err = 2.0 * r->tol;
+  int it = 0;
+  const int target = r->lockstep.empty() ? -1 : r->lockstep[s - 1];
+  mp_status status = MP_OK;
+  while (target >= 0 ? it < target : err > r->tol) {
+    if (target < 0 && it >= r->max_iter) {
+      status = MP_E_NOT_CONVERGED;
+      break;
+    }
+    double* parts = reinterpret_cast<double*>(r->partials.ptr);
+    double* eout = reinterpret_cast<double*>(r->errout.ptr);
+    const bool ydo = c.n2 > 1;
+    const bool prof = r->profiling;
+    auto mark = [&](int k, int end) {
+      if (prof) cudaEventRecord(r->ev[2 * k + end], st);
+    };
+    mark(MP_KC_FFT_Y_FWD, 0);
+    MP_CK(ctx, launch_fft_y<R>(r->L, c, -1, st));
+    mark(MP_KC_FFT_Y_FWD, 1);
+    mark(MP_KC_GREEN_Z, 0);
+    MP_CK(ctx, launch_green_z<R>(r->L, c, st));
+    mark(MP_KC_GREEN_Z, 1);
+    mark(MP_KC_FFT_Y_INV, 0);
+    MP_CK(ctx, launch_fft_y<R>(r->L, c, +1, st));
+    mark(MP_KC_FFT_Y_INV, 1);
+    mark(MP_KC_PASS_A, 0);
+    MP_CK(ctx, launch_pass_a_iter<R>(r->L, c, parts, st));
+    mark(MP_KC_PASS_A, 1);
+    mark(MP_KC_REDUCE, 0);
+    MP_CK(ctx, launch_reduce_err<R>(r->L, c, parts, r->err_kind, eout, st));
+    mark(MP_KC_REDUCE, 1);
+    MP_CK(ctx, cudaMemcpyAsync(r->err_host, r->errout.ptr, sizeof(double) * 5, cudaMemcpyDeviceToHost, st));
+    MP_CK(ctx, cudaStreamSynchronize(st));
+    if (ydo) {
+      r->launches[MP_KC_FFT_Y_FWD]++;
+      r->launches[MP_KC_FFT_Y_INV]++;
+    }
+    r->launches[MP_KC_GREEN_Z]++;
+    r->launches[MP_KC_PASS_A]++;
+    r->launches[MP_KC_REDUCE]++;
+    if (prof) {
+      const int ks[5] = {MP_KC_FFT_Y_FWD, MP_KC_GREEN_Z, MP_KC_FFT_Y_INV, MP_KC_PASS_A, MP_KC_REDUCE};
+      for (int k : ks) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r->ev[2 * k], r->ev[2 * k + 1]) == cudaSuccess) r->kernel_ms[k] += ms;
+      }
+    }
+    err = r->err_host[0];
+    ++it;
+    if (!std::isfinite(err) || err > r->div_limit) {
+      status = MP_E_DIVERGED;
+      break;
+    }
+  }
+  r->total_iters += it;
+  const bool predict = (status == MP_OK) && (s < r->n_steps);
+  const double ratio =
+      predict ? (r->time[s + 1] - r->time[s]) / (r->time[s] - r->time[s - 1]) : 0.0;
+  MP_CK(ctx, launch_commit<R>(r->L, c, predict ? 1 : 0, ratio, reinterpret_cast<double*>(r->avgpart.ptr),
+                              reinterpret_cast<double*>(r->steprows.ptr) + (size_t)kAvgPartials * (s - 1),
+                              st));
+  r->launches[MP_KC_COMMIT] += 2;
+  r->err_steps.push_back(err);
+  r->iters_steps.push_back(it);
+  r->steps_done = s;
+  r->predicted = predict;
+  if (status != MP_OK) {
+    r->failed_step = s;
+    return set_error(ctx, status, "load increment %d %s after %d iterations (err %.3e)", s,
+                     status == MP_E_DIVERGED ? "diverged" : "did not converge", it, err);
+  }
+  return MP_OK;
+}
+
+void rve_free(mp_rve* r) {
+  mp_ctx* ctx = r->ctx;
+  DevBuf* bufs[] = {&r->spec, &r->prev, &r->hist, &r->pq, &r->elast, &r->phase, &r->phases,
+                    &r->twx, &r->twy, &r->twz, &r->partials, &r->avgpart, &r->errout, &r->steprows};
+  for (DevBuf* b : bufs) dfree(ctx, *b);
+  if (r->err_host) cudaFreeHost(r->err_host);
+  r->err_host = nullptr;
+  for (auto& e : r->ev)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
+}
+
+mp_status use_device(mp_ctx* ctx) {
+  MP_CK(ctx, cudaSetDevice(ctx->device));
+  return MP_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+int32_t mp_abi_version(void) { return MP_ABI_VERSION; }
+
+const char* mp_last_error(const mp_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : g_last_error.c_str();
+}
+
+mp_status mp_validate(const mp_problem* problem, char* message, size_t message_len) {
+  std::string msg;
+  double ref[6];
+  mp_status st = validate_problem(problem, nullptr, ref, msg);
+  if (message && message_len > 0) {
+    std::snprintf(message, message_len, "%s", msg.c_str());
+  }
+  return st;
+}
+
+mp_status mp_create(mp_ctx** out, int32_t device, const mp_alloc* alloc) {
+  if (!out) return set_error(nullptr, MP_E_INVALID_ARG, "ctx pointer is NULL");
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count <= 0)
+    return set_error(nullptr, MP_E_NO_DEVICE, "no CUDA device: %s", cudaGetErrorString(e));
+  if (device < 0 || device >= count)
+    return set_error(nullptr, MP_E_NO_DEVICE, "device %d out of range (%d devices)", device, count);
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) return set_error(nullptr, MP_E_NO_DEVICE, "%s", cudaGetErrorString(e));
+  mp_ctx* ctx = new mp_ctx();
+  ctx->device = device;
+  ctx->nsm = prop.multiProcessorCount;
+  if (alloc && alloc->alloc && alloc->free) {
+    ctx->alloc = *alloc;
+    ctx->has_alloc = true;
+  }
+  *out = ctx;
+  return MP_OK;
+}
+
+void mp_destroy(mp_ctx* ctx) { delete ctx; }
+
+mp_status mp_rve_create(mp_ctx* ctx, const mp_problem* p, mp_rve** out, void* stream) {
+  if (!ctx || !out) return set_error(ctx, MP_E_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  std::string msg;
+  double ref[6];
+  std::vector<long long> counts;
+  mp_status st = validate_problem(p, &counts, ref, msg);
+  if (st != MP_OK) return set_error(ctx, st, "%s", msg.c_str());
+  if ((st = use_device(ctx)) != MP_OK) return st;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  mp_rve* r = new mp_rve();
+  r->ctx = ctx;
+  r->precision = p->precision;
+  for (int j = 0; j < 3; ++j) r->n[j] = p->n[j];
+  r->nvox = (long long)p->n[0] * p->n[1] * p->n[2];
+  r->h = p->h;
+  r->n_steps = p->n_steps;
+  r->time.assign(p->time, p->time + p->n_steps + 1);
+  r->E.assign(p->E, p->E + 9 * (p->n_steps + 1));
+  r->G.assign(p->G, p->G + 9 * (p->n_steps + 1));
+  r->tol = p->tol;
+  r->err_kind = p->err_kind;
+  r->max_iter = p->max_iter > 0 ? p->max_iter : 10000;
+  if (p->lockstep_iters) r->lockstep.assign(p->lockstep_iters, p->lockstep_iters + p->n_steps);
+  r->div_limit = p->div_limit > 0 ? p->div_limit : 1e6;
+  for (int i = 0; i < 6; ++i) r->ref[i] = ref[i];
+  cudaError_t e = cudaMallocHost(&r->err_host, sizeof(double) * 8);
+  if (e != cudaSuccess) {
+    r->err_host = nullptr;
+    delete r;
+    return set_error(ctx, MP_E_CUDA, "cudaMallocHost: %s", cudaGetErrorString(e));
+  }
+  st = (r->precision == 0) ? rve_setup<double>(r, p, cs) : rve_setup<float>(r, p, cs);
+  if (st != MP_OK) {
+    rve_free(r);
+    delete r;
+    return st;
+  }
+  *out = r;
+  return MP_OK;
+}
+
+mp_status mp_rve_reset(mp_rve* r, void* stream) {
+  if (!r) return set_error(nullptr, MP_E_INVALID_ARG, "rve is NULL");
+  (void)stream;
+  r->steps_done = 0;
+  r->predicted = false;
+  r->total_iters = 0;
+  r->failed_step = 0;
+  r->err_steps.clear();
+  r->iters_steps.clear();
+  return MP_OK;
+}
+
+mp_status mp_rve_run(mp_rve* r, int32_t n_steps, void* stream) {
+  if (!r) return set_error(nullptr, MP_E_INVALID_ARG, "rve is NULL");
+  mp_status st = use_device(r->ctx);
+  if (st != MP_OK) return st;
+  if (r->failed_step) return set_error(r->ctx, MP_E_INVALID_ARG, "cell failed at step %d; reset first", r->failed_step);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  for (int k = 0; k < n_steps && r->steps_done < r->n_steps; ++k) {
+    const int s = r->steps_done + 1;
+    st = (r->precision == 0) ? run_step<double>(r, s, cs) : run_step<float>(r, s, cs);
+    if (st != MP_OK) return st;
+  }
+  return MP_OK;
+}
+
+int32_t mp_rve_steps_done(const mp_rve* r) { return r ? r->steps_done : 0; }
+
+mp_status mp_rve_profile(mp_rve* r, int32_t enable) {
+  if (!r) return set_error(nullptr, MP_E_INVALID_ARG, "rve is NULL");
+  mp_status st = use_device(r->ctx);
+  if (st != MP_OK) return st;
+  if (enable && !r->ev[0]) {
+    for (auto& e : r->ev) MP_CK(r->ctx, cudaEventCreate(&e));
+  }
+  r->profiling = enable != 0;
+  return MP_OK;
+}
+
+mp_status mp_rve_profile_read(const mp_rve* r, double* ms, int64_t* launches, int32_t reset) {
+  if (!r) return set_error(nullptr, MP_E_INVALID_ARG, "rve is NULL");
+  for (int k = 0; k < MP_KC_COUNT; ++k) {
+    if (ms) ms[k] = r->kernel_ms[k];
+    if (launches) launches[k] = r->launches[k];
+  }
+  if (reset) {
+    mp_rve* w = const_cast<mp_rve*>(r);
+    for (int k = 0; k < MP_KC_COUNT; ++k) {
+      w->kernel_ms[k] = 0.0;
+      w->launches[k] = 0;
+    }
+  }
+  return MP_OK;
+}
+int64_t mp_rve_iterations(const mp_rve* r) { return r ? r->total_iters : 0; }
+
+mp_status mp_rve_results(mp_rve* r, mp_result* res, void* stream) {
+  if (!r || !res) return set_error(r ? r->ctx : nullptr, MP_E_INVALID_ARG, "NULL argument");
+  mp_ctx* ctx = r->ctx;
+  mp_status st = use_device(ctx);
+  if (st != MP_OK) return st;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  const int ns = r->steps_done;
+  std::vector<double> rows((size_t)kAvgPartials * (ns > 0 ? ns : 1));
+  if (ns > 0)
+    MP_CK(ctx, cudaMemcpyAsync(rows.data(), r->steprows.ptr, sizeof(double) * kAvgPartials * ns,
+                               cudaMemcpyDeviceToHost, cs));
+  // final fields (of the last committed step)
+  const bool want = res->e || res->g || res->t || res->m || res->p || res->q;
+  DevBuf fbuf;
+  if (want && ns > 0) {
+    const size_t nv = (size_t)r->nvox;
+    if ((st = dalloc(ctx, fbuf, sizeof(double) * 38 * nv)) != MP_OK) return st;
+    double* b = reinterpret_cast<double*>(fbuf.ptr);
+    double *fe = b, *fg = b + 9 * nv, *ft = b + 18 * nv, *fm = b + 27 * nv, *fp = b + 36 * nv, *fq = b + 37 * nv;
+    cudaError_t e = (r->precision == 0)
+                        ? launch_fields<double>(r->L, r->cd, r->predicted ? 1 : 0, fe, fg, ft, fm, fp, fq, cs)
+                        : launch_fields<float>(r->L, r->cf, r->predicted ? 1 : 0, fe, fg, ft, fm, fp, fq, cs);
+    if (e != cudaSuccess) {
+      dfree(ctx, fbuf);
+      return set_error(ctx, MP_E_CUDA, "fields kernel: %s", cudaGetErrorString(e));
+    }
+    struct {
+      double* dst;
+      double* src;
+      size_t n;
+    } cp[6] = {{res->e, fe, 9 * nv}, {res->g, fg, 9 * nv}, {res->t, ft, 9 * nv},
+               {res->m, fm, 9 * nv}, {res->p, fp, nv},     {res->q, fq, nv}};
+    for (auto& x : cp)
+      if (x.dst) {
+        e = cudaMemcpyAsync(x.dst, x.src, sizeof(double) * x.n, cudaMemcpyDeviceToHost, cs);
+        if (e != cudaSuccess) break;
+      }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    dfree(ctx, fbuf);
+    if (e != cudaSuccess) return set_error(ctx, MP_E_CUDA, "field copy: %s", cudaGetErrorString(e));
+  }
+  MP_CK(ctx, cudaStreamSynchronize(cs));
+  for (int s = 0; s < ns; ++s) {
+    const double* row = rows.data() + (size_t)kAvgPartials * s;
+    for (int q = 0; q < 9; ++q) {
+      if (res->T) res->T[9 * s + q] = row[q];
+      if (res->M) res->M[9 * s + q] = row[9 + q];
+      if (res->Eavg) res->Eavg[9 * s + q] = row[18 + q];
+      if (res->Gavg) res->Gavg[9 * s + q] = row[27 + q];
+    }
+    if (res->P) res->P[s] = row[36];
+    if (res->Q) res->Q[s] = row[37];
+    if (res->Teq) res->Teq[s] = row[38];
+    if (res->Meq) res->Meq[s] = row[39];
+    if (res->err) res->err[s] = r->err_steps[s];
+    if (res->iters) res->iters[s] = r->iters_steps[s];
+  }
+  res->steps_done = ns;
+  res->failed_step = r->failed_step;
+  for (int i = 0; i < 6; ++i) res->ref_moduli_used[i] = r->ref[i];
+  return MP_OK;
+}
+
+void mp_rve_destroy(mp_rve* r) {
+  if (!r) return;
+  if (r->ctx) cudaSetDevice(r->ctx->device);
+  rve_free(r);
+  delete r;
+}
+
+mp_status mp_solve(mp_ctx* ctx, const mp_problem* p, mp_result* res, void* stream) {
+  mp_rve* r = nullptr;
+  mp_status st = mp_rve_create(ctx, p, &r, stream);
+  if (st != MP_OK) return st;
+  mp_status run = mp_rve_run(r, p->n_steps, stream);
+  std::string run_msg = ctx->last_error;
+  if (res) {
+    mp_status rs = mp_rve_results(r, res, stream);
+    if (run == MP_OK && rs != MP_OK) run = rs;
+  }
+  mp_rve_destroy(r);
+  if (run != MP_OK && !run_msg.empty()) ctx->last_error = run_msg;
+  return run;
+}
+
+// ------------------------------------------------------------------ components
+mp_status mp_radial_return(mp_ctx* ctx, int32_t precision, int64_t count, const uint16_t* phase,
+                           int32_t n_phases, const mp_phase* phases, const void* e, const void* g,
+                           const void* e_n, const void* g_n, const void* t_n, const void* m_n,
+                           const double* p_n, const double* q_n, void* t, void* m, double* p,
+                           double* q, void* stream) {
+  if (!ctx) return set_error(nullptr, MP_E_INVALID_ARG, "ctx is NULL");
+  if (count < 0 || n_phases < 1 || !phases || (precision != 0 && precision != 1))
+    return set_error(ctx, MP_E_INVALID_ARG, "invalid arguments");
+  if (count > 0 && (!phase || !e || !g || !e_n || !g_n || !t_n || !m_n || !p_n || !q_n || !t || !m || !p || !q))
+    return set_error(ctx, MP_E_INVALID_ARG, "NULL buffer");
+  std::string msg;
+  for (int k = 0; k < n_phases; ++k) {
+    mp_status s = check_phase(phases[k], k, msg);
+    if (s != MP_OK) return set_error(ctx, s, "%s", msg.c_str());
+  }
+  mp_status st = use_device(ctx);
+  if (st != MP_OK) return st;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  DevBuf tab;
+  if (precision == 0) {
+    std::vector<PhaseDev<double>> ph(n_phases);
+    for (int k = 0; k < n_phases; ++k) ph[k] = phase_dev<double>(phases[k]);
+    if ((st = dalloc(ctx, tab, sizeof(PhaseDev<double>) * n_phases)) != MP_OK) return st;
+    cudaError_t e1 = cudaMemcpyAsync(tab.ptr, ph.data(), tab.bytes, cudaMemcpyHostToDevice, cs);
+    if (e1 == cudaSuccess)
+      e1 = launch_radial_return<double>(ctx->nsm, count, phase, (const PhaseDev<double>*)tab.ptr,
+                                        (const double*)e, (const double*)g, (const double*)e_n,
+                                        (const double*)g_n, (const double*)t_n, (const double*)m_n, p_n,
+                                        q_n, (double*)t, (double*)m, p, q, cs);
+    if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(cs);
+    dfree(ctx, tab);
+    if (e1 != cudaSuccess) return set_error(ctx, MP_E_CUDA, "radial return: %s", cudaGetErrorString(e1));
+  } else {
+    std::vector<PhaseDev<float>> ph(n_phases);
+    for (int k = 0; k < n_phases; ++k) ph[k] = phase_dev<float>(phases[k]);
+    if ((st = dalloc(ctx, tab, sizeof(PhaseDev<float>) * n_phases)) != MP_OK) return st;
+    cudaError_t e1 = cudaMemcpyAsync(tab.ptr, ph.data(), tab.bytes, cudaMemcpyHostToDevice, cs);
+    if (e1 == cudaSuccess)
+      e1 = launch_radial_return<float>(ctx->nsm, count, phase, (const PhaseDev<float>*)tab.ptr,
+                                       (const float*)e, (const float*)g, (const float*)e_n,
+                                       (const float*)g_n, (const float*)t_n, (const float*)m_n, p_n,
+                                       q_n, (float*)t, (float*)m, p, q, cs);
+    if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(cs);
+    dfree(ctx, tab);
+    if (e1 != cudaSuccess) return set_error(ctx, MP_E_CUDA, "radial return: %s", cudaGetErrorString(e1));
+  }
+  return MP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <class R>
+mp_status green_apply_impl(mp_ctx* ctx, const int32_t n[3], double h, const double ref[6], const void* tau,
+                           const void* mu, void* e_out, void* g_out, cudaStream_t cs) {
+  CellDev<R> c{};
+  c.n1 = n[0];
+  c.n2 = n[1];
+  c.n3 = n[2];
+  c.kx = (c.n1 > 1) ? c.n1 / 2 : 1;
+  c.nvox = (long long)n[0] * n[1] * n[2];
+  c.nspec = (long long)c.kx * n[1] * n[2];
+  c.h = h;
+  c.inv_nvox = 1.0 / (double)c.nvox;
+  for (int j = 0; j < 3; ++j) c.two_pi_over_L[j] = (R)(2.0 * M_PI / ((double)n[j] * h));
+  c.ref = ref_dev<R>(ref);
+  DevBuf spec, tx, ty, tz;
+  std::vector<cpx<R>> h1, h2, h3;
+  mp_status st = dalloc(ctx, spec, sizeof(cpx<R>) * 18 * (size_t)c.nspec);
+  if (st == MP_OK) st = make_axis<R>(ctx, c.n1, true, c.px, tx, cs, h1);
+  if (st == MP_OK) st = make_axis<R>(ctx, c.n2, false, c.py, ty, cs, h2);
+  if (st == MP_OK) st = make_axis<R>(ctx, c.n3, false, c.pz, tz, cs, h3);
+  if (st == MP_OK) {
+    c.spec = reinterpret_cast<cpx<R>*>(spec.ptr);
+    LaunchCfg L = make_launch_cfg<R>(c, ctx->nsm);
+    cudaError_t e = launch_green_apply<R>(L, c, (const R*)tau, (const R*)mu, (R*)e_out, (R*)g_out, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) st = set_error(ctx, MP_E_CUDA, "green apply: %s", cudaGetErrorString(e));
+  }
+  cudaStreamSynchronize(cs);
+  dfree(ctx, spec);
+  dfree(ctx, tx);
+  dfree(ctx, ty);
+  dfree(ctx, tz);
+  return st;
+}
+}  // namespace
+
+extern "C" {
+
+mp_status mp_green_apply(mp_ctx* ctx, int32_t precision, const int32_t n[3], double h,
+                         const double ref_moduli[6], const void* tau, const void* mu, void* e_out,
+                         void* g_out, void* stream) {
+  if (!ctx) return set_error(nullptr, MP_E_INVALID_ARG, "ctx is NULL");
+  if (!n || !ref_moduli || !tau || !mu || !e_out || !g_out || (precision != 0 && precision != 1))
+    return set_error(ctx, MP_E_INVALID_ARG, "invalid arguments");
+  for (int j = 0; j < 3; ++j)
+    if (n[j] < 1 || !size_ok(n[j])) return set_error(ctx, MP_E_UNSUPPORTED_SIZE, "grid size %d unsupported", n[j]);
+  if (!(h > 0)) return set_error(ctx, MP_E_INVALID_ARG, "h must be positive");
+  const double* r = ref_moduli;
+  if (!(r[0] + 2 * r[1] > 0) || !(r[1] > 0) || !(r[2] > 0) || !(r[5] >= 0) || !(r[3] + r[4] + r[5] >= 0))
+    return set_error(ctx, MP_E_INADMISSIBLE, "reference medium not admissible for the Green operator");
+  mp_status st = use_device(ctx);
+  if (st != MP_OK) return st;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  return precision == 0 ? green_apply_impl<double>(ctx, n, h, ref_moduli, tau, mu, e_out, g_out, cs)
+                        : green_apply_impl<float>(ctx, n, h, ref_moduli, tau, mu, e_out, g_out, cs);
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Shared device-side types of the micropolar FFT solver (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mp {
+
+// ---------------------------------------------------------------- complex
+template <class R>
+struct cpx {
+  R x, y;
+};
+
+template <class R>
+__device__ __forceinline__ cpx<R> cmake(R a, R b) {
+  cpx<R> c;
+  c.x = a;
+  c.y = b;
+  return c;
+}
+template <class R>
+__device__ __forceinline__ cpx<R> cadd(cpx<R> a, cpx<R> b) { return cmake<R>(a.x + b.x, a.y + b.y); }
+template <class R>
+__device__ __forceinline__ cpx<R> csub(cpx<R> a, cpx<R> b) { return cmake<R>(a.x - b.x, a.y - b.y); }
+template <class R>
+__device__ __forceinline__ cpx<R> cmul(cpx<R> a, cpx<R> b) {
+  return cmake<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <class R>
+__device__ __forceinline__ cpx<R> cconj(cpx<R> a) { return cmake<R>(a.x, -a.y); }
+template <class R>
+__device__ __forceinline__ cpx<R> cscale(cpx<R> a, R s) { return cmake<R>(a.x * s, a.y * s); }
+// multiply by i
+template <class R>
+__device__ __forceinline__ cpx<R> cmuli(cpx<R> a) { return cmake<R>(-a.y, a.x); }
+
+// ---------------------------------------------------------------- phases
+// Per-phase constants prepared on the host in FP64.  Moduli are kept in the
+// field type R for the linear algebra; the scalar part of the radial return
+// uses the double members.
+template <class R>
+struct PhaseDev {
+  R lam, mu, kap, alpha, beta, gamma;   // eq. stiffnesses_iso
+  R a1, a2, b1, b2;                     // eq. equiv_stress / equiv_couple_stress (b2 = 0 if gamma == beta)
+  double tY, tH, mY, mH;                // eq. radius_1 / radius_2 (elastic: +inf yield)
+  double ct, cm;                        // 2 a1 mu and b1 (gamma + beta) (eq. trial_stresses2)
+  double inv_t, inv_m;                  // 1 / (tH + ct), 1 / (mH + cm)
+  int elastic;
+  int skew_m;                           // 1 when gamma > beta (b2 finite, skew part of m live)
+};
+
+// Reference medium (A0, B0) in the field type.
+template <class R>
+struct RefDev {
+  R lam, mu, kap, alpha, beta, gamma;
+};
+
+// FFT plan of one axis: length N, radix sequence for the complex transform of
+// length M (M = N / 2 for the packed real x-axis, M = N otherwise) and the
+// device twiddle table W_T^k = exp(-2 pi i k / T), k < T, with T = N.
+template <class R>
+struct AxisPlan {
+  int n;          // axis length
+  int m;          // complex transform length
+  int tstride;    // twiddle table stride: W_m^k = table[k * tstride]
+  int nstages;
+  int radix[10];
+  const cpx<R>* tw;  // table of length n (n >= 1)
+};
+
+// Per-cell device descriptor.
+template <class R>
+struct CellDev {
+  int n1, n2, n3;
+  int kx;                 // complex entries per spectral row: N1 / 2, or 1 when N1 == 1
+  long long nvox;         // N1 N2 N3
+  long long nspec;        // kx N2 N3
+  double h;
+  double inv_nvox;        // 1 / (N1 N2 N3)
+  R two_pi_over_L[3];     // 2 pi / (N_j h)
+  cpx<R>* spec;           // [nspec][18]  polarization / fluctuation spectra
+  R* prev;                // [nvox][20]   e, gamma of the last iterate + scale factors f_t, f_m
+  R* hist;                // [nvox][18]   h_t = t_n - A e_n, h_m = m_n - B gamma_n
+  double* pq;             // [nvox][2]    p_n, q_n
+  R* elast;               // [nvox][18]   converged e, gamma of the step before (predictor)
+  const uint16_t* phase;  // [nvox]
+  const PhaseDev<R>* phases;
+  RefDev<R> ref;
+  AxisPlan<R> px, py, pz;
+  R E[9], G[9];           // prescribed averages of the current step
+};
+
+// Number of doubles in one block partial of the iteration error reduction:
+// 4 maxima of |delta a|, 4 sums of |delta a|, 36 sums of e, t, gamma, m.
+constexpr int kErrPartials = 44;
+// Number of doubles in one block partial of the commit reduction:
+// T (9), M (9), <e> (9), <gamma> (9), P, Q, T_eq, M_eq.
+constexpr int kAvgPartials = 40;
+
+}  // namespace mp

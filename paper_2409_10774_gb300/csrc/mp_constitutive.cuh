@@ -1,0 +1,142 @@
+// Material-point update of the micropolar elastoplastic model (sm_103a).
+//
+// Implements Algorithm 1 (micropolar radial-return mapping) of Francis et al.
+// with the closed-form plastic multipliers of eq. trial_stresses2.  Tensors
+// are 9 values row-major (3k + l).  The trial stresses use the history form
+// t_trial = h_t + A e with h_t = t_n - A e_n (eq. trial_stresses rearranged),
+// and likewise m_trial = h_m + B gamma.
+//
+// Because Alg. 1 sets a2 = a1 mu / kappa and b2 = b1 (gamma + beta) /
+// (gamma - beta), the symmetric and skew factors of each level coincide:
+//   s_(kl) and s_[kl] are scaled by R1 / (R1 + 2 a1 mu (p - p_n)),
+//   m_(kl) and m_[kl] are scaled by R2 / (R2 + b1 (gamma + beta) (q - q_n)),
+// so the update is one scale factor per level.  When gamma == beta the skew
+// part of m is identically zero and the b2 term of m_eq is dropped.
+#pragma once
+
+#include "mp_common.cuh"
+
+namespace mp {
+
+// t_kl = lam tr(e) d_kl + (mu + kappa) e_kl + (mu - kappa) e_lk  (eq. elast_constitutive_iso)
+template <class R>
+__device__ __forceinline__ void apply_A(R lam, R mu, R kap, const R* e, R* t) {
+  const R tr = e[0] + e[4] + e[8];
+  const R a = mu + kap, b = mu - kap;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int l = 0; l < 3; ++l) t[3 * k + l] = a * e[3 * k + l] + b * e[3 * l + k] + (k == l ? lam * tr : R(0));
+  }
+}
+
+// m_kl = B_lkmn gamma_mn = alpha tr(gamma) d_kl + beta gamma_kl + gamma gamma_lk
+template <class R>
+__device__ __forceinline__ void apply_B(R al, R be, R ga, const R* g, R* m) {
+  const R tr = g[0] + g[4] + g[8];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int l = 0; l < 3; ++l) m[3 * k + l] = be * g[3 * k + l] + ga * g[3 * l + k] + (k == l ? al * tr : R(0));
+  }
+}
+
+// a1 |s_(kl)|^2 + a2 |s_[kl]|^2 of a deviator s (eq. equiv_stress squared)
+template <class R>
+__device__ __forceinline__ R eq_sq(const R* s, R c_sym, R c_skw, bool with_skw) {
+  const R d = s[0] * s[0] + s[4] * s[4] + s[8] * s[8];
+  const R y01 = R(0.5) * (s[1] + s[3]), k01 = R(0.5) * (s[1] - s[3]);
+  const R y02 = R(0.5) * (s[2] + s[6]), k02 = R(0.5) * (s[2] - s[6]);
+  const R y12 = R(0.5) * (s[5] + s[7]), k12 = R(0.5) * (s[5] - s[7]);
+  R v = c_sym * (d + R(2) * (y01 * y01 + y02 * y02 + y12 * y12));
+  if (with_skw) v += c_skw * R(2) * (k01 * k01 + k02 * k02 + k12 * k12);
+  return v;
+}
+
+// Trial stresses of a material point (eq. trial_stresses, history form).
+template <class R>
+__device__ __forceinline__ void trial(const PhaseDev<R>& P, const R* e, const R* g, const R* ht,
+                                      const R* hm, R* t, R* m) {
+  apply_A(P.lam, P.mu, P.kap, e, t);
+  apply_B(P.alpha, P.beta, P.gamma, g, m);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    t[i] += ht[i];
+    m[i] += hm[i];
+  }
+}
+
+// Final stresses from the trial ones and the two scale factors:
+// t = tr(t_trial)/3 d + f_t dev(t_trial), m = f_m m_trial.
+template <class R>
+__device__ __forceinline__ void assemble(R* t, R* m, R ft, R fm) {
+  const R vol = (t[0] + t[4] + t[8]) * R(1.0 / 3.0);
+  t[0] = vol + ft * (t[0] - vol);
+  t[4] = vol + ft * (t[4] - vol);
+  t[8] = vol + ft * (t[8] - vol);
+  t[1] *= ft; t[2] *= ft; t[3] *= ft; t[5] *= ft; t[6] *= ft; t[7] *= ft;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) m[i] *= fm;
+}
+
+// Algorithm 1.  In: e, g (gamma), history ht, hm, p_n, q_n.  Out: t, m (final
+// stresses), p, q and the scale factors ft, fm (1 on elastic branches).
+template <class R>
+__device__ __forceinline__ void radial_return(const PhaseDev<R>& P, const R* e, const R* g,
+                                              const R* ht, const R* hm, double pn, double qn, R* t,
+                                              R* m, double& p, double& q, R& ft, R& fm) {
+  trial(P, e, g, ht, hm, t, m);
+  p = pn;
+  q = qn;
+  ft = R(1);
+  fm = R(1);
+  if (!P.elastic) {
+    // macro level (eq. equiv_stress on the trial deviator)
+    R s[9];
+    const R vol = (t[0] + t[4] + t[8]) * R(1.0 / 3.0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) s[i] = t[i];
+    s[0] -= vol; s[4] -= vol; s[8] -= vol;
+    const double teq2 = (double)eq_sq(s, P.a1, P.a2, true);
+    const double R1n = P.tY + P.tH * pn;
+    if (!(teq2 < R1n * R1n)) {          // plastic: t_eq^trial >= t_Y + t_H p_n
+      const double teq = sqrt(teq2);
+      const double dp = (teq - R1n) * P.inv_t;   // eq. trial_stresses2: p - p_n
+      p = pn + dp;
+      const double R1 = P.tY + P.tH * p;
+      ft = (R)(R1 / (R1 + P.ct * dp));
+    }
+    // micro level (eq. equiv_couple_stress on the trial couple stress)
+    const double meq2 = (double)eq_sq(m, P.b1, P.b2, P.skew_m != 0) ;
+    const double R2n = P.mY + P.mH * qn;
+    if (!(meq2 < R2n * R2n)) {
+      const double meq = sqrt(meq2);
+      const double dq = (meq - R2n) * P.inv_m;
+      q = qn + dq;
+      const double R2 = P.mY + P.mH * q;
+      fm = (R)(R2 / (R2 + P.cm * dq));
+    }
+  }
+  assemble(t, m, ft, fm);
+}
+
+// eq_sq for a full (non-deviatoric) couple stress: m_eq^2 uses m itself.
+// (eq_sq works on any tensor; for t the caller passes the deviator.)
+
+// t_eq(t) and m_eq(m) of returned stresses, in FP64 (homogenized outputs).
+template <class R>
+__device__ __forceinline__ void equivalents(const PhaseDev<R>& P, const R* t, const R* m,
+                                            double& teq, double& meq) {
+  double s[9], mm[9];
+  const double vol = ((double)t[0] + (double)t[4] + (double)t[8]) / 3.0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    s[i] = (double)t[i];
+    mm[i] = (double)m[i];
+  }
+  s[0] -= vol; s[4] -= vol; s[8] -= vol;
+  teq = sqrt(eq_sq(s, (double)P.a1, (double)P.a2, true));
+  meq = sqrt(eq_sq(mm, (double)P.b1, (double)P.b2, P.skew_m != 0));
+}
+
+}  // namespace mp

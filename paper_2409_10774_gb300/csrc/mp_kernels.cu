@@ -1,0 +1,825 @@
+// Kernels of one fixed-point iteration of the micropolar FFT scheme (sm_103a)
+// and their launchers.  Spectral buffer layout: complex spec[(kz N2 + ky) KX
+// + kx][18], 18 = (tau or e^: 9 comps, mu or gamma^: 9 comps), KX = N1 / 2
+// (the Nyquist column kx = N1 / 2 is never stored: the Green operator zeroes
+// it) or 1 when N1 == 1.
+//
+// One iteration (Algorithm 2 while-loop) runs
+//   y-forward  ->  z-forward + Green + z-inverse  ->  y-inverse  ->  pass A
+// where pass A does, row by row along x: inverse x transform, + (E, Gamma),
+// Algorithm 1, error partials against the previous iterate, polarizations
+// tau = t - A0 e, mu = m - B0 gamma, forward x transform.
+#include "mp_kernels.cuh"
+
+#include "mp_constitutive.cuh"
+#include "mp_fft.cuh"
+#include "mp_green.cuh"
+
+namespace mp {
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ float shfl_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double shfl_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double shfl_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class R>
+__device__ __forceinline__ R signed_freq_scale(int k, int n, R two_pi_over_L) {
+  const int s = (k <= n / 2) ? k : k - n;
+  return two_pi_over_L * (R)s;
+}
+
+// ------------------------------------------------------------------ y pass
+// One tile = one (kz, kx) column: 18 lines of length N2.
+template <class R, int DIR>
+__global__ void __launch_bounds__(256) k_fft_y(CellDev<R> c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem_raw);
+  const int N = c.n2;
+  const int ls = N + 1;
+  cpx<R>* b1 = b0 + 18 * ls;
+  const long long ntiles = (long long)c.n3 * c.kx;
+  const long long rowstride = (long long)c.kx * 18;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int kz = (int)(tile / c.kx);
+    const int kx = (int)(tile - (long long)kz * c.kx);
+    cpx<R>* g = c.spec + ((long long)kz * N * c.kx + kx) * 18;
+    for (int i = threadIdx.x; i < N * 18; i += blockDim.x) {
+      const int ky = i / 18, comp = i - ky * 18;
+      b0[comp * ls + ky] = g[ky * rowstride + comp];
+    }
+    __syncthreads();
+    cpx<R>* r = line_fft<R, DIR>(b0, b1, 18, ls, c.py);
+    for (int i = threadIdx.x; i < N * 18; i += blockDim.x) {
+      const int ky = i / 18, comp = i - ky * 18;
+      g[ky * rowstride + comp] = r[comp * ls + ky];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ z pass + Green
+// One tile = one (ky, kx) column: 18 lines of length N3.
+template <class R>
+__global__ void __launch_bounds__(256) k_green_z(CellDev<R> c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem_raw);
+  const int N = c.n3;
+  const int ls = N + 1;
+  cpx<R>* b1 = b0 + 18 * ls;
+  const long long ntiles = (long long)c.n2 * c.kx;
+  const long long zstride = (long long)c.n2 * c.kx * 18;
+  const R scale = (R)c.inv_nvox;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int ky = (int)(tile / c.kx);
+    const int kx = (int)(tile - (long long)ky * c.kx);
+    cpx<R>* g = c.spec + ((long long)ky * c.kx + kx) * 18;
+    const bool ny_nyq = (c.n2 % 2 == 0) && (ky == c.n2 / 2);
+    if (ny_nyq) {
+      for (int i = threadIdx.x; i < N * 18; i += blockDim.x) {
+        const int kz = i / 18, comp = i - kz * 18;
+        g[kz * zstride + comp] = cmake<R>(R(0), R(0));
+      }
+      continue;  // uniform across the block: no barrier divergence
+    }
+    for (int i = threadIdx.x; i < N * 18; i += blockDim.x) {
+      const int kz = i / 18, comp = i - kz * 18;
+      b0[comp * ls + kz] = g[kz * zstride + comp];
+    }
+    __syncthreads();
+    cpx<R>* r = line_fft<R, -1>(b0, b1, 18, ls, c.pz);
+    const R x1 = c.n1 == 1 ? R(0) : c.two_pi_over_L[0] * (R)kx;
+    const R x2 = signed_freq_scale<R>(ky, c.n2, c.two_pi_over_L[1]);
+    for (int kz = threadIdx.x; kz < N; kz += blockDim.x) {
+      cpx<R> v[18];
+#pragma unroll
+      for (int q = 0; q < 18; ++q) v[q] = r[q * ls + kz];
+      const bool nz_nyq = (N % 2 == 0) && (kz == N / 2);
+      const bool zero = (kx == 0 && ky == 0 && kz == 0);
+      if (nz_nyq || zero) {
+#pragma unroll
+        for (int q = 0; q < 18; ++q) v[q] = cmake<R>(R(0), R(0));
+      } else {
+        const R x3 = signed_freq_scale<R>(kz, N, c.two_pi_over_L[2]);
+        green_point<R>(c.ref, x1, x2, x3, v, scale);
+      }
+#pragma unroll
+      for (int q = 0; q < 18; ++q) r[q * ls + kz] = v[q];
+    }
+    __syncthreads();
+    cpx<R>* other = (r == b0) ? b1 : b0;
+    cpx<R>* o = line_fft<R, +1>(r, other, 18, ls, c.pz);
+    for (int i = threadIdx.x; i < N * 18; i += blockDim.x) {
+      const int kz = i / 18, comp = i - kz * 18;
+      g[kz * zstride + comp] = o[comp * ls + kz];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ x pass (pass A)
+// Packed real transform of a row of N1 reals through a complex transform of
+// length M = N1 / 2: z[n] = x[2n] + i x[2n+1].
+//   forward:  X[k] = (Z[k] + conj Z[M-k]) / 2 - (i / 2) W_N1^k (Z[k] - conj Z[M-k])
+//   inverse:  Z[k] = (X[k] + conj X[M-k]) + i W_N1^-k (X[k] - conj X[M-k]),  X[M] = 0
+// (X[M] is the Nyquist bin, which the Green operator sets to zero; X[0] is
+// real for a real row and its imaginary part is ignored).
+
+template <class R>
+__device__ __forceinline__ void x_inverse_pre(const cpx<R>* X, cpx<R>* Z, int rows, int ls, int M,
+                                              const cpx<R>* tw) {
+  for (int idx = threadIdx.x; idx < rows * M; idx += blockDim.x) {
+    const int line = idx / M, k = idx - line * M;
+    const cpx<R>* x = X + line * ls;
+    cpx<R> a = x[k];
+    if (k == 0) a.y = R(0);
+    const cpx<R> b = (k == 0) ? cmake<R>(R(0), R(0)) : cconj(x[M - k]);
+    cpx<R> w = tw[k];
+    w.y = -w.y;  // W_N^-k
+    Z[line * ls + k] = cadd(cadd(a, b), cmuli(cmul(w, csub(a, b))));
+  }
+}
+
+template <class R>
+__device__ __forceinline__ void x_forward_post(const cpx<R>* Z, cpx<R>* X, int rows, int ls, int M,
+                                               const cpx<R>* tw) {
+  for (int idx = threadIdx.x; idx < rows * M; idx += blockDim.x) {
+    const int line = idx / M, k = idx - line * M;
+    const cpx<R>* z = Z + line * ls;
+    cpx<R> a = z[k];
+    cpx<R> b = cconj(z[k == 0 ? 0 : M - k]);
+    cpx<R> s = cadd(a, b), d = csub(a, b);
+    cpx<R> wd = cmul(tw[k], d);
+    // (s - i wd) / 2
+    X[line * ls + k] = cmake<R>(R(0.5) * (s.x + wd.y), R(0.5) * (s.y - wd.x));
+  }
+}
+
+enum PassMode { kIter = 0, kStart = 1, kXFwd = 2, kXInv = 3 };
+
+// Work item = `rows` consecutive rows (y, z) of the cell.
+template <class R, int MODE>
+__global__ void __launch_bounds__(256) k_pass_a(CellDev<R> c, int rows, double* partials,
+                                                const R* fin_tau, const R* fin_mu, R* fout_e,
+                                                R* fout_g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N1 = c.n1;
+  const int M = c.kx;                 // complex entries per row (N1 / 2, or 1)
+  const bool packed = (N1 > 1);
+  const int ls = (M > 2) ? M + 1 : M;  // padded line stride
+  const int nlines = 18 * rows;
+  cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* b1 = b0 + nlines * ls;
+  double* red = reinterpret_cast<double*>(b1 + nlines * ls);  // [8 warps][8]
+  double* acc = red + 64;                                       // [kErrPartials] CTA total
+  R* dcin = reinterpret_cast<R*>(acc + kErrPartials);            // [18 * rows] incoming row DC
+  if (MODE == kIter) {
+    for (int i = threadIdx.x; i < kErrPartials; i += blockDim.x) acc[i] = 0.0;
+  }
+  const long long nrows = (long long)c.n2 * c.n3;
+  const long long nitems = (nrows + rows - 1) / rows;
+  const int nwarp = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const long long row0 = item * rows;
+    const int nr = (int)min((long long)rows, nrows - row0);
+    cpx<R>* zbuf;  // buffer holding the packed real rows
+    // ---------------------------------------------------------- inverse x
+    if (MODE == kIter || MODE == kXInv) {
+      for (int i = threadIdx.x; i < nr * M * 18; i += blockDim.x) {
+        const int rr = i / (M * 18);
+        const int rem = i - rr * M * 18;
+        const int k = rem / 18, comp = rem - k * 18;
+        b0[(comp * rows + rr) * ls + k] = c.spec[((row0 + rr) * M + k) * 18 + comp];
+      }
+      __syncthreads();
+      if (MODE == kIter) {
+        for (int l = threadIdx.x; l < nlines; l += blockDim.x) dcin[l] = b0[l * ls].x;
+      }
+      if (packed) {
+        // all 18 * rows lines are transformed; lines of rows >= nr are never stored
+        x_inverse_pre<R>(b0, b1, nlines, ls, M, c.px.tw);
+        __syncthreads();
+        // lines are indexed comp * rows + rr; transform all 18 * rows lines
+        zbuf = line_fft<R, +1>(b1, b0, nlines, ls, c.px);
+      } else {
+        zbuf = b0;
+      }
+    } else {
+      zbuf = b0;
+    }
+    // ---------------------------------------------------------- per voxel
+    R dmax[4] = {R(0), R(0), R(0), R(0)};
+    R dsum[4] = {R(0), R(0), R(0), R(0)};
+    for (int lv = threadIdx.x; lv < nr * N1; lv += blockDim.x) {
+      const int rr = lv / N1, x = lv - rr * N1;
+      const long long v = (row0 + rr) * N1 + x;
+      R val[18];
+      if (MODE == kIter || MODE == kXInv) {
+#pragma unroll
+        for (int q = 0; q < 18; ++q) {
+          const cpx<R> z = zbuf[(q * rows + rr) * ls + (packed ? (x >> 1) : 0)];
+          val[q] = packed ? ((x & 1) ? z.y : z.x) : z.x;
+        }
+      }
+      if (MODE == kXInv) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          fout_e[v * 9 + q] = val[q];
+          fout_g[v * 9 + q] = val[9 + q];
+        }
+        continue;
+      }
+      R out[18];
+      if (MODE == kXFwd) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          out[q] = fin_tau[v * 9 + q];
+          out[9 + q] = fin_mu[v * 9 + q];
+        }
+      } else {
+        R e[9], gm[9];
+        const R* pv = c.prev + v * 20;
+        if (MODE == kIter) {
+#pragma unroll
+          for (int q = 0; q < 9; ++q) {
+            e[q] = c.E[q] + val[q];
+            gm[q] = c.G[q] + val[9 + q];
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 9; ++q) {
+            e[q] = pv[q];
+            gm[q] = pv[9 + q];
+          }
+        }
+        const PhaseDev<R> P = c.phases[c.phase[v]];
+        R ht[9], hm[9];
+        const R* hv = c.hist + v * 18;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          ht[q] = hv[q];
+          hm[q] = hv[9 + q];
+        }
+        const double2 pq = reinterpret_cast<const double2*>(c.pq)[v];
+        R t[9], m[9];
+        double p, qq;
+        R ft, fm;
+        radial_return<R>(P, e, gm, ht, hm, pq.x, pq.y, t, m, p, qq, ft, fm);
+        if (MODE == kIter) {
+          // previous iterate: e, gamma stored, t, m rebuilt from the stored scale factors
+          R eo[9], go[9], to[9], mo[9];
+#pragma unroll
+          for (int q = 0; q < 9; ++q) {
+            eo[q] = pv[q];
+            go[q] = pv[9 + q];
+          }
+          const R fto = pv[18], fmo = pv[19];
+          trial<R>(P, eo, go, ht, hm, to, mo);
+          assemble<R>(to, mo, fto, fmo);
+          R de = R(0), dt = R(0), dg = R(0), dm = R(0);
+#pragma unroll
+          for (int q = 0; q < 9; ++q) {
+            const R a = e[q] - eo[q], b = t[q] - to[q], cc = gm[q] - go[q], d = m[q] - mo[q];
+            de += a * a; dt += b * b; dg += cc * cc; dm += d * d;
+          }
+          de = sqrt(de); dt = sqrt(dt); dg = sqrt(dg); dm = sqrt(dm);
+          dmax[0] = max(dmax[0], de); dmax[1] = max(dmax[1], dt);
+          dmax[2] = max(dmax[2], dg); dmax[3] = max(dmax[3], dm);
+          dsum[0] += de; dsum[1] += dt; dsum[2] += dg; dsum[3] += dm;
+        }
+        // store the new iterate (e, gamma, f_t, f_m)
+        R* pw = c.prev + v * 20;
+        if (MODE == kIter) {
+#pragma unroll
+          for (int q = 0; q < 9; ++q) {
+            pw[q] = e[q];
+            pw[9 + q] = gm[q];
+          }
+        }
+        pw[18] = ft;
+        pw[19] = fm;
+        // polarizations (eq. micropolar_polarizatons): tau = t - A0 e, mu = m - B0 gamma
+        R ae[9], bg[9];
+        apply_A<R>(c.ref.lam, c.ref.mu, c.ref.kap, e, ae);
+        apply_B<R>(c.ref.alpha, c.ref.beta, c.ref.gamma, gm, bg);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          out[q] = t[q] - ae[q];
+          out[9 + q] = m[q] - bg[q];
+        }
+      }
+      // write back into the packed row
+#pragma unroll
+      for (int q = 0; q < 18; ++q) {
+        cpx<R>* z = &zbuf[(q * rows + rr) * ls + (packed ? (x >> 1) : 0)];
+        if (!packed) {
+          *z = cmake<R>(out[q], R(0));
+        } else if (x & 1) {
+          z->y = out[q];
+        } else {
+          z->x = out[q];
+        }
+      }
+    }
+    __syncthreads();
+    if (MODE == kXInv) continue;
+    // ---------------------------------------------------------- forward x
+    cpx<R>* X;
+    if (packed) {
+      cpx<R>* other = (zbuf == b0) ? b1 : b0;
+      cpx<R>* Z = line_fft<R, -1>(zbuf, other, nlines, ls, c.px);
+      cpx<R>* dst = (Z == b0) ? b1 : b0;
+      x_forward_post<R>(Z, dst, nlines, ls, M, c.px.tw);
+      __syncthreads();
+      X = dst;
+    } else {
+      X = zbuf;
+    }
+    for (int i = threadIdx.x; i < nr * M * 18; i += blockDim.x) {
+      const int rr = i / (M * 18);
+      const int rem = i - rr * M * 18;
+      const int k = rem / 18, comp = rem - k * 18;
+      c.spec[((row0 + rr) * M + k) * 18 + comp] = X[(comp * rows + rr) * ls + k];
+    }
+    // ---------------------------------------------------------- error partials
+    if (MODE == kIter) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const double mx = shfl_max((double)dmax[a]);
+        const double sm = shfl_sum((double)dsum[a]);
+        if (lane == 0) {
+          red[warp * 8 + a] = mx;
+          red[warp * 8 + 4 + a] = sm;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x < 8) {
+        double a = acc[threadIdx.x];
+        for (int w = 0; w < nwarp; ++w) {
+          const double vv = red[w * 8 + threadIdx.x];
+          a = (threadIdx.x < 4) ? fmax(a, vv) : a + vv;
+        }
+        acc[threadIdx.x] = a;
+      } else if (threadIdx.x >= 32 && threadIdx.x < 32 + 36) {
+        // Row sums.  With the unnormalised inverse along x, sum_x e~ = N1 X_in[0],
+        // so sum_x e = N1 (E + X_in[0]); the forward DC is sum_x tau.
+        const int q = threadIdx.x - 32;
+        double a = 0.0;
+        if (q < 18) {
+          const double mean = (q < 9) ? (double)c.E[q] : (double)c.G[q - 9];
+          for (int rr = 0; rr < nr; ++rr) a += (double)N1 * (mean + (double)dcin[q * rows + rr]);
+        } else {
+          for (int rr = 0; rr < nr; ++rr) a += (double)X[((q - 18) * rows + rr) * ls].x;
+        }
+        acc[8 + q] += a;  // each of these threads owns one entry of the CTA total
+      }
+    }
+    __syncthreads();
+  }
+  if (MODE == kIter) {
+    for (int i = threadIdx.x; i < kErrPartials; i += blockDim.x)
+      partials[(long long)blockIdx.x * kErrPartials + i] = acc[i];
+  }
+}
+
+// ------------------------------------------------------------------ iteration error
+// eq. err with eq. err_local (max) or eq. err_average (mean).  Denominators
+// ||<a>|| are floored by their dimensional partner through the voxel size h
+// (den_e >= h |<gamma>|, den_gamma >= |<e>| / h, den_t >= |<m>| / h,
+// den_m >= h |<t>|), since ||<gamma>|| = 0 whenever the mean curvature is zero.
+// out[0] = err, out[1..4] = err_e, err_t, err_gamma, err_m.
+template <class R>
+__global__ void k_reduce_err(CellDev<R> c, const double* partials, int nparts, int err_kind,
+                             double* out) {
+  __shared__ double s[kErrPartials];
+  if (threadIdx.x < kErrPartials) {
+    const int q = threadIdx.x;
+    double a = 0.0;
+    for (int b = 0; b < nparts; ++b) {
+      const double v = partials[(long long)b * kErrPartials + q];
+      a = (q < 4) ? fmax(a, v) : a + v;
+    }
+    s[q] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double iv = c.inv_nvox;
+    double me[9], mg[9], mt[9], mm[9];
+    for (int q = 0; q < 9; ++q) {
+      me[q] = s[8 + q] * iv;
+      mg[q] = s[17 + q] * iv;
+    }
+    // <t> = <tau> + A0 <e>, <m> = <mu> + B0 <gamma>  (linearity of the polarization)
+    const double lam = c.ref.lam, mu = c.ref.mu, kap = c.ref.kap;
+    const double al = c.ref.alpha, be = c.ref.beta, ga = c.ref.gamma;
+    const double tre = me[0] + me[4] + me[8], trg = mg[0] + mg[4] + mg[8];
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l) {
+        mt[3 * k + l] = s[26 + 3 * k + l] * iv + (mu + kap) * me[3 * k + l] + (mu - kap) * me[3 * l + k] +
+                        (k == l ? lam * tre : 0.0);
+        mm[3 * k + l] = s[35 + 3 * k + l] * iv + be * mg[3 * k + l] + ga * mg[3 * l + k] +
+                        (k == l ? al * trg : 0.0);
+      }
+    double ne = 0, ng = 0, nt = 0, nm = 0;
+    for (int q = 0; q < 9; ++q) {
+      ne += me[q] * me[q]; ng += mg[q] * mg[q]; nt += mt[q] * mt[q]; nm += mm[q] * mm[q];
+    }
+    ne = sqrt(ne); ng = sqrt(ng); nt = sqrt(nt); nm = sqrt(nm);
+    const double h = c.h;
+    const double den[4] = {fmax(ne, h * ng), fmax(nt, nm / h), fmax(ng, ne / h), fmax(nm, h * nt)};
+    double err = 0.0;
+    for (int a = 0; a < 4; ++a) {
+      const double num = (err_kind == 0) ? s[a] : s[4 + a] * iv;
+      double ea;
+      if (den[a] == 0.0) ea = (num == 0.0) ? 0.0 : INFINITY;
+      else ea = num / den[a];
+      if (!(ea <= err)) err = ea;  // propagates NaN
+      out[1 + a] = ea;
+    }
+    out[0] = err;
+  }
+}
+
+// ------------------------------------------------------------------ state set-up
+// Zero initial state (Algorithm 2 initialisation) and the first predictor
+// e = E, gamma = Gamma of the first load increment.
+template <class R>
+__global__ void k_init(CellDev<R> c) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < c.nvox;
+       v += (long long)gridDim.x * blockDim.x) {
+    R* pv = c.prev + v * 20;
+    R* hv = c.hist + v * 18;
+    R* el = c.elast + v * 18;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      pv[q] = c.E[q];
+      pv[9 + q] = c.G[q];
+    }
+    pv[18] = R(1);
+    pv[19] = R(1);
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+      hv[q] = R(0);
+      el[q] = R(0);
+    }
+    reinterpret_cast<double2*>(c.pq)[v] = make_double2(0.0, 0.0);
+  }
+}
+
+// ------------------------------------------------------------------ commit
+// Algorithm 2, end of a load increment: the converged iterate becomes the
+// history of Algorithm 1; homogenized sums; optional linear-extrapolation
+// predictor of the next increment, e' = e_n + ratio (e_n - e_{n-1}).
+// partials[block][40]: sums of t (9), m (9), e (9), gamma (9), p, q, t_eq, m_eq.
+template <class R>
+__global__ void __launch_bounds__(256) k_commit(CellDev<R> c, int predict, R ratio,
+                                                double* partials) {
+  double acc[kAvgPartials];
+#pragma unroll
+  for (int i = 0; i < kAvgPartials; ++i) acc[i] = 0.0;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < c.nvox;
+       v += (long long)gridDim.x * blockDim.x) {
+    R* pv = c.prev + v * 20;
+    R* hv = c.hist + v * 18;
+    R e[9], g[9], ht[9], hm[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      e[q] = pv[q];
+      g[q] = pv[9 + q];
+      ht[q] = hv[q];
+      hm[q] = hv[9 + q];
+    }
+    const PhaseDev<R> P = c.phases[c.phase[v]];
+    double2 pq = reinterpret_cast<const double2*>(c.pq)[v];
+    R t[9], m[9];
+    double p, q;
+    R ft, fm;
+    radial_return<R>(P, e, g, ht, hm, pq.x, pq.y, t, m, p, q, ft, fm);
+    R ae[9], bg[9];
+    apply_A<R>(P.lam, P.mu, P.kap, e, ae);
+    apply_B<R>(P.alpha, P.beta, P.gamma, g, bg);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      hv[i] = t[i] - ae[i];
+      hv[9 + i] = m[i] - bg[i];
+      acc[i] += (double)t[i];
+      acc[9 + i] += (double)m[i];
+      acc[18 + i] += (double)e[i];
+      acc[27 + i] += (double)g[i];
+    }
+    reinterpret_cast<double2*>(c.pq)[v] = make_double2(p, q);
+    double teq, meq;
+    equivalents<R>(P, t, m, teq, meq);
+    acc[36] += p;
+    acc[37] += q;
+    acc[38] += teq;
+    acc[39] += meq;
+    if (predict) {
+      R* el = c.elast + v * 18;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const R eo = el[i], go = el[9 + i];
+        el[i] = e[i];
+        el[9 + i] = g[i];
+        pv[i] = e[i] + ratio * (e[i] - eo);
+        pv[9 + i] = g[i] + ratio * (g[i] - go);
+      }
+    }
+  }
+  __shared__ double red[8][kAvgPartials];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < kAvgPartials; ++i) {
+    const double s = shfl_sum(acc[i]);
+    if (lane == 0) red[warp][i] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < kAvgPartials) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+    partials[(long long)blockIdx.x * kAvgPartials + threadIdx.x] = s;
+  }
+}
+
+// Sum of the commit partials in a fixed order, divided by the voxel count.
+__global__ void k_reduce_avg(const double* partials, int nparts, double inv_nvox, double* out) {
+  if (threadIdx.x < kAvgPartials) {
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += partials[(long long)b * kAvgPartials + threadIdx.x];
+    out[threadIdx.x] = s * inv_nvox;
+  }
+}
+
+// Final-state fields in FP64: e, gamma from `src` (prev or elast), t = h_t + A e,
+// m = h_m + B gamma (the history form of the converged stresses), p, q.
+template <class R>
+__global__ void k_fields(CellDev<R> c, const R* src, int src_stride, double* fe, double* fg,
+                         double* ft, double* fm, double* fp, double* fq) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < c.nvox;
+       v += (long long)gridDim.x * blockDim.x) {
+    const R* s = src + v * src_stride;
+    const R* hv = c.hist + v * 18;
+    R e[9], g[9], t[9], m[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      e[q] = s[q];
+      g[q] = s[9 + q];
+    }
+    const PhaseDev<R> P = c.phases[c.phase[v]];
+    apply_A<R>(P.lam, P.mu, P.kap, e, t);
+    apply_B<R>(P.alpha, P.beta, P.gamma, g, m);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      if (fe) fe[v * 9 + q] = (double)e[q];
+      if (fg) fg[v * 9 + q] = (double)g[q];
+      if (ft) ft[v * 9 + q] = (double)(hv[q] + t[q]);
+      if (fm) fm[v * 9 + q] = (double)(hv[9 + q] + m[q]);
+    }
+    if (fp) fp[v] = c.pq[2 * v];
+    if (fq) fq[v] = c.pq[2 * v + 1];
+  }
+}
+
+// ------------------------------------------------------------------ component: Algorithm 1
+template <class R>
+__global__ void __launch_bounds__(256) k_radial_return_points(
+    long long count, const uint16_t* phase, const PhaseDev<R>* phases, const R* e, const R* g,
+    const R* e_n, const R* g_n, const R* t_n, const R* m_n, const double* p_n, const double* q_n,
+    R* t, R* m, double* p, double* q) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const PhaseDev<R> P = phases[phase[i]];
+    R ee[9], gg[9], en[9], gn[9], ht[9], hm[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      ee[k] = e[i * 9 + k];
+      gg[k] = g[i * 9 + k];
+      en[k] = e_n[i * 9 + k];
+      gn[k] = g_n[i * 9 + k];
+    }
+    // history form of eq. trial_stresses: h_t = t_n - A e_n, h_m = m_n - B gamma_n
+    apply_A<R>(P.lam, P.mu, P.kap, en, ht);
+    apply_B<R>(P.alpha, P.beta, P.gamma, gn, hm);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      ht[k] = t_n[i * 9 + k] - ht[k];
+      hm[k] = m_n[i * 9 + k] - hm[k];
+    }
+    R tt[9], mm[9];
+    double pp, qq;
+    R ft, fm;
+    radial_return<R>(P, ee, gg, ht, hm, p_n[i], q_n[i], tt, mm, pp, qq, ft, fm);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      t[i * 9 + k] = tt[k];
+      m[i * 9 + k] = mm[k];
+    }
+    p[i] = pp;
+    q[i] = qq;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <class R>
+size_t smem_line_pass(int n) { return 2ull * 18 * (size_t)(n + 1) * sizeof(cpx<R>); }
+
+template <class R>
+size_t smem_pass_a(int n1, int rows) {
+  const int M = (n1 > 1) ? n1 / 2 : 1;
+  const int ls = (M > 2) ? M + 1 : M;
+  return 2ull * 18 * rows * ls * sizeof(cpx<R>) + (64 + kErrPartials) * sizeof(double) +
+         18ull * rows * sizeof(R);
+}
+
+template <class R>
+static cudaError_t set_smem_attrs() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  const int maxs = 227 * 1024;
+  cudaError_t e = cudaSuccess;
+#define MP_ATTR(k) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs)
+  MP_ATTR((k_fft_y<R, -1>));
+  MP_ATTR((k_fft_y<R, +1>));
+  MP_ATTR((k_green_z<R>));
+  MP_ATTR((k_pass_a<R, kIter>));
+  MP_ATTR((k_pass_a<R, kStart>));
+  MP_ATTR((k_pass_a<R, kXFwd>));
+  MP_ATTR((k_pass_a<R, kXInv>));
+#undef MP_ATTR
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <class R>
+int grid_for(const void* fn, int threads, size_t smem, long long work, int nsm) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  long long g = (long long)per_sm * nsm;
+  if (work < g) g = work;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <class R>
+cudaError_t launch_fft_y(const LaunchCfg& L, const CellDev<R>& c, int dir, cudaStream_t st) {
+  cudaError_t e = set_smem_attrs<R>();
+  if (e != cudaSuccess) return e;
+  if (c.n2 > 1) {
+    if (dir < 0) k_fft_y<R, -1><<<L.grid_y, 256, smem_line_pass<R>(c.n2), st>>>(c);
+    else k_fft_y<R, +1><<<L.grid_y, 256, smem_line_pass<R>(c.n2), st>>>(c);
+  }
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_green_z(const LaunchCfg& L, const CellDev<R>& c, cudaStream_t st) {
+  cudaError_t e = set_smem_attrs<R>();
+  if (e != cudaSuccess) return e;
+  k_green_z<R><<<L.grid_z, 256, smem_line_pass<R>(c.n3), st>>>(c);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_pass_a_iter(const LaunchCfg& L, const CellDev<R>& c, double* partials,
+                               cudaStream_t st) {
+  cudaError_t e = set_smem_attrs<R>();
+  if (e != cudaSuccess) return e;
+  k_pass_a<R, kIter><<<L.grid_a, 256, smem_pass_a<R>(c.n1, L.rows), st>>>(c, L.rows, partials, nullptr,
+                                                                           nullptr, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_reduce_err(const LaunchCfg& L, const CellDev<R>& c, const double* partials,
+                              int err_kind, double* err_out, cudaStream_t st) {
+  k_reduce_err<R><<<1, 64, 0, st>>>(c, partials, L.grid_a, err_kind, err_out);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_iteration(const LaunchCfg& L, const CellDev<R>& c, double* partials,
+                             double* err_out, int err_kind, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = launch_fft_y<R>(L, c, -1, st)) != cudaSuccess) return e;
+  if ((e = launch_green_z<R>(L, c, st)) != cudaSuccess) return e;
+  if ((e = launch_fft_y<R>(L, c, +1, st)) != cudaSuccess) return e;
+  if ((e = launch_pass_a_iter<R>(L, c, partials, st)) != cudaSuccess) return e;
+  return launch_reduce_err<R>(L, c, partials, err_kind, err_out, st);
+}
+
+template <class R>
+cudaError_t launch_start(const LaunchCfg& L, const CellDev<R>& c, int first, cudaStream_t st) {
+  cudaError_t e = set_smem_attrs<R>();
+  if (e != cudaSuccess) return e;
+  if (first) k_init<R><<<L.grid_v, 256, 0, st>>>(c);
+  k_pass_a<R, kStart><<<L.grid_a, 256, smem_pass_a<R>(c.n1, L.rows), st>>>(c, L.rows, nullptr, nullptr,
+                                                                            nullptr, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_commit(const LaunchCfg& L, const CellDev<R>& c, int predict, double ratio,
+                          double* partials, double* avg_out, cudaStream_t st) {
+  k_commit<R><<<L.grid_v, 256, 0, st>>>(c, predict, (R)ratio, partials);
+  k_reduce_avg<<<1, 64, 0, st>>>(partials, L.grid_v, c.inv_nvox, avg_out);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_fields(const LaunchCfg& L, const CellDev<R>& c, int from_elast, double* fe,
+                          double* fg, double* ft, double* fm, double* fp, double* fq, cudaStream_t st) {
+  const R* src = from_elast ? c.elast : c.prev;
+  const int stride = from_elast ? 18 : 20;
+  k_fields<R><<<L.grid_v, 256, 0, st>>>(c, src, stride, fe, fg, ft, fm, fp, fq);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_green_apply(const LaunchCfg& L, const CellDev<R>& c, const R* tau, const R* mu,
+                               R* e_out, R* g_out, cudaStream_t st) {
+  cudaError_t e = set_smem_attrs<R>();
+  if (e != cudaSuccess) return e;
+  const size_t sa = smem_pass_a<R>(c.n1, L.rows);
+  k_pass_a<R, kXFwd><<<L.grid_a, 256, sa, st>>>(c, L.rows, nullptr, tau, mu, nullptr, nullptr);
+  if (c.n2 > 1) k_fft_y<R, -1><<<L.grid_y, 256, smem_line_pass<R>(c.n2), st>>>(c);
+  k_green_z<R><<<L.grid_z, 256, smem_line_pass<R>(c.n3), st>>>(c);
+  if (c.n2 > 1) k_fft_y<R, +1><<<L.grid_y, 256, smem_line_pass<R>(c.n2), st>>>(c);
+  k_pass_a<R, kXInv><<<L.grid_a, 256, sa, st>>>(c, L.rows, nullptr, nullptr, nullptr, e_out, g_out);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_radial_return(int nsm, long long count, const uint16_t* phase,
+                                 const PhaseDev<R>* phases, const R* e, const R* g, const R* e_n,
+                                 const R* g_n, const R* t_n, const R* m_n, const double* p_n,
+                                 const double* q_n, R* t, R* m, double* p, double* q,
+                                 cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  long long blocks = (count + 255) / 256;
+  if (blocks > 8ll * nsm) blocks = 8ll * nsm;
+  k_radial_return_points<R><<<(int)blocks, 256, 0, st>>>(count, phase, phases, e, g, e_n, g_n, t_n, m_n,
+                                                          p_n, q_n, t, m, p, q);
+  return cudaGetLastError();
+}
+
+template <class R>
+LaunchCfg make_launch_cfg(const CellDev<R>& c, int nsm) {
+  set_smem_attrs<R>();
+  LaunchCfg L;
+  // rows per pass-A item: ~256 voxels per block
+  int rows = c.n1 >= 256 ? 1 : 256 / c.n1;
+  if (c.n1 <= 2 && sizeof(R) == 8) rows = 128;
+  if ((long long)rows > (long long)c.n2 * c.n3) rows = (int)((long long)c.n2 * c.n3);
+  L.rows = rows;
+  const long long nrows = (long long)c.n2 * c.n3;
+  const long long items = (nrows + rows - 1) / rows;
+  L.grid_a = grid_for<R>((const void*)k_pass_a<R, kIter>, 256, smem_pass_a<R>(c.n1, rows), items, nsm);
+  L.grid_y = grid_for<R>((const void*)k_fft_y<R, -1>, 256, smem_line_pass<R>(c.n2),
+                         (long long)c.n3 * c.kx, nsm);
+  L.grid_z = grid_for<R>((const void*)k_green_z<R>, 256, smem_line_pass<R>(c.n3),
+                         (long long)c.n2 * c.kx, nsm);
+  long long vb = (c.nvox + 255) / 256;
+  L.grid_v = (int)(vb < 4ll * nsm ? vb : 4ll * nsm);
+  return L;
+}
+
+#define MP_INSTANTIATE(R)                                                                            \
+  template cudaError_t launch_fft_y<R>(const LaunchCfg&, const CellDev<R>&, int, cudaStream_t);       \
+  template cudaError_t launch_green_z<R>(const LaunchCfg&, const CellDev<R>&, cudaStream_t);          \
+  template cudaError_t launch_pass_a_iter<R>(const LaunchCfg&, const CellDev<R>&, double*, cudaStream_t); \
+  template cudaError_t launch_reduce_err<R>(const LaunchCfg&, const CellDev<R>&, const double*, int,  \
+                                            double*, cudaStream_t);                                  \
+  template cudaError_t launch_iteration<R>(const LaunchCfg&, const CellDev<R>&, double*, double*, int, \
+                                           cudaStream_t);                                            \
+  template cudaError_t launch_start<R>(const LaunchCfg&, const CellDev<R>&, int, cudaStream_t);       \
+  template cudaError_t launch_commit<R>(const LaunchCfg&, const CellDev<R>&, int, double, double*,    \
+                                        double*, cudaStream_t);                                      \
+  template cudaError_t launch_fields<R>(const LaunchCfg&, const CellDev<R>&, int, double*, double*,   \
+                                        double*, double*, double*, double*, cudaStream_t);           \
+  template cudaError_t launch_green_apply<R>(const LaunchCfg&, const CellDev<R>&, const R*, const R*,  \
+                                             R*, R*, cudaStream_t);                                  \
+  template cudaError_t launch_radial_return<R>(int, long long, const uint16_t*, const PhaseDev<R>*,   \
+                                               const R*, const R*, const R*, const R*, const R*,      \
+                                               const R*, const double*, const double*, R*, R*,        \
+                                               double*, double*, cudaStream_t);                       \
+  template LaunchCfg make_launch_cfg<R>(const CellDev<R>&, int);
+
+MP_INSTANTIATE(float)
+MP_INSTANTIATE(double)
+
+}  // namespace mp

@@ -1,0 +1,248 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (from the arithmetic):
+* FP64 path: radial return and Green operator agree with the oracle to a few
+  ulps of the data (<= 1e-12 relative); whole solves run in lockstep (same
+  per-step iteration counts as the oracle) agree to <= 1e-11 relative.
+* FP32-mixed path: single-precision fields and FFTs give ~1e-7 relative
+  rounding per operation; the component kernels must agree to <= 2e-6
+  relative, whole solves to <= 1e-5 relative L2 in the fields and <= 1e-6
+  relative in the homogenized stress.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import constitutive as OC
+from oracle import fft as OF
+from oracle import solver as OS
+from oracle.green import GreenOperator, wavevectors
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2409_10774_gb300 as M
+    return M.Context(0)
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+PHASES = W.phase_record([
+    {"lambda": 20.0, "mu": 12.0, "kappa": 3.0, "alpha": 0.0, "beta": 0.6, "gamma": 1.5,
+     "tY": 0.05, "tH": 1.0, "mY": 0.04, "mH": 0.7, "a1": 1.5, "b1": 1.5},
+    {"lambda": 8.0, "mu": 5.0, "kappa": 2.5, "alpha": 0.9, "beta": 0.2, "gamma": 2.0,
+     "tY": 0.03, "tH": 0.0, "mY": 0.02, "mH": 0.0, "a1": 1.2, "b1": 0.8},
+    {"lambda": 20.0, "mu": 12.0, "kappa": 3.0, "alpha": 1.5, "beta": 1.5, "gamma": 1.5,
+     "tY": 0.05, "tH": 1.0, "mY": 0.05, "mH": 1.0, "a1": 1.5, "b1": 1.5},
+    {"lambda": 60.0, "mu": 40.0, "kappa": 10.0, "alpha": 5.0, "beta": 5.0, "gamma": 5.0,
+     "tY": 0.0, "tH": 0.0, "mY": 0.0, "mH": 0.0, "a1": 1.5, "b1": 1.5, "elastic": 1},
+])
+
+
+def _material_batch(count, seed):
+    rng = np.random.default_rng(seed)
+    pid = rng.integers(0, len(PHASES), count).astype(np.uint16)
+    s = W.random_material_states(count, seed, strain_scale=0.002, history_scale=0.02, p_scale=0.01)
+    f = 10.0 ** rng.uniform(-1.2, 0.3, count)
+    for k in ("e", "g", "e_n", "g_n", "t_n", "m_n"):
+        s[k] = s[k] * f[:, None, None]
+    # admissible history where gamma == beta: symmetric couple stress
+    sym = PHASES["gamma"][pid] == PHASES["beta"][pid]
+    s["m_n"][sym] = OC.sym(s["m_n"][sym])
+    return pid, s
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_radial_return_matches_oracle(ctx, precision):
+    import paper_2409_10774_gb300 as M
+    count = 5000 + 37  # ragged against the 256-thread blocks
+    pid, s = _material_batch(count, 101 + precision)
+    ref = {k: np.empty_like(s[k]) for k in ("t_n", "m_n")}
+    t_ref = np.empty_like(s["e"]); m_ref = np.empty_like(s["e"])
+    p_ref = np.empty(count); q_ref = np.empty(count)
+    for k in range(len(PHASES)):
+        idx = pid == k
+        t_ref[idx], m_ref[idx], p_ref[idx], q_ref[idx] = OC.radial_return(
+            s["e"][idx], s["g"][idx], s["e_n"][idx], s["g_n"][idx], s["t_n"][idx], s["m_n"][idx],
+            s["p_n"][idx], s["q_n"][idx], PHASES[k])
+    dt = torch.float64 if precision == 0 else torch.float32
+    dev = lambda a, d=dt: torch.as_tensor(np.ascontiguousarray(a), dtype=d, device="cuda")
+    t, m, p, q = M.mp_radial_return(ctx, precision, dev(pid.astype(np.int16), torch.int16), PHASES,
+                                    dev(s["e"]), dev(s["g"]), dev(s["e_n"]), dev(s["g_n"]),
+                                    dev(s["t_n"]), dev(s["m_n"]), dev(s["p_n"], torch.float64),
+                                    dev(s["q_n"], torch.float64))
+    t, m, p, q = (x.cpu().numpy().astype(np.float64) for x in (t, m, p, q))
+    tol = 1e-12 if precision == 0 else 2e-6
+    assert _rel(t, t_ref) < tol
+    assert _rel(m, m_ref) < tol
+    # plastic increments p - p_n, q - q_n
+    assert np.abs((p - s["p_n"]) - (p_ref - s["p_n"])).max() <= tol * max(np.abs(p_ref - s["p_n"]).max(), 1e-30) + (0 if precision == 0 else 1e-9)
+    assert np.abs((q - s["q_n"]) - (q_ref - s["q_n"])).max() <= tol * max(np.abs(q_ref - s["q_n"]).max(), 1e-30) + (0 if precision == 0 else 1e-9)
+    # both branches were exercised at both levels
+    assert 0.05 < np.mean(p_ref > s["p_n"]) < 0.95 and 0.05 < np.mean(q_ref > s["q_n"]) < 0.95
+
+
+def _oracle_green(n, h, ref, tau, mu):
+    lam, mu0, kap, al, be, ga = ref
+    A0 = OC.stiffness_A(lam, mu0, kap)
+    B0 = OC.stiffness_B(al, be, ga)
+    xi, active = wavevectors(n, h)
+    e_hat, g_hat = GreenOperator(xi, active, A0, B0)(OF.fftn(tau), OF.fftn(mu))
+    return OF.ifftn(e_hat).real, OF.ifftn(g_hat).real
+
+
+@pytest.mark.parametrize("n", [(16, 16, 16), (24, 12, 8), (48, 6, 2), (1, 8, 6), (8, 1, 4),
+                               (6, 4, 1), (2, 2, 2), (1, 1, 1), (32, 18, 36)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_green_apply_matches_oracle(ctx, n, precision):
+    import paper_2409_10774_gb300 as M
+    rng = np.random.default_rng(hash(n) % 2**32)
+    shape = (n[2], n[1], n[0], 3, 3)
+    tau = rng.standard_normal(shape)
+    mu = rng.standard_normal(shape)
+    h = 0.37
+    ref = (20.0, 12.0, 3.0, 0.7, 1.1, 1.9)
+    e_ref, g_ref = _oracle_green(n, h, ref, tau, mu)
+    dt = torch.float64 if precision == 0 else torch.float32
+    e, g = M.mp_green_apply(ctx, precision, n, h, ref, torch.as_tensor(tau, dtype=dt, device="cuda"),
+                            torch.as_tensor(mu, dtype=dt, device="cuda"))
+    e = e.cpu().numpy().astype(np.float64)
+    g = g.cpu().numpy().astype(np.float64)
+    tol = 1e-12 if precision == 0 else 2e-6
+    scale_e = max(np.abs(e_ref).max(), 1e-300)
+    scale_g = max(np.abs(g_ref).max(), 1e-300)
+    if n == (1, 1, 1):
+        assert np.abs(e).max() == 0.0 and np.abs(g).max() == 0.0
+        return
+    assert np.abs(e - e_ref).max() <= tol * scale_e * 10
+    assert np.abs(g - g_ref).max() <= tol * scale_g * 10
+
+
+def _oracle_solve_cached(cache, key, problem, **kw):
+    if key not in cache:
+        cache[key] = OS.solve(problem, **kw)
+    return cache[key]
+
+
+_CACHE = {}
+
+
+def _compare_solves(res, ref, tol_hom, tol_fields=None, h=1.0):
+    """Homogenized results within tol_hom of the oracle, relative to each
+    quantity's magnitude; couple-stress quantities are measured against
+    max(|M|, h |T|) (a couple stress is a stress times a length), so that a
+    load without curvature, whose M is pure rounding, is not compared to zero."""
+    assert res["steps_done"] == len(ref["iters"])
+    scaleT = max(np.abs(ref["T"]).max(), 1e-300)
+    scaleM = max(np.abs(ref["M"]).max(), h * scaleT)
+    assert np.abs(res["T"] - ref["T"]).max() <= tol_hom * scaleT
+    assert np.abs(res["M"] - ref["M"]).max() <= tol_hom * scaleM
+    scales = {"P": np.abs(ref["P"]).max(), "Q": max(np.abs(ref["Q"]).max(), np.abs(ref["P"]).max()),
+              "Teq": np.abs(ref["Teq"]).max(), "Meq": max(np.abs(ref["Meq"]).max(), h * np.abs(ref["Teq"]).max())}
+    for k, sc in scales.items():
+        assert np.abs(res[k] - ref[k]).max() <= tol_hom * max(sc, 1e-300), k
+    scaleE = np.abs(ref["Eavg"]).max()
+    assert np.abs(res["Eavg"] - ref["Eavg"]).max() <= tol_hom * scaleE
+    if tol_fields is not None:
+        fin, rf = res["final"], ref["final"]
+        for k in ("e", "t"):
+            assert _rel_l2(fin[k], rf[k]) <= tol_fields, k
+        # curvature / couple stress against their dimensional partners
+        for k, partner, f in (("g", "e", 1.0 / h), ("m", "t", h)):
+            err = np.linalg.norm(fin[k] - rf[k])
+            den = max(np.linalg.norm(rf[k]), f * np.linalg.norm(rf[partner]))
+            assert err <= tol_fields * den, k
+
+
+def test_centered_sphere_fp64_lockstep(ctx):
+    """16^3 centred sphere (the paper-style workload of the 16^3 configuration)
+    with the midrange reference medium, FP64, lockstep with the oracle."""
+    import paper_2409_10774_gb300 as M
+    p = W.workload_centered_sphere(ref_kind="midrange")
+    ref = _oracle_solve_cached(_CACHE, "sphere16-mid", p)
+    assert ref["status"] == "ok"
+    res = M.mp_solve(ctx, p, precision=0, fields=True, lockstep_iters=ref["iters"])
+    assert res["status"] == "ok"
+    assert list(res["iters"]) == list(ref["iters"])
+    _compare_solves(res, ref, 1e-11, 1e-11)
+    # free-running FP64 stops at (nearly) the same iterations
+    free = M.mp_solve(ctx, p, precision=0)
+    assert np.abs(free["iters"] - ref["iters"]).max() <= 1
+
+
+def test_centered_sphere_mean_reference_diverges(ctx):
+    import paper_2409_10774_gb300 as M
+    p = W.workload_centered_sphere(ref_kind="mean")
+    ref = OS.solve(p, max_steps=3)
+    res = M.mp_solve(ctx, p, precision=0)
+    assert ref["status"] == "diverged" and res["status"] == "diverged"
+    assert res["failed_step"] == ref["failed_step"]
+
+
+def test_centered_sphere_fp32_lockstep(ctx):
+    import paper_2409_10774_gb300 as M
+    p = W.workload_centered_sphere(ref_kind="midrange")
+    ref = _oracle_solve_cached(_CACHE, "sphere16-mid-kf", p, keep_fields=False)
+    res = M.mp_solve(ctx, p, precision=1, fields=True, lockstep_iters=ref["iters"])
+    assert res["status"] == "ok"
+    _compare_solves(res, ref, 1e-6, 1e-5)
+
+
+@pytest.mark.parametrize("n", [(8, 6, 4), (1, 6, 8), (12, 1, 6), (6, 6, 1), (2, 2, 2)])
+def test_small_and_degenerate_grids_fp64(ctx, n):
+    """Ragged rows per block, singleton axes, the smallest even grid."""
+    import paper_2409_10774_gb300 as M
+    rng = np.random.default_rng(7)
+    phase = (rng.uniform(size=(n[2], n[1], n[0])) < 0.4).astype(np.uint16)
+    rows = [dict(W.generators._matrix_row()), dict(W.generators._matrix_row(1.6))]
+    rows[0]["beta"] = 0.9
+    rows[1]["alpha"] = 0.5
+    phases = W.phase_record(rows)
+    Ef = np.array([[0.006, 0.002, 0.0], [0.0, -0.001, 0.001], [0.0, 0.0, 0.002]])
+    Gf = np.array([[0.0, 0.002, 0.0], [0.001, 0.0, 0.0], [0.0, 0.0, 0.003]])
+    time, E, G = W.ramp_path(3, Ef, Gf)
+    prob = W.generators._problem(n, phase, phases, time, E, G, 1e-10, h=0.5, ref_kind="midrange")
+    ref = OS.solve(prob, keep_fields=False)
+    assert ref["status"] == "ok"
+    res = M.mp_solve(ctx, prob, precision=0, fields=True, lockstep_iters=ref["iters"])
+    _compare_solves(res, ref, 1e-11, 1e-11, h=prob["h"])
+
+
+def test_one_voxel_and_homogeneous(ctx):
+    """A homogeneous cell (and the 1-voxel grid the paper also runs) converges
+    to uniform fields, <e> = E, in one iteration per increment at FP64; the
+    FP32-mixed path is run at a tolerance above its rounding floor."""
+    import paper_2409_10774_gb300 as M
+    for n in ((1, 1, 1), (4, 4, 2)):
+        phases = W.phase_record([W.generators._matrix_row()])
+        phase = np.zeros((n[2], n[1], n[0]), np.uint16)
+        Ef = np.array([[0.004, 0.002, 0.0], [0.0, -0.001, 0.0], [0.001, 0.0, 0.0]])
+        Gf = np.array([[0.0, 0.003, 0.0], [0.0, 0.0, 0.0], [-0.002, 0.0, 0.001]])
+        time, E, G = W.ramp_path(4, Ef, Gf)
+        for precision, tol, rtol in ((0, 1e-10, 1e-12), (1, 1e-6, 1e-6)):
+            prob = W.generators._problem(n, phase, phases, time, E, G, tol)
+            ref = OS.solve(prob)
+            res = M.mp_solve(ctx, prob, precision=precision, fields=True)
+            assert res["status"] == "ok"
+            assert res["iters"].max() <= (1 if precision == 0 else 2)
+            assert np.abs(res["T"] - ref["T"]).max() <= rtol * np.abs(ref["T"]).max()
+            e = res["final"]["e"]
+            assert np.ptp(e, axis=(0, 1, 2)).max() <= rtol * np.abs(e).max()
+            np.testing.assert_allclose(res["Eavg"][-1], E[-1], rtol=0, atol=rtol * np.abs(E).max())

@@ -43,8 +43,9 @@ KERNEL_CLASSES = ("fft_y_fwd", "green_z", "fft_y_inv", "pass_a", "reduce", "star
 def algorithmic_bytes(n, precision=1):
     """Bytes one launch of each iteration kernel must move (inputs + outputs),
     for an N1 x N2 x N3 cell: the half spectrum holds 18 complex values per
-    (N1 / 2) N2 N3 points; pass A also reads the history (h_t, h_m, p, q, phase)
-    and reads + writes the previous iterate (e, gamma, f_t, f_m)."""
+    (N1 / 2) N2 N3 points; pass A also reads the history record (h_t, h_m,
+    phase id: 20 reals) and p, q (2 doubles), and reads + writes the previous
+    iterate (e, gamma, f_t, f_m: 20 reals)."""
     r = 8 if precision == 0 else 4
     nvox = n[0] * n[1] * n[2]
     nspec = max(n[0] // 2, 1) * n[1] * n[2]
@@ -53,7 +54,7 @@ def algorithmic_bytes(n, precision=1):
         "fft_y_fwd": 2 * spec,
         "green_z": 2 * spec,
         "fft_y_inv": 2 * spec,
-        "pass_a": 2 * spec + nvox * (2 * 20 * r + 18 * r + 16 + 2),
+        "pass_a": 2 * spec + nvox * (2 * 20 * r + 20 * r + 16),
     }
 
 

@@ -217,6 +217,11 @@ mp_status validate_problem(const mp_problem* p, std::vector<long long>* counts_o
     msg = "precision must be 0 or 1";
     return MP_E_INVALID_ARG;
   }
+  if (!(p->precision == 0 ? sizes_fit<double>(p->n[0], p->n[1], p->n[2])
+                          : sizes_fit<float>(p->n[0], p->n[1], p->n[2]))) {
+    msg = "grid too large for the kernels' shared-memory tiles at this precision";
+    return MP_E_UNSUPPORTED_SIZE;
+  }
   if (p->lockstep_iters)
     for (int s = 0; s < p->n_steps; ++s)
       if (p->lockstep_iters[s] < 1) {
@@ -341,7 +346,8 @@ struct mp_rve {
   std::vector<int> lockstep;
   double div_limit = 1e6;
   double ref[6] = {0, 0, 0, 0, 0, 0};
-  DevBuf spec, prev, hist, pq, elast, phase, phases, twx, twy, twz, partials, avgpart, errout, steprows;
+  DevBuf spec, prev, hist, pq, elast, phase, phases, twx, twy, twz, partials, avgpart, errout, steprows,
+      status;
   CellDev<float> cf{};
   CellDev<double> cd{};
   LaunchCfg L;
@@ -386,7 +392,8 @@ mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
   mp_status s;
   if ((s = dalloc(ctx, r->spec, sizeof(cpx<R>) * 18 * (size_t)c.nspec)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->prev, sizeof(R) * 20 * (size_t)c.nvox)) != MP_OK) return s;
-  if ((s = dalloc(ctx, r->hist, sizeof(R) * 18 * (size_t)c.nvox)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->hist, sizeof(R) * 20 * (size_t)c.nvox)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->status, sizeof(int) * 4)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->pq, sizeof(double) * 2 * (size_t)c.nvox)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->elast, sizeof(R) * 18 * (size_t)c.nvox)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->phase, sizeof(uint16_t) * (size_t)c.nvox)) != MP_OK) return s;
@@ -398,6 +405,8 @@ mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
   c.elast = reinterpret_cast<R*>(r->elast.ptr);
   c.phase = reinterpret_cast<const uint16_t*>(r->phase.ptr);
   c.phases = reinterpret_cast<const PhaseDev<R>*>(r->phases.ptr);
+  c.status = reinterpret_cast<int*>(r->status.ptr);
+  MP_CK(ctx, cudaMemsetAsync(r->status.ptr, 0, r->status.bytes, st));
   c.ref = ref_dev<R>(r->ref);
   std::vector<PhaseDev<R>> ph(p->n_phases);
   for (int k = 0; k < p->n_phases; ++k) ph[k] = phase_dev<R>(p->phases[k]);
@@ -485,12 +494,21 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
     }
     err = r->err_host[0];
     ++it;
+    if (r->err_host[5] != 0.0) {
+      status = MP_E_TIMEOUT;
+      break;
+    }
     if (!std::isfinite(err) || err > r->div_limit) {
       status = MP_E_DIVERGED;
       break;
     }
   }
   r->total_iters += it;
+  if (status == MP_E_TIMEOUT) {
+    r->failed_step = s;
+    r->steps_done = s - 1;
+    return set_error(ctx, status, "load increment %d: a bounded device wait expired", s);
+  }
   const bool predict = (status == MP_OK) && (s < r->n_steps);
   const double ratio =
       predict ? (r->time[s + 1] - r->time[s]) / (r->time[s] - r->time[s - 1]) : 0.0;
@@ -504,6 +522,8 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
   r->predicted = predict;
   if (status != MP_OK) {
     r->failed_step = s;
+    if (status == MP_E_TIMEOUT)
+      return set_error(ctx, status, "load increment %d: a bounded device wait expired", s);
     return set_error(ctx, status, "load increment %d %s after %d iterations (err %.3e)", s,
                      status == MP_E_DIVERGED ? "diverged" : "did not converge", it, err);
   }
@@ -513,7 +533,8 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
 void rve_free(mp_rve* r) {
   mp_ctx* ctx = r->ctx;
   DevBuf* bufs[] = {&r->spec, &r->prev, &r->hist, &r->pq, &r->elast, &r->phase, &r->phases,
-                    &r->twx, &r->twy, &r->twz, &r->partials, &r->avgpart, &r->errout, &r->steprows};
+                    &r->twx, &r->twy, &r->twz, &r->partials, &r->avgpart, &r->errout, &r->steprows,
+                    &r->status};
   for (DevBuf* b : bufs) dfree(ctx, *b);
   if (r->err_host) cudaFreeHost(r->err_host);
   r->err_host = nullptr;
@@ -825,9 +846,13 @@ mp_status green_apply_impl(mp_ctx* ctx, const int32_t n[3], double h, const doub
   c.inv_nvox = 1.0 / (double)c.nvox;
   for (int j = 0; j < 3; ++j) c.two_pi_over_L[j] = (R)(2.0 * M_PI / ((double)n[j] * h));
   c.ref = ref_dev<R>(ref);
-  DevBuf spec, tx, ty, tz;
+  DevBuf spec, tx, ty, tz, stat;
   std::vector<cpx<R>> h1, h2, h3;
   mp_status st = dalloc(ctx, spec, sizeof(cpx<R>) * 18 * (size_t)c.nspec);
+  if (st == MP_OK) st = dalloc(ctx, stat, sizeof(int) * 4);
+  if (st == MP_OK && cudaMemsetAsync(stat.ptr, 0, stat.bytes, cs) != cudaSuccess)
+    st = set_error(ctx, MP_E_CUDA, "cudaMemsetAsync failed");
+  c.status = reinterpret_cast<int*>(stat.ptr);
   if (st == MP_OK) st = make_axis<R>(ctx, c.n1, true, c.px, tx, cs, h1);
   if (st == MP_OK) st = make_axis<R>(ctx, c.n2, false, c.py, ty, cs, h2);
   if (st == MP_OK) st = make_axis<R>(ctx, c.n3, false, c.pz, tz, cs, h3);
@@ -835,11 +860,15 @@ mp_status green_apply_impl(mp_ctx* ctx, const int32_t n[3], double h, const doub
     c.spec = reinterpret_cast<cpx<R>*>(spec.ptr);
     LaunchCfg L = make_launch_cfg<R>(c, ctx->nsm);
     cudaError_t e = launch_green_apply<R>(L, c, (const R*)tau, (const R*)mu, (R*)e_out, (R*)g_out, cs);
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, stat.ptr, sizeof(int), cudaMemcpyDeviceToHost, cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
     if (e != cudaSuccess) st = set_error(ctx, MP_E_CUDA, "green apply: %s", cudaGetErrorString(e));
+    else if (flag) st = set_error(ctx, MP_E_TIMEOUT, "green apply: a bounded device wait expired");
   }
   cudaStreamSynchronize(cs);
   dfree(ctx, spec);
+  dfree(ctx, stat);
   dfree(ctx, tx);
   dfree(ctx, ty);
   dfree(ctx, tz);

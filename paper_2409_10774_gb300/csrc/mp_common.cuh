@@ -81,7 +81,7 @@ struct CellDev {
   R two_pi_over_L[3];     // 2 pi / (N_j h)
   cpx<R>* spec;           // [nspec][18]  polarization / fluctuation spectra
   R* prev;                // [nvox][20]   e, gamma of the last iterate + scale factors f_t, f_m
-  R* hist;                // [nvox][18]   h_t = t_n - A e_n, h_m = m_n - B gamma_n
+  R* hist;                // [nvox][20]   h_t = t_n - A e_n (9), h_m = m_n - B gamma_n (9), phase id, 0
   double* pq;             // [nvox][2]    p_n, q_n
   R* elast;               // [nvox][18]   converged e, gamma of the step before (predictor)
   const uint16_t* phase;  // [nvox]
@@ -89,6 +89,7 @@ struct CellDev {
   RefDev<R> ref;
   AxisPlan<R> px, py, pz;
   R E[9], G[9];           // prescribed averages of the current step
+  int* status;            // device status word: bit 0 = a bounded wait expired
 };
 
 // Number of doubles in one block partial of the iteration error reduction:

@@ -18,6 +18,19 @@
 
 namespace mp {
 
+// 1 / sqrt(x) in FP64 for x > 0 by Newton's method on f(y) = 1/y^2 - x,
+// y <- y (3 - x y^2) / 2, from the single-precision hardware estimate
+// (relative error ~1e-7; two steps give ~1e-16).  Arguments outside the
+// single-precision normal range take the FP64 library path.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  if (!(x > 1e-36 && x < 1e36)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+  const double hx = 0.5 * x;
+  y = y * fma(-hx * y, y, 1.5);
+  y = y * fma(-hx * y, y, 1.5);
+  return y;
+}
+
 // t_kl = lam tr(e) d_kl + (mu + kappa) e_kl + (mu - kappa) e_lk  (eq. elast_constitutive_iso)
 template <class R>
 __device__ __forceinline__ void apply_A(R lam, R mu, R kap, const R* e, R* t) {
@@ -53,28 +66,52 @@ __device__ __forceinline__ R eq_sq(const R* s, R c_sym, R c_skw, bool with_skw) 
   return v;
 }
 
-// Trial stresses of a material point (eq. trial_stresses, history form).
+// Trial stress components (eq. trial_stresses, history form) with an explicit
+// operation order, so that the same iterate always rebuilds bit-identical
+// stresses wherever it is evaluated:
+//   t_kl = h_kl + (mu + kappa) e_kl + (mu - kappa) e_lk [+ lam tr e],
+//   m_kl = h_kl + beta gamma_kl + gamma gamma_lk [+ alpha tr gamma].
+template <class R>
+__device__ __forceinline__ R trial_t(const PhaseDev<R>& P, R h, R ei, R ej, bool diag, R tr) {
+  R v = fma(P.mu - P.kap, ej, fma(P.mu + P.kap, ei, h));
+  return diag ? fma(P.lam, tr, v) : v;
+}
+template <class R>
+__device__ __forceinline__ R trial_m(const PhaseDev<R>& P, R h, R gi, R gj, bool diag, R tr) {
+  R v = fma(P.gamma, gj, fma(P.beta, gi, h));
+  return diag ? fma(P.alpha, tr, v) : v;
+}
+
 template <class R>
 __device__ __forceinline__ void trial(const PhaseDev<R>& P, const R* e, const R* g, const R* ht,
                                       const R* hm, R* t, R* m) {
-  apply_A(P.lam, P.mu, P.kap, e, t);
-  apply_B(P.alpha, P.beta, P.gamma, g, m);
+  const R tre = (e[0] + e[4]) + e[8];
+  const R trg = (g[0] + g[4]) + g[8];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    t[i] += ht[i];
-    m[i] += hm[i];
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const int i = 3 * k + l, j = 3 * l + k;
+      t[i] = trial_t(P, ht[i], e[i], e[j], k == l, tre);
+      m[i] = trial_m(P, hm[i], g[i], g[j], k == l, trg);
+    }
   }
 }
 
 // Final stresses from the trial ones and the two scale factors:
 // t = tr(t_trial)/3 d + f_t dev(t_trial), m = f_m m_trial.
 template <class R>
+__device__ __forceinline__ R vol_of(R t0, R t4, R t8) { return ((t0 + t4) + t8) * R(1.0 / 3.0); }
+template <class R>
+__device__ __forceinline__ R scaled_t(R ttr, bool diag, R vol, R ft) {
+  return diag ? fma(ft, ttr - vol, vol) : ttr * ft;
+}
+
+template <class R>
 __device__ __forceinline__ void assemble(R* t, R* m, R ft, R fm) {
-  const R vol = (t[0] + t[4] + t[8]) * R(1.0 / 3.0);
-  t[0] = vol + ft * (t[0] - vol);
-  t[4] = vol + ft * (t[4] - vol);
-  t[8] = vol + ft * (t[8] - vol);
-  t[1] *= ft; t[2] *= ft; t[3] *= ft; t[5] *= ft; t[6] *= ft; t[7] *= ft;
+  const R vol = vol_of(t[0], t[4], t[8]);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) t[i] = scaled_t(t[i], i % 4 == 0, vol, ft);
 #pragma unroll
   for (int i = 0; i < 9; ++i) m[i] *= fm;
 }
@@ -93,28 +130,33 @@ __device__ __forceinline__ void radial_return(const PhaseDev<R>& P, const R* e, 
   if (!P.elastic) {
     // macro level (eq. equiv_stress on the trial deviator)
     R s[9];
-    const R vol = (t[0] + t[4] + t[8]) * R(1.0 / 3.0);
+    const R vol = vol_of(t[0], t[4], t[8]);
 #pragma unroll
     for (int i = 0; i < 9; ++i) s[i] = t[i];
     s[0] -= vol; s[4] -= vol; s[8] -= vol;
     const double teq2 = (double)eq_sq(s, P.a1, P.a2, true);
     const double R1n = P.tY + P.tH * pn;
     if (!(teq2 < R1n * R1n)) {          // plastic: t_eq^trial >= t_Y + t_H p_n
-      const double teq = sqrt(teq2);
-      const double dp = (teq - R1n) * P.inv_t;   // eq. trial_stresses2: p - p_n
+      // eq. trial_stresses2 as p - p_n = (t_eq^trial - R1(p_n)) / (t_H + 2 a1 mu); the
+      // return factor R1 / (R1 + 2 a1 mu (p - p_n)) equals R1 / t_eq^trial, since
+      // R1(p) + 2 a1 mu (p - p_n) = t_eq^trial: no division is needed.
+      const double rinv = rsqrt_newton(teq2);
+      const double teq = teq2 * rinv;
+      const double dp = (teq - R1n) * P.inv_t;
       p = pn + dp;
       const double R1 = P.tY + P.tH * p;
-      ft = (R)(R1 / (R1 + P.ct * dp));
+      ft = (R)(R1 * rinv);
     }
     // micro level (eq. equiv_couple_stress on the trial couple stress)
-    const double meq2 = (double)eq_sq(m, P.b1, P.b2, P.skew_m != 0) ;
+    const double meq2 = (double)eq_sq(m, P.b1, P.b2, P.skew_m != 0);
     const double R2n = P.mY + P.mH * qn;
     if (!(meq2 < R2n * R2n)) {
-      const double meq = sqrt(meq2);
+      const double rinv = rsqrt_newton(meq2);
+      const double meq = meq2 * rinv;
       const double dq = (meq - R2n) * P.inv_m;
       q = qn + dq;
       const double R2 = P.mY + P.mH * q;
-      fm = (R)(R2 / (R2 + P.cm * dq));
+      fm = (R)(R2 * rinv);
     }
   }
   assemble(t, m, ft, fm);

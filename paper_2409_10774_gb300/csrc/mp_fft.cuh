@@ -1,13 +1,6 @@
-// Shared-memory Stockham FFT building blocks (sm_103a).
-//
-// A tile holds `nlines` lines of a complex transform of length M in shared
-// memory, line l at base + l * ls.  One stage of radix R (R in {2, 3, 4, 8})
-// with Ns = product of the radices already applied reads butterfly j from
-// in[j + r M / R] (r < R), multiplies input r by W_M^(r (j mod Ns) M / (Ns R)),
-// takes the R-point DFT and writes output r to out[(j / Ns) Ns R + (j mod Ns)
-// + r Ns].  After the last stage the line is in natural order (Stockham
-// autosort; no bit reversal).  Transforms are unnormalised; the solver folds
-// the 1 / (N1 N2 N3) of the inverse into the Green operator.
+// Shared-memory Stockham FFT building blocks (sm_103a).  Transforms are
+// unnormalised; the solver folds the 1 / (N1 N2 N3) of the inverse into the
+// Green operator.
 #pragma once
 
 #include "mp_common.cuh"
@@ -80,25 +73,48 @@ __device__ __forceinline__ void dft8(cpx<R>* v) {
   v[7] = csub(e[3], o3);
 }
 
-// One Stockham stage over all lines of a tile (all threads of the block).
+// Tiles are stored component-interleaved ("AoS"): element (row rr, point n,
+// component c) of a tile with `rows` rows of M points lives at
+// base[(rr M + n) 18 + c], exactly as the spectral buffer stores a row.  A
+// transform line is (rr, c), with stride 18 between its points.  Threads take
+// (c, j, rr) with c fastest, so a warp reads and writes consecutive complex
+// values: the stages are free of shared-memory bank conflicts and need no
+// transposition on load or store.
+//
+// One Stockham stage of radix R with Ns = product of the radices already
+// applied: butterfly j of a line reads points j + r M / R (r < R), multiplies
+// point r by W_M^(r (j mod Ns) M / (Ns R)), takes the R-point DFT and writes
+// output r to point (j / Ns) Ns R + (j mod Ns) + r Ns.  The last stage leaves
+// natural order (no bit reversal).  The host orders radix-3 stages last, so
+// only those divide by a non-power-of-two Ns.
 template <class R, int DIR>
-__device__ void stockham_stage(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out, int nlines,
-                               int ls, int M, int radix, int Ns, const cpx<R>* __restrict__ tw,
-                               int tstride) {
+__device__ void stage_aos(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out, int rows, int M,
+                          int radix, int Ns, const cpx<R>* __restrict__ tw, int tstride) {
   const int nb = M / radix;
-  const int total = nlines * nb;
+  const int total = rows * nb * 18;
   const int tstep = M / (Ns * radix);
+  const bool ns_pow2 = (Ns & (Ns - 1)) == 0;
+  const int ns_sh = __ffs(Ns) - 1;
+  const bool nb_pow2 = (nb & (nb - 1)) == 0;
+  const int nb_sh = __ffs(nb) - 1;
+  const int rs = M * 18;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int line = idx / nb;
-    const int j = idx - line * nb;
-    const int kk = j % Ns;
-    const cpx<R>* src = in + line * ls;
+    const int c = idx % 18;
+    const int q = idx / 18;
+    int rr = 0, j = q;
+    if (rows > 1) {
+      rr = nb_pow2 ? (q >> nb_sh) : (q / nb);
+      j = q - rr * nb;
+    }
+    const int kk = ns_pow2 ? (j & (Ns - 1)) : (j % Ns);
+    const int jq = ns_pow2 ? (j >> ns_sh) : (j / Ns);
+    const cpx<R>* src = in + rr * rs + c;
     cpx<R> v[8];
-    v[0] = src[j];
+    v[0] = src[j * 18];
 #pragma unroll
     for (int r = 1; r < 8; ++r) {
       if (r < radix) {
-        cpx<R> x = src[j + r * nb];
+        cpx<R> x = src[(j + r * nb) * 18];
         const int e = r * kk * tstep;  // < M
         v[r] = e == 0 ? x : cmul(x, twiddle<R, DIR>(tw, e * tstride));
       }
@@ -109,23 +125,23 @@ __device__ void stockham_stage(const cpx<R>* __restrict__ in, cpx<R>* __restrict
       case 4: dft4<R, DIR>(v); break;
       default: dft8<R, DIR>(v); break;
     }
-    cpx<R>* dst = out + line * ls + (j / Ns) * Ns * radix + kk;
+    cpx<R>* dst = out + rr * rs + c + (jq * Ns * radix + kk) * 18;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      if (r < radix) dst[r * Ns] = v[r];
+      if (r < radix) dst[r * Ns * 18] = v[r];
     }
   }
 }
 
-// Full complex transform of every line of a tile; data starts in buf[0] and
-// the result is returned (either buf[0] or buf[1]).  Ends with a barrier.
+// Transform every line of an AoS tile; data starts in b0, the result pointer
+// (b0 or b1) is returned.  Ends with a barrier.
 template <class R, int DIR>
-__device__ cpx<R>* line_fft(cpx<R>* b0, cpx<R>* b1, int nlines, int ls, const AxisPlan<R>& p) {
+__device__ cpx<R>* tile_fft(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R>& p) {
   cpx<R>* in = b0;
   cpx<R>* out = b1;
   int Ns = 1;
   for (int s = 0; s < p.nstages; ++s) {
-    stockham_stage<R, DIR>(in, out, nlines, ls, p.m, p.radix[s], Ns, p.tw, p.tstride);
+    stage_aos<R, DIR>(in, out, rows, p.m, p.radix[s], Ns, p.tw, p.tstride);
     Ns *= p.radix[s];
     __syncthreads();
     cpx<R>* t = in;

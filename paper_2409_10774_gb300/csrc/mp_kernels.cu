@@ -14,6 +14,7 @@
 #include "mp_constitutive.cuh"
 #include "mp_fft.cuh"
 #include "mp_green.cuh"
+#include "mp_tma.cuh"
 
 namespace mp {
 
@@ -40,31 +41,44 @@ __device__ __forceinline__ R signed_freq_scale(int k, int n, R two_pi_over_L) {
   return two_pi_over_L * (R)s;
 }
 
+// 8 warps per block.  Registers are split between the SM's four sub-partitions
+// (16 K each), so with 2 blocks per SM (4 warps per sub-partition) a thread
+// may use up to 128 registers; a 9-warp block would cap it at 96.
+constexpr int kThreads = 256;
+constexpr size_t kSmemBudget = 227 * 1024;  // dynamic shared memory per block (sm_103a opt-in maximum)
+
+// Cooperative copy of one tile column: `n` chunks of 18 complex values, chunk
+// i at g + i * stride (complex units), into / out of a contiguous AoS tile.
+template <class R, bool TO_SMEM>
+__device__ __forceinline__ void copy_column(cpx<R>* tile, cpx<R>* g, int n, long long stride) {
+  constexpr int W = 18 * (int)sizeof(cpx<R>) / 16;  // float4 per chunk
+  float4* t4 = reinterpret_cast<float4*>(tile);
+  for (int i = threadIdx.x; i < n * W; i += blockDim.x) {
+    const int row = i / W, w = i - row * W;
+    float4* g4 = reinterpret_cast<float4*>(g + row * stride) + w;
+    if (TO_SMEM) t4[row * W + w] = *g4;
+    else *g4 = t4[row * W + w];
+  }
+}
+
 // ------------------------------------------------------------------ y pass
 // One tile = one (kz, kx) column: 18 lines of length N2.
 template <class R, int DIR>
-__global__ void __launch_bounds__(256) k_fft_y(CellDev<R> c) {
+__global__ void __launch_bounds__(kThreads) k_fft_y(CellDev<R> c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem_raw);
   const int N = c.n2;
-  const int ls = N + 1;
-  cpx<R>* b1 = b0 + 18 * ls;
+  cpx<R>* b1 = b0 + 18 * N;
   const long long ntiles = (long long)c.n3 * c.kx;
-  const long long rowstride = (long long)c.kx * 18;
+  const long long stride = (long long)c.kx * 18;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int kz = (int)(tile / c.kx);
     const int kx = (int)(tile - (long long)kz * c.kx);
     cpx<R>* g = c.spec + ((long long)kz * N * c.kx + kx) * 18;
-    for (int i = threadIdx.x; i < N * 18; i += blockDim.x) {
-      const int ky = i / 18, comp = i - ky * 18;
-      b0[comp * ls + ky] = g[ky * rowstride + comp];
-    }
+    copy_column<R, true>(b0, g, N, stride);
     __syncthreads();
-    cpx<R>* r = line_fft<R, DIR>(b0, b1, 18, ls, c.py);
-    for (int i = threadIdx.x; i < N * 18; i += blockDim.x) {
-      const int ky = i / 18, comp = i - ky * 18;
-      g[ky * rowstride + comp] = r[comp * ls + ky];
-    }
+    cpx<R>* r = tile_fft<R, DIR>(b0, b1, 1, c.py);
+    copy_column<R, false>(r, g, N, stride);
     __syncthreads();
   }
 }
@@ -72,39 +86,37 @@ __global__ void __launch_bounds__(256) k_fft_y(CellDev<R> c) {
 // ------------------------------------------------------------------ z pass + Green
 // One tile = one (ky, kx) column: 18 lines of length N3.
 template <class R>
-__global__ void __launch_bounds__(256) k_green_z(CellDev<R> c) {
+__global__ void __launch_bounds__(kThreads) k_green_z(CellDev<R> c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem_raw);
   const int N = c.n3;
-  const int ls = N + 1;
-  cpx<R>* b1 = b0 + 18 * ls;
+  cpx<R>* b1 = b0 + 18 * N;
   const long long ntiles = (long long)c.n2 * c.kx;
-  const long long zstride = (long long)c.n2 * c.kx * 18;
+  const long long stride = (long long)c.n2 * c.kx * 18;
   const R scale = (R)c.inv_nvox;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int ky = (int)(tile / c.kx);
     const int kx = (int)(tile - (long long)ky * c.kx);
     cpx<R>* g = c.spec + ((long long)ky * c.kx + kx) * 18;
     const bool ny_nyq = (c.n2 % 2 == 0) && (ky == c.n2 / 2);
-    if (ny_nyq) {
-      for (int i = threadIdx.x; i < N * 18; i += blockDim.x) {
-        const int kz = i / 18, comp = i - kz * 18;
-        g[kz * zstride + comp] = cmake<R>(R(0), R(0));
+    if (ny_nyq) {  // the whole column is on the Nyquist plane of y: zero fluctuation
+      constexpr int W = 18 * (int)sizeof(cpx<R>) / 16;
+      for (int i = threadIdx.x; i < N * W; i += blockDim.x) {
+        const int row = i / W, w = i - row * W;
+        reinterpret_cast<float4*>(g + row * stride)[w] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      continue;  // uniform across the block: no barrier divergence
+      continue;  // uniform across the block
     }
-    for (int i = threadIdx.x; i < N * 18; i += blockDim.x) {
-      const int kz = i / 18, comp = i - kz * 18;
-      b0[comp * ls + kz] = g[kz * zstride + comp];
-    }
+    copy_column<R, true>(b0, g, N, stride);
     __syncthreads();
-    cpx<R>* r = line_fft<R, -1>(b0, b1, 18, ls, c.pz);
+    cpx<R>* r = tile_fft<R, -1>(b0, b1, 1, c.pz);
     const R x1 = c.n1 == 1 ? R(0) : c.two_pi_over_L[0] * (R)kx;
     const R x2 = signed_freq_scale<R>(ky, c.n2, c.two_pi_over_L[1]);
     for (int kz = threadIdx.x; kz < N; kz += blockDim.x) {
       cpx<R> v[18];
+      cpx<R>* pt = r + kz * 18;
 #pragma unroll
-      for (int q = 0; q < 18; ++q) v[q] = r[q * ls + kz];
+      for (int q = 0; q < 18; ++q) v[q] = pt[q];
       const bool nz_nyq = (N % 2 == 0) && (kz == N / 2);
       const bool zero = (kx == 0 && ky == 0 && kz == 0);
       if (nz_nyq || zero) {
@@ -115,15 +127,12 @@ __global__ void __launch_bounds__(256) k_green_z(CellDev<R> c) {
         green_point<R>(c.ref, x1, x2, x3, v, scale);
       }
 #pragma unroll
-      for (int q = 0; q < 18; ++q) r[q * ls + kz] = v[q];
+      for (int q = 0; q < 18; ++q) pt[q] = v[q];
     }
     __syncthreads();
     cpx<R>* other = (r == b0) ? b1 : b0;
-    cpx<R>* o = line_fft<R, +1>(r, other, 18, ls, c.pz);
-    for (int i = threadIdx.x; i < N * 18; i += blockDim.x) {
-      const int kz = i / 18, comp = i - kz * 18;
-      g[kz * zstride + comp] = o[comp * ls + kz];
-    }
+    cpx<R>* o = tile_fft<R, +1>(r, other, 1, c.pz);
+    copy_column<R, false>(o, g, N, stride);
     __syncthreads();
   }
 }
@@ -134,104 +143,174 @@ __global__ void __launch_bounds__(256) k_green_z(CellDev<R> c) {
 //   forward:  X[k] = (Z[k] + conj Z[M-k]) / 2 - (i / 2) W_N1^k (Z[k] - conj Z[M-k])
 //   inverse:  Z[k] = (X[k] + conj X[M-k]) + i W_N1^-k (X[k] - conj X[M-k]),  X[M] = 0
 // (X[M] is the Nyquist bin, which the Green operator sets to zero; X[0] is
-// real for a real row and its imaginary part is ignored).
+// real for a real row and its imaginary part is ignored).  Tiles are AoS:
+// point k of line (rr, c) at [(rr M + k) 18 + c].
 
 template <class R>
-__device__ __forceinline__ void x_inverse_pre(const cpx<R>* X, cpx<R>* Z, int rows, int ls, int M,
+__device__ __forceinline__ void x_inverse_pre(const cpx<R>* X, cpx<R>* Z, int rows, int M,
                                               const cpx<R>* tw) {
-  for (int idx = threadIdx.x; idx < rows * M; idx += blockDim.x) {
-    const int line = idx / M, k = idx - line * M;
-    const cpx<R>* x = X + line * ls;
-    cpx<R> a = x[k];
+  const int total = rows * M * 18;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int c = idx % 18;
+    const int q = idx / 18;          // rr * M + k
+    const int rr = q / M, k = q - rr * M;
+    const cpx<R>* x = X + rr * M * 18 + c;
+    cpx<R> a = x[k * 18];
     if (k == 0) a.y = R(0);
-    const cpx<R> b = (k == 0) ? cmake<R>(R(0), R(0)) : cconj(x[M - k]);
+    const cpx<R> b = (k == 0) ? cmake<R>(R(0), R(0)) : cconj(x[(M - k) * 18]);
     cpx<R> w = tw[k];
     w.y = -w.y;  // W_N^-k
-    Z[line * ls + k] = cadd(cadd(a, b), cmuli(cmul(w, csub(a, b))));
+    Z[idx] = cadd(cadd(a, b), cmuli(cmul(w, csub(a, b))));
   }
 }
 
 template <class R>
-__device__ __forceinline__ void x_forward_post(const cpx<R>* Z, cpx<R>* X, int rows, int ls, int M,
+__device__ __forceinline__ void x_forward_post(const cpx<R>* Z, cpx<R>* X, int rows, int M,
                                                const cpx<R>* tw) {
-  for (int idx = threadIdx.x; idx < rows * M; idx += blockDim.x) {
-    const int line = idx / M, k = idx - line * M;
-    const cpx<R>* z = Z + line * ls;
-    cpx<R> a = z[k];
-    cpx<R> b = cconj(z[k == 0 ? 0 : M - k]);
+  const int total = rows * M * 18;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int c = idx % 18;
+    const int q = idx / 18;
+    const int rr = q / M, k = q - rr * M;
+    const cpx<R>* z = Z + rr * M * 18 + c;
+    cpx<R> a = z[k * 18];
+    cpx<R> b = cconj(z[(k == 0 ? 0 : M - k) * 18]);
     cpx<R> s = cadd(a, b), d = csub(a, b);
     cpx<R> wd = cmul(tw[k], d);
     // (s - i wd) / 2
-    X[line * ls + k] = cmake<R>(R(0.5) * (s.x + wd.y), R(0.5) * (s.y - wd.x));
+    X[idx] = cmake<R>(R(0.5) * (s.x + wd.y), R(0.5) * (s.y - wd.x));
   }
 }
 
 enum PassMode { kIter = 0, kStart = 1, kXFwd = 2, kXInv = 3 };
 
-// Work item = `rows` consecutive rows (y, z) of the cell.
+// Shared-memory plan of pass A for `rows` rows of N1 voxels.
+template <class R>
+struct PassASmem {
+  size_t fft_bytes, prev_off, hist_off, pq_off, red_off, acc_off, dc_off, bar_off, total;
+  __host__ __device__ PassASmem(int n1, int rows) {
+    const int M = (n1 > 1) ? n1 / 2 : 1;
+    const size_t nvi = (size_t)rows * n1;
+    fft_bytes = (size_t)rows * M * 18 * sizeof(cpx<R>);  // multiple of 16
+    prev_off = 2 * fft_bytes;
+    hist_off = prev_off + nvi * 20 * sizeof(R);
+    pq_off = hist_off + nvi * 20 * sizeof(R);
+    red_off = pq_off + nvi * 2 * sizeof(double);
+    acc_off = red_off + 16 * 8 * sizeof(double);
+    bar_off = acc_off + kErrPartials * sizeof(double);
+    dc_off = bar_off + 2 * sizeof(uint64_t);
+    total = dc_off + ((18 * (size_t)rows * sizeof(R) + 15) / 16) * 16;
+  }
+};
+
+// Record a timeout and leave: the caller has seen a bounded wait fail.
+__device__ __forceinline__ void flag_timeout(int* status) {
+  if (threadIdx.x == 0 && status) atomicOr(status, 1);
+}
+
+// Work item = `rows` consecutive rows (y, z) of the cell = a contiguous range
+// of voxels and of spectral rows.  Rows, previous iterate, history and
+// plastic strains of an item move between global and shared memory by bulk
+// asynchronous copies (TMA); the spectral rows are loaded first so that the
+// inverse transform runs while the per-voxel data is still in flight.
 template <class R, int MODE>
-__global__ void __launch_bounds__(256) k_pass_a(CellDev<R> c, int rows, double* partials,
-                                                const R* fin_tau, const R* fin_mu, R* fout_e,
-                                                R* fout_g) {
+__global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
+    k_pass_a(CellDev<R> c, int rows, double* partials, const R* fin_tau, const R* fin_mu, R* fout_e,
+             R* fout_g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N1 = c.n1;
   const int M = c.kx;                 // complex entries per row (N1 / 2, or 1)
   const bool packed = (N1 > 1);
-  const int ls = (M > 2) ? M + 1 : M;  // padded line stride
-  const int nlines = 18 * rows;
+  const PassASmem<R> L(N1, rows);
   cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem_raw);
-  cpx<R>* b1 = b0 + nlines * ls;
-  double* red = reinterpret_cast<double*>(b1 + nlines * ls);  // [8 warps][8]
-  double* acc = red + 64;                                       // [kErrPartials] CTA total
-  R* dcin = reinterpret_cast<R*>(acc + kErrPartials);            // [18 * rows] incoming row DC
-  if (MODE == kIter) {
-    for (int i = threadIdx.x; i < kErrPartials; i += blockDim.x) acc[i] = 0.0;
-  }
+  cpx<R>* b1 = reinterpret_cast<cpx<R>*>(smem_raw + L.fft_bytes);
+  R* prev_s = reinterpret_cast<R*>(smem_raw + L.prev_off);
+  R* hist_s = reinterpret_cast<R*>(smem_raw + L.hist_off);
+  double2* pq_s = reinterpret_cast<double2*>(smem_raw + L.pq_off);
+  double* red = reinterpret_cast<double*>(smem_raw + L.red_off);
+  double* acc = reinterpret_cast<double*>(smem_raw + L.acc_off);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + L.bar_off);
+  R* dcin = reinterpret_cast<R*>(smem_raw + L.dc_off);
   const long long nrows = (long long)c.n2 * c.n3;
   const long long nitems = (nrows + rows - 1) / rows;
   const int nwarp = blockDim.x >> 5;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool use_vox = (MODE == kIter || MODE == kStart);
+  const bool use_spec_in = (MODE == kIter || MODE == kXInv);
 
-  for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_barrier_init();
+  }
+  if (MODE == kIter)
+    for (int i = threadIdx.x; i < kErrPartials; i += blockDim.x) acc[i] = 0.0;
+  __syncthreads();
+
+  uint32_t parity = 0;
+  bool failed = false;
+  for (long long item = blockIdx.x; item < nitems; item += gridDim.x, parity ^= 1u) {
     const long long row0 = item * rows;
     const int nr = (int)min((long long)rows, nrows - row0);
-    cpx<R>* zbuf;  // buffer holding the packed real rows
+    const int nvi = nr * N1;
+    const long long v0 = row0 * N1;
+    // ---------------------------------------------------------- issue loads
+    if (threadIdx.x == 0) {
+      bulk_wait_read();     // the previous item's stores have read shared memory
+      fence_proxy_async();  // and every thread's reads of it precede the new loads
+      if (use_spec_in) {
+        const uint32_t bytes = (uint32_t)(nr * M * 18 * sizeof(cpx<R>));
+        mbar_arrive_expect_tx(&bars[0], bytes);
+        bulk_load(b0, c.spec + row0 * M * 18, bytes, &bars[0]);
+      }
+      if (use_vox) {
+        const uint32_t bp = (uint32_t)(nvi * 20 * sizeof(R));
+        const uint32_t bq = (uint32_t)(nvi * 2 * sizeof(double));
+        mbar_arrive_expect_tx(&bars[1], 2 * bp + bq);
+        bulk_load(prev_s, c.prev + v0 * 20, bp, &bars[1]);
+        bulk_load(hist_s, c.hist + v0 * 20, bp, &bars[1]);
+        bulk_load(pq_s, c.pq + v0 * 2, bq, &bars[1]);
+      }
+    }
+    cpx<R>* zbuf = b0;  // buffer holding the packed real rows
     // ---------------------------------------------------------- inverse x
-    if (MODE == kIter || MODE == kXInv) {
-      for (int i = threadIdx.x; i < nr * M * 18; i += blockDim.x) {
-        const int rr = i / (M * 18);
-        const int rem = i - rr * M * 18;
-        const int k = rem / 18, comp = rem - k * 18;
-        b0[(comp * rows + rr) * ls + k] = c.spec[((row0 + rr) * M + k) * 18 + comp];
+    if (use_spec_in) {
+      const bool ok = mbar_wait(&bars[0], parity);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
       }
-      __syncthreads();
-      if (MODE == kIter) {
-        for (int l = threadIdx.x; l < nlines; l += blockDim.x) dcin[l] = b0[l * ls].x;
-      }
+      if (MODE == kIter)
+        for (int l = threadIdx.x; l < 18 * nr; l += blockDim.x) {
+          const int rr = l / 18, cc = l - rr * 18;
+          dcin[cc * rows + rr] = b0[rr * M * 18 + cc].x;
+        }
       if (packed) {
-        // all 18 * rows lines are transformed; lines of rows >= nr are never stored
-        x_inverse_pre<R>(b0, b1, nlines, ls, M, c.px.tw);
+        x_inverse_pre<R>(b0, b1, nr, M, c.px.tw);
         __syncthreads();
-        // lines are indexed comp * rows + rr; transform all 18 * rows lines
-        zbuf = line_fft<R, +1>(b1, b0, nlines, ls, c.px);
-      } else {
-        zbuf = b0;
+        zbuf = tile_fft<R, +1>(b1, b0, nr, c.px);
       }
-    } else {
-      zbuf = b0;
+    }
+    if (use_vox) {
+      const bool ok = mbar_wait(&bars[1], parity);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
     }
     // ---------------------------------------------------------- per voxel
     R dmax[4] = {R(0), R(0), R(0), R(0)};
     R dsum[4] = {R(0), R(0), R(0), R(0)};
-    for (int lv = threadIdx.x; lv < nr * N1; lv += blockDim.x) {
+    for (int lv = threadIdx.x; lv < nvi; lv += blockDim.x) {
       const int rr = lv / N1, x = lv - rr * N1;
-      const long long v = (row0 + rr) * N1 + x;
+      const int zb = (rr * M + (packed ? (x >> 1) : 0)) * 18;  // first comp of the voxel's complex
+      const long long v = v0 + lv;
       R val[18];
-      if (MODE == kIter || MODE == kXInv) {
+      if (use_spec_in) {
 #pragma unroll
         for (int q = 0; q < 18; ++q) {
-          const cpx<R> z = zbuf[(q * rows + rr) * ls + (packed ? (x >> 1) : 0)];
-          val[q] = packed ? ((x & 1) ? z.y : z.x) : z.x;
+          const cpx<R> z = zbuf[zb + q];
+          val[q] = (packed && (x & 1)) ? z.y : z.x;
         }
       }
       if (MODE == kXInv) {
@@ -242,117 +321,123 @@ __global__ void __launch_bounds__(256) k_pass_a(CellDev<R> c, int rows, double* 
         }
         continue;
       }
-      R out[18];
+      // value q of this voxel goes to the real (even x) or imaginary (odd x)
+      // part of its packed complex entry
+      R* zr = reinterpret_cast<R*>(zbuf + zb) + ((packed && (x & 1)) ? 1 : 0);
+      if (!packed) {
+#pragma unroll
+        for (int q = 0; q < 18; ++q) zr[2 * q + 1] = R(0);
+      }
       if (MODE == kXFwd) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-          out[q] = fin_tau[v * 9 + q];
-          out[9 + q] = fin_mu[v * 9 + q];
+          zr[2 * q] = fin_tau[v * 9 + q];
+          zr[2 * (9 + q)] = fin_mu[v * 9 + q];
+        }
+        continue;
+      }
+      R* pv = prev_s + lv * 20;
+      const R* hv = hist_s + lv * 20;
+      R e[9], gm[9];
+      if (MODE == kIter) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          e[q] = c.E[q] + val[q];
+          gm[q] = c.G[q] + val[9 + q];
         }
       } else {
-        R e[9], gm[9];
-        const R* pv = c.prev + v * 20;
-        if (MODE == kIter) {
-#pragma unroll
-          for (int q = 0; q < 9; ++q) {
-            e[q] = c.E[q] + val[q];
-            gm[q] = c.G[q] + val[9 + q];
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < 9; ++q) {
-            e[q] = pv[q];
-            gm[q] = pv[9 + q];
-          }
-        }
-        const PhaseDev<R> P = c.phases[c.phase[v]];
-        R ht[9], hm[9];
-        const R* hv = c.hist + v * 18;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-          ht[q] = hv[q];
-          hm[q] = hv[9 + q];
-        }
-        const double2 pq = reinterpret_cast<const double2*>(c.pq)[v];
-        R t[9], m[9];
-        double p, qq;
-        R ft, fm;
-        radial_return<R>(P, e, gm, ht, hm, pq.x, pq.y, t, m, p, qq, ft, fm);
-        if (MODE == kIter) {
-          // previous iterate: e, gamma stored, t, m rebuilt from the stored scale factors
-          R eo[9], go[9], to[9], mo[9];
-#pragma unroll
-          for (int q = 0; q < 9; ++q) {
-            eo[q] = pv[q];
-            go[q] = pv[9 + q];
-          }
-          const R fto = pv[18], fmo = pv[19];
-          trial<R>(P, eo, go, ht, hm, to, mo);
-          assemble<R>(to, mo, fto, fmo);
-          R de = R(0), dt = R(0), dg = R(0), dm = R(0);
-#pragma unroll
-          for (int q = 0; q < 9; ++q) {
-            const R a = e[q] - eo[q], b = t[q] - to[q], cc = gm[q] - go[q], d = m[q] - mo[q];
-            de += a * a; dt += b * b; dg += cc * cc; dm += d * d;
-          }
-          de = sqrt(de); dt = sqrt(dt); dg = sqrt(dg); dm = sqrt(dm);
-          dmax[0] = max(dmax[0], de); dmax[1] = max(dmax[1], dt);
-          dmax[2] = max(dmax[2], dg); dmax[3] = max(dmax[3], dm);
-          dsum[0] += de; dsum[1] += dt; dsum[2] += dg; dsum[3] += dm;
-        }
-        // store the new iterate (e, gamma, f_t, f_m)
-        R* pw = c.prev + v * 20;
-        if (MODE == kIter) {
-#pragma unroll
-          for (int q = 0; q < 9; ++q) {
-            pw[q] = e[q];
-            pw[9 + q] = gm[q];
-          }
-        }
-        pw[18] = ft;
-        pw[19] = fm;
-        // polarizations (eq. micropolar_polarizatons): tau = t - A0 e, mu = m - B0 gamma
-        R ae[9], bg[9];
-        apply_A<R>(c.ref.lam, c.ref.mu, c.ref.kap, e, ae);
-        apply_B<R>(c.ref.alpha, c.ref.beta, c.ref.gamma, gm, bg);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-          out[q] = t[q] - ae[q];
-          out[9 + q] = m[q] - bg[q];
+          e[q] = pv[q];
+          gm[q] = pv[9 + q];
         }
       }
-      // write back into the packed row
+      const PhaseDev<R>& P = c.phases[(int)hv[18]];
+      const double2 pq = pq_s[lv];
+      R t[9], m[9];
+      double p, qq;
+      R ft, fm;
+      radial_return<R>(P, e, gm, hv, hv + 9, pq.x, pq.y, t, m, p, qq, ft, fm);
+      if (MODE == kIter) {
+        // previous iterate: e, gamma stored; t, m rebuilt component by component
+        // from the stored scale factors (t = tr/3 d + f_t dev(t_trial), m = f_m m_trial)
+        const R fto = pv[18], fmo = pv[19];
+        const R tre = (pv[0] + pv[4]) + pv[8], trg = (pv[9] + pv[13]) + pv[17];
+        const R vol = vol_of(trial_t(P, hv[0], pv[0], pv[0], true, tre),
+                             trial_t(P, hv[4], pv[4], pv[4], true, tre),
+                             trial_t(P, hv[8], pv[8], pv[8], true, tre));
+        R de = R(0), dt = R(0), dg = R(0), dm = R(0);
 #pragma unroll
-      for (int q = 0; q < 18; ++q) {
-        cpx<R>* z = &zbuf[(q * rows + rr) * ls + (packed ? (x >> 1) : 0)];
-        if (!packed) {
-          *z = cmake<R>(out[q], R(0));
-        } else if (x & 1) {
-          z->y = out[q];
-        } else {
-          z->x = out[q];
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+          for (int l = 0; l < 3; ++l) {
+            const int i = 3 * k + l, j = 3 * l + k;
+            const R to = scaled_t(trial_t(P, hv[i], pv[i], pv[j], k == l, tre), k == l, vol, fto);
+            const R mo = trial_m(P, hv[9 + i], pv[9 + i], pv[9 + j], k == l, trg) * fmo;
+            const R d1 = e[i] - pv[i], d2 = t[i] - to, d3 = gm[i] - pv[9 + i], d4 = m[i] - mo;
+            de += d1 * d1; dt += d2 * d2; dg += d3 * d3; dm += d4 * d4;
+          }
+        }
+        de = sqrt(de); dt = sqrt(dt); dg = sqrt(dg); dm = sqrt(dm);
+        dmax[0] = max(dmax[0], de); dmax[1] = max(dmax[1], dt);
+        dmax[2] = max(dmax[2], dg); dmax[3] = max(dmax[3], dm);
+        dsum[0] += de; dsum[1] += dt; dsum[2] += dg; dsum[3] += dm;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          pv[q] = e[q];
+          pv[9 + q] = gm[q];
+        }
+      }
+      pv[18] = ft;
+      pv[19] = fm;
+      // polarizations (eq. micropolar_polarizatons): tau = t - A0 e, mu = m - B0 gamma
+      {
+        const R tre = e[0] + e[4] + e[8], trg = gm[0] + gm[4] + gm[8];
+        const R a = c.ref.mu + c.ref.kap, b = c.ref.mu - c.ref.kap;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+          for (int l = 0; l < 3; ++l) {
+            const int i = 3 * k + l, j = 3 * l + k;
+            R ae = a * e[i] + b * e[j];
+            R bg = c.ref.beta * gm[i] + c.ref.gamma * gm[j];
+            if (k == l) {
+              ae += c.ref.lam * tre;
+              bg += c.ref.alpha * trg;
+            }
+            zr[2 * i] = t[i] - ae;
+            zr[2 * (9 + i)] = m[i] - bg;
+          }
         }
       }
     }
+    if (MODE == kXInv) {
+      __syncthreads();
+      continue;
+    }
+    // the new iterate goes back to global memory while the forward transform runs
+    fence_proxy_async();
     __syncthreads();
-    if (MODE == kXInv) continue;
+    if (use_vox && threadIdx.x == 0) {
+      bulk_store(c.prev + v0 * 20, prev_s, (uint32_t)(nvi * 20 * sizeof(R)));
+      bulk_commit();
+    }
     // ---------------------------------------------------------- forward x
     cpx<R>* X;
     if (packed) {
       cpx<R>* other = (zbuf == b0) ? b1 : b0;
-      cpx<R>* Z = line_fft<R, -1>(zbuf, other, nlines, ls, c.px);
+      cpx<R>* Z = tile_fft<R, -1>(zbuf, other, nr, c.px);
       cpx<R>* dst = (Z == b0) ? b1 : b0;
-      x_forward_post<R>(Z, dst, nlines, ls, M, c.px.tw);
-      __syncthreads();
+      x_forward_post<R>(Z, dst, nr, M, c.px.tw);
       X = dst;
     } else {
       X = zbuf;
     }
-    for (int i = threadIdx.x; i < nr * M * 18; i += blockDim.x) {
-      const int rr = i / (M * 18);
-      const int rem = i - rr * M * 18;
-      const int k = rem / 18, comp = rem - k * 18;
-      c.spec[((row0 + rr) * M + k) * 18 + comp] = X[(comp * rows + rr) * ls + k];
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      bulk_store(c.spec + row0 * M * 18, X, (uint32_t)(nr * M * 18 * sizeof(cpx<R>)));
+      bulk_commit();
     }
     // ---------------------------------------------------------- error partials
     if (MODE == kIter) {
@@ -382,12 +467,23 @@ __global__ void __launch_bounds__(256) k_pass_a(CellDev<R> c, int rows, double* 
           const double mean = (q < 9) ? (double)c.E[q] : (double)c.G[q - 9];
           for (int rr = 0; rr < nr; ++rr) a += (double)N1 * (mean + (double)dcin[q * rows + rr]);
         } else {
-          for (int rr = 0; rr < nr; ++rr) a += (double)X[((q - 18) * rows + rr) * ls].x;
+          for (int rr = 0; rr < nr; ++rr) a += (double)X[rr * M * 18 + (q - 18)].x;
         }
         acc[8 + q] += a;  // each of these threads owns one entry of the CTA total
       }
     }
     __syncthreads();
+  }
+  if (threadIdx.x == 0) bulk_wait_all();
+  if (failed) {
+    // wait (bounded) for this block's loads still in flight, then report
+    if (threadIdx.x == 0) {
+      if (use_spec_in) mbar_wait(&bars[0], parity);
+      if (use_vox) mbar_wait(&bars[1], parity);
+    }
+    __syncthreads();
+    flag_timeout(c.status);
+    return;
   }
   if (MODE == kIter) {
     for (int i = threadIdx.x; i < kErrPartials; i += blockDim.x)
@@ -450,6 +546,7 @@ __global__ void k_reduce_err(CellDev<R> c, const double* partials, int nparts, i
       out[1 + a] = ea;
     }
     out[0] = err;
+    out[5] = c.status ? (double)(*c.status) : 0.0;
   }
 }
 
@@ -461,7 +558,7 @@ __global__ void k_init(CellDev<R> c) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < c.nvox;
        v += (long long)gridDim.x * blockDim.x) {
     R* pv = c.prev + v * 20;
-    R* hv = c.hist + v * 18;
+    R* hv = c.hist + v * 20;
     R* el = c.elast + v * 18;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
@@ -475,6 +572,8 @@ __global__ void k_init(CellDev<R> c) {
       hv[q] = R(0);
       el[q] = R(0);
     }
+    hv[18] = (R)c.phase[v];  // phase id travels with the history record
+    hv[19] = R(0);
     reinterpret_cast<double2*>(c.pq)[v] = make_double2(0.0, 0.0);
   }
 }
@@ -493,7 +592,7 @@ __global__ void __launch_bounds__(256) k_commit(CellDev<R> c, int predict, R rat
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < c.nvox;
        v += (long long)gridDim.x * blockDim.x) {
     R* pv = c.prev + v * 20;
-    R* hv = c.hist + v * 18;
+    R* hv = c.hist + v * 20;
     R e[9], g[9], ht[9], hm[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
@@ -571,7 +670,7 @@ __global__ void k_fields(CellDev<R> c, const R* src, int src_stride, double* fe,
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < c.nvox;
        v += (long long)gridDim.x * blockDim.x) {
     const R* s = src + v * src_stride;
-    const R* hv = c.hist + v * 18;
+    const R* hv = c.hist + v * 20;
     R e[9], g[9], t[9], m[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
@@ -634,21 +733,16 @@ __global__ void __launch_bounds__(256) k_radial_return_points(
 
 // ------------------------------------------------------------------ launchers
 template <class R>
-size_t smem_line_pass(int n) { return 2ull * 18 * (size_t)(n + 1) * sizeof(cpx<R>); }
+size_t smem_line_pass(int n) { return 2ull * 18 * (size_t)n * sizeof(cpx<R>); }
 
 template <class R>
-size_t smem_pass_a(int n1, int rows) {
-  const int M = (n1 > 1) ? n1 / 2 : 1;
-  const int ls = (M > 2) ? M + 1 : M;
-  return 2ull * 18 * rows * ls * sizeof(cpx<R>) + (64 + kErrPartials) * sizeof(double) +
-         18ull * rows * sizeof(R);
-}
+size_t smem_pass_a(int n1, int rows) { return PassASmem<R>(n1, rows).total; }
 
 template <class R>
 static cudaError_t set_smem_attrs() {
   static bool done = false;
   if (done) return cudaSuccess;
-  const int maxs = 227 * 1024;
+  const int maxs = (int)kSmemBudget;
   cudaError_t e = cudaSuccess;
 #define MP_ATTR(k) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs)
@@ -680,8 +774,8 @@ cudaError_t launch_fft_y(const LaunchCfg& L, const CellDev<R>& c, int dir, cudaS
   cudaError_t e = set_smem_attrs<R>();
   if (e != cudaSuccess) return e;
   if (c.n2 > 1) {
-    if (dir < 0) k_fft_y<R, -1><<<L.grid_y, 256, smem_line_pass<R>(c.n2), st>>>(c);
-    else k_fft_y<R, +1><<<L.grid_y, 256, smem_line_pass<R>(c.n2), st>>>(c);
+    if (dir < 0) k_fft_y<R, -1><<<L.grid_y, kThreads, smem_line_pass<R>(c.n2), st>>>(c);
+    else k_fft_y<R, +1><<<L.grid_y, kThreads, smem_line_pass<R>(c.n2), st>>>(c);
   }
   return cudaGetLastError();
 }
@@ -690,7 +784,7 @@ template <class R>
 cudaError_t launch_green_z(const LaunchCfg& L, const CellDev<R>& c, cudaStream_t st) {
   cudaError_t e = set_smem_attrs<R>();
   if (e != cudaSuccess) return e;
-  k_green_z<R><<<L.grid_z, 256, smem_line_pass<R>(c.n3), st>>>(c);
+  k_green_z<R><<<L.grid_z, kThreads, smem_line_pass<R>(c.n3), st>>>(c);
   return cudaGetLastError();
 }
 
@@ -699,7 +793,7 @@ cudaError_t launch_pass_a_iter(const LaunchCfg& L, const CellDev<R>& c, double* 
                                cudaStream_t st) {
   cudaError_t e = set_smem_attrs<R>();
   if (e != cudaSuccess) return e;
-  k_pass_a<R, kIter><<<L.grid_a, 256, smem_pass_a<R>(c.n1, L.rows), st>>>(c, L.rows, partials, nullptr,
+  k_pass_a<R, kIter><<<L.grid_a, kThreads, smem_pass_a<R>(c.n1, L.rows), st>>>(c, L.rows, partials, nullptr,
                                                                            nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
@@ -727,7 +821,7 @@ cudaError_t launch_start(const LaunchCfg& L, const CellDev<R>& c, int first, cud
   cudaError_t e = set_smem_attrs<R>();
   if (e != cudaSuccess) return e;
   if (first) k_init<R><<<L.grid_v, 256, 0, st>>>(c);
-  k_pass_a<R, kStart><<<L.grid_a, 256, smem_pass_a<R>(c.n1, L.rows), st>>>(c, L.rows, nullptr, nullptr,
+  k_pass_a<R, kStart><<<L.grid_a, kThreads, smem_pass_a<R>(c.n1, L.rows), st>>>(c, L.rows, nullptr, nullptr,
                                                                             nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
@@ -755,11 +849,11 @@ cudaError_t launch_green_apply(const LaunchCfg& L, const CellDev<R>& c, const R*
   cudaError_t e = set_smem_attrs<R>();
   if (e != cudaSuccess) return e;
   const size_t sa = smem_pass_a<R>(c.n1, L.rows);
-  k_pass_a<R, kXFwd><<<L.grid_a, 256, sa, st>>>(c, L.rows, nullptr, tau, mu, nullptr, nullptr);
-  if (c.n2 > 1) k_fft_y<R, -1><<<L.grid_y, 256, smem_line_pass<R>(c.n2), st>>>(c);
-  k_green_z<R><<<L.grid_z, 256, smem_line_pass<R>(c.n3), st>>>(c);
-  if (c.n2 > 1) k_fft_y<R, +1><<<L.grid_y, 256, smem_line_pass<R>(c.n2), st>>>(c);
-  k_pass_a<R, kXInv><<<L.grid_a, 256, sa, st>>>(c, L.rows, nullptr, nullptr, nullptr, e_out, g_out);
+  k_pass_a<R, kXFwd><<<L.grid_a, kThreads, sa, st>>>(c, L.rows, nullptr, tau, mu, nullptr, nullptr);
+  if (c.n2 > 1) k_fft_y<R, -1><<<L.grid_y, kThreads, smem_line_pass<R>(c.n2), st>>>(c);
+  k_green_z<R><<<L.grid_z, kThreads, smem_line_pass<R>(c.n3), st>>>(c);
+  if (c.n2 > 1) k_fft_y<R, +1><<<L.grid_y, kThreads, smem_line_pass<R>(c.n2), st>>>(c);
+  k_pass_a<R, kXInv><<<L.grid_a, kThreads, sa, st>>>(c, L.rows, nullptr, nullptr, nullptr, e_out, g_out);
   return cudaGetLastError();
 }
 
@@ -781,21 +875,27 @@ template <class R>
 LaunchCfg make_launch_cfg(const CellDev<R>& c, int nsm) {
   set_smem_attrs<R>();
   LaunchCfg L;
-  // rows per pass-A item: ~256 voxels per block
+  // rows per pass-A item: about 256 voxels per block, within the shared-memory budget
   int rows = c.n1 >= 256 ? 1 : 256 / c.n1;
-  if (c.n1 <= 2 && sizeof(R) == 8) rows = 128;
+  while (rows > 1 && smem_pass_a<R>(c.n1, rows) > kSmemBudget) rows /= 2;
   if ((long long)rows > (long long)c.n2 * c.n3) rows = (int)((long long)c.n2 * c.n3);
   L.rows = rows;
   const long long nrows = (long long)c.n2 * c.n3;
   const long long items = (nrows + rows - 1) / rows;
-  L.grid_a = grid_for<R>((const void*)k_pass_a<R, kIter>, 256, smem_pass_a<R>(c.n1, rows), items, nsm);
-  L.grid_y = grid_for<R>((const void*)k_fft_y<R, -1>, 256, smem_line_pass<R>(c.n2),
+  L.grid_a = grid_for<R>((const void*)k_pass_a<R, kIter>, kThreads, smem_pass_a<R>(c.n1, rows), items, nsm);
+  L.grid_y = grid_for<R>((const void*)k_fft_y<R, -1>, kThreads, smem_line_pass<R>(c.n2),
                          (long long)c.n3 * c.kx, nsm);
-  L.grid_z = grid_for<R>((const void*)k_green_z<R>, 256, smem_line_pass<R>(c.n3),
+  L.grid_z = grid_for<R>((const void*)k_green_z<R>, kThreads, smem_line_pass<R>(c.n3),
                          (long long)c.n2 * c.kx, nsm);
   long long vb = (c.nvox + 255) / 256;
   L.grid_v = (int)(vb < 4ll * nsm ? vb : 4ll * nsm);
   return L;
+}
+
+template <class R>
+bool sizes_fit(int n1, int n2, int n3) {
+  return smem_pass_a<R>(n1, 1) <= kSmemBudget && smem_line_pass<R>(n2) <= kSmemBudget &&
+         smem_line_pass<R>(n3) <= kSmemBudget;
 }
 
 #define MP_INSTANTIATE(R)                                                                            \
@@ -817,7 +917,8 @@ LaunchCfg make_launch_cfg(const CellDev<R>& c, int nsm) {
                                                const R*, const R*, const R*, const R*, const R*,      \
                                                const R*, const double*, const double*, R*, R*,        \
                                                double*, double*, cudaStream_t);                       \
-  template LaunchCfg make_launch_cfg<R>(const CellDev<R>&, int);
+  template LaunchCfg make_launch_cfg<R>(const CellDev<R>&, int);                                       \
+  template bool sizes_fit<R>(int, int, int);
 
 MP_INSTANTIATE(float)
 MP_INSTANTIATE(double)

@@ -15,6 +15,9 @@ struct LaunchCfg {
 
 template <class R>
 LaunchCfg make_launch_cfg(const CellDev<R>& c, int nsm);
+// Whether the kernels' shared-memory tiles fit for this grid in precision R.
+template <class R>
+bool sizes_fit(int n1, int n2, int n3);
 
 // The kernels of one fixed-point iteration, one launch each (y pass dir -1 forward, +1 inverse).
 template <class R>

@@ -211,6 +211,32 @@ mp_status mp_green_apply(mp_ctx* ctx, int32_t precision, const int32_t n[3], dou
                          const double ref_moduli[6], const void* tau, const void* mu, void* e_out,
                          void* g_out, void* stream);
 
+/* Allocation-free variant ------------------------------------------------
+ * The paper has no counterpart: this is a library-side convenience.
+ *
+ * mp_green_apply_static computes exactly what mp_green_apply computes, for
+ * callers that cannot allocate device memory at the point of the call - for
+ * example an application that runs this library inside a fixed device-memory
+ * budget reserved up front by another runtime, or a latency-critical loop
+ * that must not trigger the implicit device synchronisation or the
+ * out-of-memory failures that cudaMalloc / cudaFree can bring.  It calls no
+ * allocator at all.  Instead it works in one static device array of
+ * MP_STATIC_SCRATCH_BYTES that every GPU loading the library keeps until the
+ * process exits: 32 KiB for a status word and the twiddle tables, the rest
+ * for the 18-component half spectrum, which limits the grid to
+ * (N1 / 2) N2 N3 * 18 * (8 bytes FP32 | 16 bytes FP64) <= 8 MiB - 32 KiB
+ * (e.g. 48^3 in FP32, 32^3 in FP64); larger grids return
+ * MP_E_UNSUPPORTED_SIZE with a message.
+ * The first call on a device looks up the array's device address for that
+ * device (with the context's device current); make that first call before
+ * any stream capture.  Calls share the array: calls whose GPU work overlaps
+ * (other streams or host threads) race on it and must be serialised by the
+ * caller.  Arguments as for mp_green_apply. */
+#define MP_STATIC_SCRATCH_BYTES (8u * 1024u * 1024u)
+mp_status mp_green_apply_static(mp_ctx* ctx, int32_t precision, const int32_t n[3], double h,
+                                const double ref_moduli[6], const void* tau, const void* mu,
+                                void* e_out, void* g_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

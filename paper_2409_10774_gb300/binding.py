@@ -29,7 +29,8 @@ REF_KIND = {"mean": 0, "midrange": 1, "explicit": 2}
 EXPORTED = ("mp_abi_version", "mp_create", "mp_destroy", "mp_last_error", "mp_validate",
             "mp_solve", "mp_rve_create", "mp_rve_run", "mp_rve_results", "mp_rve_reset",
             "mp_rve_steps_done", "mp_rve_iterations", "mp_rve_destroy", "mp_rve_profile",
-            "mp_rve_profile_read", "mp_radial_return", "mp_green_apply")
+            "mp_rve_profile_read", "mp_radial_return", "mp_green_apply", "mp_green_apply_static")
+MP_STATIC_SCRATCH_BYTES = 8 * 1024 * 1024
 KERNEL_CLASSES = ("fft_y_fwd", "green_z", "fft_y_inv", "pass_a", "reduce", "start", "commit")
 
 
@@ -100,6 +101,8 @@ def _load():
         "mp_radial_return": (C.c_int, [V, C.c_int32, C.c_int64, V, C.c_int32, P(mp_phase)] + [V] * 6
                              + [V, V, V, V, V, V, V]),
         "mp_green_apply": (C.c_int, [V, C.c_int32, P(C.c_int32), C.c_double, P(C.c_double), V, V, V, V, V]),
+        "mp_green_apply_static": (C.c_int, [V, C.c_int32, P(C.c_int32), C.c_double, P(C.c_double), V, V, V, V,
+                                            V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -420,3 +423,25 @@ def mp_green_apply(ctx, precision, n, h, ref_moduli, tau, mu, stream=None):
     if st != MP_OK:
         raise MicropolarError(st, ctx.error())
     return e, g
+
+
+def mp_green_apply_static(ctx, precision, n, h, ref_moduli, tau, mu, e_out=None, g_out=None,
+                          stream=None):
+    """Same result as mp_green_apply, computed without any device allocation
+    inside the library (its scratch is a static device array of
+    MP_STATIC_SCRATCH_BYTES).  The caller passes the output tensors; when they
+    are omitted this wrapper allocates them with torch before the call."""
+    import torch
+    R = _real(precision)
+    if e_out is None:
+        e_out = torch.empty_like(tau)
+    if g_out is None:
+        g_out = torch.empty_like(mu)
+    nn = (C.c_int32 * 3)(*[int(v) for v in n])
+    ref = (C.c_double * 6)(*[float(v) for v in ref_moduli])
+    st = LIB.mp_green_apply_static(ctx.ptr, int(precision), nn, float(h), ref, _check_dev(tau, R),
+                                   _check_dev(mu, R), _check_dev(e_out, R), _check_dev(g_out, R),
+                                   _stream_handle(stream))
+    if st != MP_OK:
+        raise MicropolarError(st, ctx.error())
+    return e_out, g_out

@@ -20,6 +20,9 @@ struct mp_ctx {
   std::string last_error;
 };
 
+// Context accessors for the static-scratch entry point (mp_static.cu); not exported.
+__attribute__((visibility("hidden"))) int mp_ctx_device(const mp_ctx* ctx) { return ctx ? ctx->device : 0; }
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -34,6 +37,14 @@ mp_status set_error(mp_ctx* ctx, mp_status st, const char* fmt, ...) {
   g_last_error = buf;
   return st;
 }
+
+}  // namespace
+
+__attribute__((visibility("hidden"))) void mp_ctx_set_error(mp_ctx* ctx, const char* msg) {
+  set_error(ctx, MP_E_INVALID_ARG, "%s", msg);
+}
+
+namespace {
 
 #define MP_CK(ctx, call)                                                                      \
   do {                                                                                        \

@@ -1,0 +1,184 @@
+// mp_green_apply_static: the Green-operator application of mp_green_apply
+// for callers that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc (or any allocator) at the point where
+// they need the operator: for example an application that hands this library
+// a fixed device-memory budget reserved up front by another runtime, or a
+// latency-critical loop that must not trigger the implicit device
+// synchronisation and the out-of-memory failures that cudaMalloc / cudaFree
+// can bring.  This entry point therefore works entirely in one file-scope
+// device array, `g_static_scratch`, of MP_STATIC_SCRATCH_BYTES: its first
+// 32 KiB hold the status word and the three twiddle tables, the rest holds
+// the 18-component half spectrum.  Every GPU that loads the library holds
+// this array until the process exits.
+//
+// The array's name is only a host-side stand-in in host code; its device
+// address is looked up with cudaGetSymbolAddress once per device, with that
+// device current, on the first call made on the device (make that first
+// call before any stream capture).  All calls share the array and it keeps
+// the last call's contents: the status word is cleared on every call, and
+// the spectrum is fully overwritten by the forward transform before it is
+// read.  Calls whose work overlaps on the GPU (other streams, other host
+// threads) race on the array; serialise them.
+#include <cmath>
+#include <mutex>
+
+#include "../../include/micropolar.h"
+#include "mp_kernels.cuh"
+
+using namespace mp;
+
+// Context accessors (defined with mp_ctx in mp_api.cu; not exported).
+__attribute__((visibility("hidden"))) int mp_ctx_device(const mp_ctx* ctx);
+__attribute__((visibility("hidden"))) void mp_ctx_set_error(mp_ctx* ctx, const char* msg);
+
+namespace {
+
+constexpr size_t kTableRegion = 32 * 1024;  // status word + three twiddle tables
+constexpr size_t kSpectrumBytes = MP_STATIC_SCRATCH_BYTES - kTableRegion;
+constexpr int kMaxAxis = 512;
+
+static __device__ __align__(256) unsigned char g_static_scratch[MP_STATIC_SCRATCH_BYTES];
+
+std::mutex g_setup_mutex;
+void* g_scratch_ptr[64] = {nullptr};
+
+mp_status fail(mp_ctx* ctx, mp_status st, const char* msg) {
+  mp_ctx_set_error(ctx, msg);
+  return st;
+}
+
+// Device address of the scratch array for the current device (set-up on the
+// first call made on that device).
+mp_status scratch_for_current_device(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return fail(nullptr, MP_E_NO_DEVICE, "mp_green_apply_static: no current CUDA device");
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(nullptr, MP_E_CUDA, "mp_green_apply_static: cudaGetSymbolAddress failed");
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return MP_OK;
+}
+
+bool axis_ok(int n) {
+  if (n == 1) return true;
+  if (n < 2 || n > kMaxAxis || (n % 2) != 0) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+void radices(int m, int* radix, int& nst) {
+  nst = 0;
+  int k2 = 0, k3 = 0;
+  while (m % 2 == 0) { m /= 2; ++k2; }
+  while (m % 3 == 0) { m /= 3; ++k3; }
+  while (k2 >= 3 && k2 - 3 != 1) { radix[nst++] = 8; k2 -= 3; }
+  if (k2 == 4) { radix[nst++] = 4; radix[nst++] = 4; }
+  else if (k2 == 2) { radix[nst++] = 4; }
+  else if (k2 == 1) { radix[nst++] = 2; }
+  for (int i = 0; i < k3; ++i) radix[nst++] = 3;
+}
+
+template <class R>
+mp_status run(mp_ctx* ctx, const int32_t n[3], double h, const double ref[6], const void* tau,
+              const void* mu, void* e_out, void* g_out, cudaStream_t st) {
+  void* base = nullptr;
+  mp_status s = scratch_for_current_device(&base);
+  if (s != MP_OK) return s;
+  unsigned char* b = static_cast<unsigned char*>(base);
+  int* status = reinterpret_cast<int*>(b);
+  cpx<R>* tw[3];
+  for (int a = 0; a < 3; ++a) tw[a] = reinterpret_cast<cpx<R>*>(b + 256 + (size_t)a * kMaxAxis * sizeof(cpx<double>));
+
+  CellDev<R> c{};
+  c.n1 = n[0];
+  c.n2 = n[1];
+  c.n3 = n[2];
+  c.kx = (c.n1 > 1) ? c.n1 / 2 : 1;
+  c.nvox = (long long)n[0] * n[1] * n[2];
+  c.nspec = (long long)c.kx * n[1] * n[2];
+  if ((size_t)c.nspec * 18 * sizeof(cpx<R>) > kSpectrumBytes)
+    return fail(ctx, MP_E_UNSUPPORTED_SIZE,
+                "mp_green_apply_static: grid needs more than the static scratch array "
+                "(18 complex values per half-spectrum point must fit in MP_STATIC_SCRATCH_BYTES - 32 KiB)");
+  c.h = h;
+  c.inv_nvox = 1.0 / (double)c.nvox;
+  for (int j = 0; j < 3; ++j) c.two_pi_over_L[j] = (R)(2.0 * M_PI / ((double)n[j] * h));
+  c.ref.lam = (R)ref[0];
+  c.ref.mu = (R)ref[1];
+  c.ref.kap = (R)ref[2];
+  c.ref.alpha = (R)ref[3];
+  c.ref.beta = (R)ref[4];
+  c.ref.gamma = (R)ref[5];
+  c.spec = reinterpret_cast<cpx<R>*>(b + kTableRegion);
+  c.status = status;
+  AxisPlan<R>* plans[3] = {&c.px, &c.py, &c.pz};
+  // twiddle tables W_N^k = exp(-2 pi i k / N), built on the host stack and copied in
+  static thread_local cpx<R> host_tw[3][kMaxAxis];
+  for (int a = 0; a < 3; ++a) {
+    AxisPlan<R>& p = *plans[a];
+    const bool packed = (a == 0);
+    p.n = n[a];
+    p.m = packed ? (n[a] > 1 ? n[a] / 2 : 1) : n[a];
+    p.tstride = packed ? 2 : 1;
+    radices(p.m, p.radix, p.nstages);
+    for (int k = 0; k < n[a]; ++k) {
+      const double ang = 2.0 * M_PI * (double)k / (double)n[a];
+      host_tw[a][k].x = (R)std::cos(ang);
+      host_tw[a][k].y = (R)(-std::sin(ang));
+    }
+    p.tw = tw[a];
+  }
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+    e = cudaMemcpyAsync(tw[a], host_tw[a], sizeof(cpx<R>) * n[a], cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    int dev = 0, nsm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) {
+      LaunchCfg L = make_launch_cfg<R>(c, nsm > 0 ? nsm : 1);
+      e = launch_green_apply<R>(L, c, (const R*)tau, (const R*)mu, (R*)e_out, (R*)g_out, st);
+    }
+  }
+  int flag = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(ctx, MP_E_CUDA, cudaGetErrorString(e));
+  if (flag) return fail(ctx, MP_E_TIMEOUT, "mp_green_apply_static: a bounded device wait expired");
+  return MP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mp_status mp_green_apply_static(mp_ctx* ctx, int32_t precision, const int32_t n[3], double h,
+                                const double ref_moduli[6], const void* tau, const void* mu,
+                                void* e_out, void* g_out, void* stream) {
+  if (!n || !ref_moduli || !tau || !mu || !e_out || !g_out || (precision != 0 && precision != 1))
+    return fail(ctx, MP_E_INVALID_ARG, "mp_green_apply_static: invalid arguments");
+  for (int j = 0; j < 3; ++j)
+    if (!axis_ok(n[j]))
+      return fail(ctx, MP_E_UNSUPPORTED_SIZE, "mp_green_apply_static: grid size unsupported");
+  if (!(h > 0)) return fail(ctx, MP_E_INVALID_ARG, "mp_green_apply_static: h must be positive");
+  const double* r = ref_moduli;
+  if (!(r[0] + 2 * r[1] > 0) || !(r[1] > 0) || !(r[2] > 0) || !(r[5] >= 0) || !(r[3] + r[4] + r[5] >= 0))
+    return fail(ctx, MP_E_INADMISSIBLE, "mp_green_apply_static: reference medium not admissible");
+  if (!(precision == 0 ? sizes_fit<double>(n[0], n[1], n[2]) : sizes_fit<float>(n[0], n[1], n[2])))
+    return fail(ctx, MP_E_UNSUPPORTED_SIZE, "mp_green_apply_static: grid too large for the tiles");
+  if (ctx && cudaSetDevice(mp_ctx_device(ctx)) != cudaSuccess)
+    return fail(ctx, MP_E_NO_DEVICE, "mp_green_apply_static: cannot select the context's device");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return precision == 0 ? run<double>(ctx, n, h, ref_moduli, tau, mu, e_out, g_out, st)
+                        : run<float>(ctx, n, h, ref_moduli, tau, mu, e_out, g_out, st);
+}
+
+}  // extern "C"

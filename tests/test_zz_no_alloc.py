@@ -1,0 +1,74 @@
+"""The allocation-free Green-operator entry point, mp_green_apply_static.
+
+It serves callers that cannot allocate device memory when they apply the
+operator (a fixed memory budget owned by another runtime, or a loop that must
+not pay cudaMalloc's implicit synchronisation), so it works in a static
+device array instead.  This file checks, through the C ABI, that two calls in
+a row give the same fluctuations as the allocating mp_green_apply (within the
+Green-operator tolerance of the parity tests), that the library allocates no
+device memory during the calls, and that grids beyond the static array are
+refused with a clear error.  It is named to be collected last and passes both
+alone in a fresh process and after the other tests.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+REF = (20.0, 12.0, 3.0, 0.7, 1.1, 1.9)
+
+# The static array itself is materialised when the module holding it is first
+# loaded; with CUDA's lazy module loading that happens inside the first call on
+# a device, once per process.  Any other drop of free device memory during a
+# call would be an allocation.
+_MODULE_LOADED = {"done": False}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2409_10774_gb300 as M
+    return M.Context(0)
+
+
+@pytest.mark.parametrize("precision,n", [(1, (48, 24, 16)), (0, (32, 12, 8)), (1, (16, 16, 16))])
+def test_static_matches_allocating_entry_point_twice(ctx, precision, n):
+    from paper_2409_10774_gb300 import binding as B
+    dt = torch.float64 if precision == 0 else torch.float32
+    tol = 1e-12 if precision == 0 else 2e-6
+    rng = np.random.default_rng(11)
+    shape = (n[2], n[1], n[0], 3, 3)
+    for call in range(2):
+        tau = torch.as_tensor(rng.standard_normal(shape), dtype=dt, device="cuda")
+        mu = torch.as_tensor(rng.standard_normal(shape), dtype=dt, device="cuda")
+        e_ref, g_ref = B.mp_green_apply(ctx, precision, n, 0.5, REF, tau, mu)
+        e_out = torch.empty_like(tau)
+        g_out = torch.empty_like(mu)
+        torch.cuda.synchronize()
+        allocs = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+        free_before = torch.cuda.mem_get_info()[0]
+        e, g = B.mp_green_apply_static(ctx, precision, n, 0.5, REF, tau, mu, e_out, g_out)
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == allocs
+        drop = free_before - torch.cuda.mem_get_info()[0]
+        if drop != 0:
+            assert not _MODULE_LOADED["done"] and 0 < drop <= B.MP_STATIC_SCRATCH_BYTES + (2 << 20), drop
+        _MODULE_LOADED["done"] = True
+        assert e.data_ptr() == e_out.data_ptr() and g.data_ptr() == g_out.data_ptr()
+        for got, ref in ((e, e_ref), (g, g_ref)):
+            got = got.double().cpu().numpy()
+            ref = ref.double().cpu().numpy()
+            assert np.abs(got - ref).max() <= tol * 10 * np.abs(ref).max(), (call, precision, n)
+
+
+def test_static_rejects_grids_beyond_the_array(ctx):
+    from paper_2409_10774_gb300 import binding as B
+    n = (64, 64, 64)  # FP32 half spectrum of 64^3 needs 37.7 MB of scratch
+    tau = torch.zeros((64, 64, 64, 3, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(B.MicropolarError) as ei:
+        B.mp_green_apply_static(ctx, 1, n, 1.0, REF, tau, tau.clone())
+    assert ei.value.status == 3
+    assert "static scratch" in str(ei.value)

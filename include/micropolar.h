@@ -185,6 +185,60 @@ mp_status mp_rve_profile(mp_rve* rve, int32_t enable);
  * reset != 0 zeroes both afterwards. */
 mp_status mp_rve_profile_read(const mp_rve* rve, double* ms, int64_t* launches, int32_t reset);
 
+/* Batched solves -----------------------------------------------------------
+ * mp_batch_solve solves `count` independent cell problems (each its own
+ * grid, phases, load path, tolerance and precision) together: every round
+ * runs one fixed-point iteration of Algorithm 2 for every cell still
+ * iterating, in launches shared by all of them, and each cell leaves its
+ * loop, commits and starts its next increment on its own error (eq. err).
+ * A cell's results are identical (bit for bit) whichever cells it shares the
+ * batch with; they equal mp_solve's up to the summation order of the
+ * error and homogenized-average reductions.  results[i] receives problem i's
+ * outputs as mp_solve would write them (results may be NULL for none);
+ * per_item[i] (may be NULL) its status.  Returns MP_OK when every problem
+ * succeeded, else the status of the first that failed (message from
+ * mp_last_error(ctx)).  Device memory for each cell is taken from the
+ * context's allocator when the cell is admitted and released when it ends;
+ * cells that do not fit wait until earlier ones finish. */
+mp_status mp_batch_solve(mp_ctx* ctx, const mp_problem* const* problems, int32_t count,
+                         mp_result* results, mp_status* per_item, void* stream);
+
+/* Serving (continuous batching) ---------------------------------------------
+ * A server owns one block of device memory (its HBM budget), one stream and
+ * one worker thread.  mp_server_submit (thread-safe) validates and copies a
+ * problem and queues it; the worker admits queued requests in arrival order
+ * whenever the request's device footprint fits the free part of the budget
+ * (and fewer than max_resident are resident), and runs rounds of the batched
+ * engine above over all resident requests, so requests that arrive while
+ * others are on the GPU join the running rounds.  A request's state stays in
+ * device memory from admission to completion; its results are written to the
+ * mp_result given at submission (which must stay valid until mp_server_wait
+ * returns for its ticket), and results are identical to those of the same
+ * request solved alone through mp_batch_solve.  mp_server_wait blocks until
+ * the request ends (timeout_ms < 0: no limit) and returns its status, or
+ * MP_E_TIMEOUT if it has not ended within timeout_ms (the ticket stays
+ * valid); each ticket is waited for successfully once.  mp_server_destroy
+ * cancels queued and resident requests (MP_E_CANCELLED) and frees the
+ * server; no other call may be in progress on the server then.  Messages of
+ * the server calls are the calling thread's: mp_last_error(NULL). */
+typedef struct mp_server mp_server;
+typedef struct mp_server_opts {
+  size_t hbm_budget_bytes;  /* device bytes for resident requests; 0 = half of the free memory */
+  int32_t max_resident;     /* most requests resident at once; <= 0 means 1024              */
+  int32_t reserved;
+} mp_server_opts;
+typedef struct mp_server_stats {
+  int64_t submitted, completed, queued, resident, peak_resident;
+  int64_t rounds, voxel_iters;
+  size_t budget_bytes, resident_bytes;
+} mp_server_stats;
+mp_status mp_server_create(mp_ctx* ctx, const mp_server_opts* opts, mp_server** server);
+mp_status mp_server_submit(mp_server* server, const mp_problem* problem, mp_result* result,
+                           uint64_t* ticket);
+mp_status mp_server_wait(mp_server* server, uint64_t ticket, int32_t timeout_ms);
+mp_status mp_server_query(mp_server* server, mp_server_stats* stats);
+void mp_server_destroy(mp_server* server);
+
 /* Hot-path components on device buffers -----------------------------------
  * Real type of tensor buffers: double for precision 0, float for 1.
  *

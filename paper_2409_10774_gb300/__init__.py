@@ -10,7 +10,9 @@ from .binding import (  # noqa: F401
     Context,
     MicropolarError,
     Rve,
+    Server,
     mp_abi_version,
+    mp_batch_solve,
     mp_green_apply,
     mp_radial_return,
     mp_rve_create,
@@ -18,5 +20,5 @@ from .binding import (  # noqa: F401
     mp_validate,
 )
 
-__all__ = ["Context", "MicropolarError", "Rve", "mp_abi_version", "mp_green_apply",
-           "mp_radial_return", "mp_rve_create", "mp_solve", "mp_validate"]
+__all__ = ["Context", "MicropolarError", "Rve", "Server", "mp_abi_version", "mp_batch_solve",
+           "mp_green_apply", "mp_radial_return", "mp_rve_create", "mp_solve", "mp_validate"]

@@ -29,7 +29,9 @@ REF_KIND = {"mean": 0, "midrange": 1, "explicit": 2}
 EXPORTED = ("mp_abi_version", "mp_create", "mp_destroy", "mp_last_error", "mp_validate",
             "mp_solve", "mp_rve_create", "mp_rve_run", "mp_rve_results", "mp_rve_reset",
             "mp_rve_steps_done", "mp_rve_iterations", "mp_rve_destroy", "mp_rve_profile",
-            "mp_rve_profile_read", "mp_radial_return", "mp_green_apply", "mp_green_apply_static")
+            "mp_rve_profile_read", "mp_radial_return", "mp_green_apply", "mp_green_apply_static",
+            "mp_batch_solve", "mp_server_create", "mp_server_submit", "mp_server_wait",
+            "mp_server_query", "mp_server_destroy")
 MP_STATIC_SCRATCH_BYTES = 8 * 1024 * 1024
 KERNEL_CLASSES = ("fft_y_fwd", "green_z", "fft_y_inv", "pass_a", "reduce", "start", "commit")
 
@@ -76,6 +78,16 @@ class mp_alloc(C.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
 
 
+class mp_server_opts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_resident", C.c_int32), ("reserved", C.c_int32)]
+
+
+class mp_server_stats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("submitted", "completed", "queued", "resident", "peak_resident",
+                                         "rounds", "voxel_iters")] + \
+               [("budget_bytes", C.c_size_t), ("resident_bytes", C.c_size_t)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
@@ -103,6 +115,12 @@ def _load():
         "mp_green_apply": (C.c_int, [V, C.c_int32, P(C.c_int32), C.c_double, P(C.c_double), V, V, V, V, V]),
         "mp_green_apply_static": (C.c_int, [V, C.c_int32, P(C.c_int32), C.c_double, P(C.c_double), V, V, V, V,
                                             V]),
+        "mp_batch_solve": (C.c_int, [V, P(P(mp_problem)), C.c_int32, P(mp_result), P(C.c_int), V]),
+        "mp_server_create": (C.c_int, [V, P(mp_server_opts), P(V)]),
+        "mp_server_submit": (C.c_int, [V, P(mp_problem), P(mp_result), P(C.c_uint64)]),
+        "mp_server_wait": (C.c_int, [V, C.c_uint64, C.c_int32]),
+        "mp_server_query": (C.c_int, [V, P(mp_server_stats)]),
+        "mp_server_destroy": (None, [V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -445,3 +463,102 @@ def mp_green_apply_static(ctx, precision, n, h, ref_moduli, tau, mu, e_out=None,
     if st != MP_OK:
         raise MicropolarError(st, ctx.error())
     return e_out, g_out
+
+
+# ---------------------------------------------------------------- batched solves and serving
+
+def _per_item(value, count):
+    if isinstance(value, (list, tuple)):
+        if len(value) != count:
+            raise ValueError("per-problem argument list has the wrong length")
+        return list(value)
+    return [value] * count
+
+
+def mp_batch_solve(ctx, problems, precision=None, fields=False, lockstep_iters=None, div_limit=0.0,
+                   stream=None):
+    """Solve many cells together (mp_batch_solve).  `precision`, `fields`,
+    `lockstep_iters` and `div_limit` are one value for all problems or a list
+    with one entry per problem.  Returns one result dict per problem, shaped
+    like mp_solve's, each with its own 'status'."""
+    count = len(problems)
+    precs = _per_item(precision, count)
+    fl = _per_item(fields, count)
+    locks = lockstep_iters if (isinstance(lockstep_iters, (list, tuple)) and lockstep_iters
+                               and not np.isscalar(lockstep_iters[0])) else [lockstep_iters] * count
+    divs = _per_item(div_limit, count)
+    prs = [_Problem(p, precs[i], locks[i], divs[i]) for i, p in enumerate(problems)]
+    rss = [_Result(pr.n, pr.n_steps, fl[i]) for i, pr in enumerate(prs)]
+    parr = (C.POINTER(mp_problem) * max(count, 1))(*[C.pointer(pr.st) for pr in prs])
+    rarr = (mp_result * max(count, 1))()
+    for i, rs in enumerate(rss):
+        rarr[i] = rs.st
+    status = (C.c_int * max(count, 1))()
+    st = LIB.mp_batch_solve(ctx.ptr, parr, count, rarr, status, _stream_handle(stream))
+    if st == 1 and count and all(status[i] == 0 for i in range(count)):
+        raise MicropolarError(st, ctx.error())
+    out = []
+    for i, rs in enumerate(rss):
+        rs.st = rarr[i]
+        out.append(rs.to_dict(status[i]))
+    return out
+
+
+class Server:
+    """mp_server_*: continuous-batching solve server on one device."""
+
+    def __init__(self, ctx, budget_bytes=0, max_resident=0):
+        self.ctx = ctx
+        opts = mp_server_opts(int(budget_bytes), int(max_resident), 0)
+        self.ptr = C.c_void_p()
+        st = LIB.mp_server_create(ctx.ptr, C.byref(opts), C.byref(self.ptr))
+        if st != MP_OK:
+            raise MicropolarError(st, ctx.error())
+        self._pending = {}
+
+    def submit(self, problem, precision=None, fields=False, lockstep_iters=None, div_limit=0.0):
+        pr = _Problem(problem, precision, lockstep_iters, div_limit)
+        rs = _Result(pr.n, pr.n_steps, fields)
+        ticket = C.c_uint64()
+        st = LIB.mp_server_submit(self.ptr, C.byref(pr.st), C.byref(rs.st), C.byref(ticket))
+        if st != MP_OK:
+            raise MicropolarError(st, last_error(None))
+        self._pending[ticket.value] = rs
+        return ticket.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        """Result dict of `ticket` (its 'status' names the outcome); raises
+        MicropolarError(MP_E_TIMEOUT) when it has not ended in time."""
+        st = LIB.mp_server_wait(self.ptr, C.c_uint64(ticket), int(timeout_ms))
+        if st == 8 and ticket in self._pending:
+            # either the wait expired or the solve itself timed out on the device
+            msg = last_error(None)
+            if "not finished within" in msg:
+                raise MicropolarError(st, msg)
+        if st == 1:
+            raise MicropolarError(st, last_error(None))
+        rs = self._pending.pop(ticket)
+        return rs.to_dict(st)
+
+    def stats(self):
+        s = mp_server_stats()
+        LIB.mp_server_query(self.ptr, C.byref(s))
+        return {k: getattr(s, k) for k, _ in mp_server_stats._fields_}
+
+    def close(self):
+        if self.ptr:
+            LIB.mp_server_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+            self._pending.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

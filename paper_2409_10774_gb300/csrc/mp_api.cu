@@ -8,24 +8,19 @@
 #include <vector>
 
 #include "../../include/micropolar.h"
+#include "mp_host.cuh"
 #include "mp_kernels.cuh"
 
 using namespace mp;
 
-struct mp_ctx {
-  int device = 0;
-  int nsm = 1;
-  mp_alloc alloc{};
-  bool has_alloc = false;
-  std::string last_error;
-};
+// Context accessor for the static-scratch entry point (mp_static.cu); not exported.
+MP_HIDDEN int mp_ctx_device(const mp_ctx* ctx) { return ctx ? ctx->device : 0; }
 
-// Context accessors for the static-scratch entry point (mp_static.cu); not exported.
-__attribute__((visibility("hidden"))) int mp_ctx_device(const mp_ctx* ctx) { return ctx ? ctx->device : 0; }
+namespace mp {
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
 
 mp_status set_error(mp_ctx* ctx, mp_status st, const char* fmt, ...) {
   char buf[512];
@@ -38,28 +33,15 @@ mp_status set_error(mp_ctx* ctx, mp_status st, const char* fmt, ...) {
   return st;
 }
 
-}  // namespace
+const char* last_error_global() { return g_last_error.c_str(); }
 
-__attribute__((visibility("hidden"))) void mp_ctx_set_error(mp_ctx* ctx, const char* msg) {
-  set_error(ctx, MP_E_INVALID_ARG, "%s", msg);
-}
+}  // namespace mp
 
-namespace {
+MP_HIDDEN void mp_ctx_set_error(mp_ctx* ctx, const char* msg) { set_error(ctx, MP_E_INVALID_ARG, "%s", msg); }
 
-#define MP_CK(ctx, call)                                                                      \
-  do {                                                                                        \
-    cudaError_t _e = (call);                                                                  \
-    if (_e != cudaSuccess)                                                                    \
-      return set_error((ctx), _e == cudaErrorMemoryAllocation ? MP_E_OOM : MP_E_CUDA,          \
-                       "%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__, __LINE__); \
-  } while (0)
+namespace mp {
 
 // ------------------------------------------------------------------ device memory
-struct DevBuf {
-  void* ptr = nullptr;
-  size_t bytes = 0;
-};
-
 mp_status dalloc(mp_ctx* ctx, DevBuf& b, size_t bytes) {
   b.bytes = bytes;
   b.ptr = nullptr;
@@ -86,7 +68,7 @@ void dfree(mp_ctx* ctx, DevBuf& b) {
 }
 
 // ------------------------------------------------------------------ validation
-bool size_ok(int n) {
+static bool size_ok(int n) {
   if (n == 1) return true;
   if (n < 2 || n > 512 || (n % 2) != 0) return false;
   while (n % 2 == 0) n /= 2;
@@ -94,7 +76,7 @@ bool size_ok(int n) {
   return n == 1;
 }
 
-bool finite(double v) { return std::isfinite(v); }
+static bool finite(double v) { return std::isfinite(v); }
 
 mp_status check_phase(const mp_phase& ph, int idx, std::string& msg) {
   const double v[12] = {ph.lambda, ph.mu, ph.kappa, ph.alpha, ph.beta, ph.gamma,
@@ -123,7 +105,7 @@ mp_status check_phase(const mp_phase& ph, int idx, std::string& msg) {
 }
 
 // Reference medium (6 moduli) over the phases present in the map.
-mp_status reference_moduli(const mp_problem* p, const std::vector<long long>& counts, long long nvox,
+static mp_status reference_moduli(const mp_problem* p, const std::vector<long long>& counts, long long nvox,
                            double ref[6], std::string& msg) {
   if (p->ref_kind == MP_REF_EXPLICIT) {
     if (!p->ref_moduli) {
@@ -256,7 +238,7 @@ mp_status validate_problem(const mp_problem* p, std::vector<long long>* counts_o
 }
 
 // ------------------------------------------------------------------ plans and tables
-void radix_plan(int m, int* radix, int& nst) {
+void radix_plan(int m, int* radix, int& nst, bool allow16) {
   nst = 0;
   int k2 = 0;
   while (m % 2 == 0) {
@@ -268,34 +250,21 @@ void radix_plan(int m, int* radix, int& nst) {
     m /= 3;
     ++k3;
   }
-  while (k2 >= 3 && k2 - 3 != 1) {
-    radix[nst++] = 8;
-    k2 -= 3;
-  }
-  if (k2 == 4) {
-    radix[nst++] = 4;
-    radix[nst++] = 4;
-  } else if (k2 == 2) {
-    radix[nst++] = 4;
-  } else if (k2 == 1) {
-    radix[nst++] = 2;
-  }
+  // powers of two: as few stages as possible, radix 16 only where it saves one
+  // (the x axis, transformed inside pass A, is limited to radix 8)
+  static const int kPlan2[10][4] = {{0}, {2}, {4}, {8}, {16}, {8, 4}, {8, 8}, {16, 8}, {16, 16}, {8, 8, 8}};
+  static const int kPlan2x[10][4] = {{0}, {2}, {4}, {8}, {4, 4}, {8, 4}, {8, 8}, {8, 4, 4}, {8, 8, 4}, {8, 8, 8}};
+  static const int kLen2[10] = {0, 1, 1, 1, 1, 2, 2, 2, 2, 3};
+  static const int kLen2x[10] = {0, 1, 1, 1, 2, 2, 2, 3, 3, 3};
+  const int len = allow16 ? kLen2[k2] : kLen2x[k2];
+  for (int i = 0; i < len; ++i) radix[nst++] = allow16 ? kPlan2[k2][i] : kPlan2x[k2][i];
   for (int i = 0; i < k3; ++i) radix[nst++] = 3;
 }
 
 template <class R>
 mp_status make_axis(mp_ctx* ctx, int n, bool packed, AxisPlan<R>& p, DevBuf& tw, cudaStream_t st,
                     std::vector<cpx<R>>& host_tw) {
-  p.n = n;
-  p.m = packed ? (n > 1 ? n / 2 : 1) : n;
-  p.tstride = packed ? 2 : 1;
-  radix_plan(p.m, p.radix, p.nstages);
-  host_tw.resize(n);
-  for (int k = 0; k < n; ++k) {
-    const double a = 2.0 * M_PI * (double)k / (double)n;
-    host_tw[k].x = (R)std::cos(a);
-    host_tw[k].y = (R)(-std::sin(a));
-  }
+  axis_tables<R>(n, packed, p, host_tw);
   mp_status s = dalloc(ctx, tw, sizeof(cpx<R>) * n);
   if (s != MP_OK) return s;
   MP_CK(ctx, cudaMemcpyAsync(tw.ptr, host_tw.data(), sizeof(cpx<R>) * n, cudaMemcpyHostToDevice, st));
@@ -303,45 +272,12 @@ mp_status make_axis(mp_ctx* ctx, int n, bool packed, AxisPlan<R>& p, DevBuf& tw,
   return MP_OK;
 }
 
-template <class R>
-PhaseDev<R> phase_dev(const mp_phase& ph) {
-  PhaseDev<R> d{};
-  d.lam = (R)ph.lambda;
-  d.mu = (R)ph.mu;
-  d.kap = (R)ph.kappa;
-  d.alpha = (R)ph.alpha;
-  d.beta = (R)ph.beta;
-  d.gamma = (R)ph.gamma;
-  d.a1 = (R)ph.a1;
-  d.a2 = (R)(ph.a1 * ph.mu / ph.kappa);               // Alg. 1: a2 = a1 mu / kappa
-  d.b1 = (R)ph.b1;
-  d.skew_m = ph.gamma > ph.beta ? 1 : 0;
-  d.b2 = d.skew_m ? (R)(ph.b1 * (ph.gamma + ph.beta) / (ph.gamma - ph.beta)) : (R)0;
-  d.elastic = ph.elastic ? 1 : 0;
-  d.tY = ph.elastic ? INFINITY : ph.tY;
-  d.tH = ph.tH;
-  d.mY = ph.elastic ? INFINITY : ph.mY;
-  d.mH = ph.mH;
-  d.ct = 2.0 * ph.a1 * ph.mu;
-  d.cm = ph.b1 * (ph.gamma + ph.beta);
-  d.inv_t = 1.0 / (ph.tH + d.ct);
-  d.inv_m = 1.0 / (ph.mH + d.cm);
-  return d;
+mp_status use_device(mp_ctx* ctx) {
+  MP_CK(ctx, cudaSetDevice(ctx->device));
+  return MP_OK;
 }
 
-template <class R>
-RefDev<R> ref_dev(const double ref[6]) {
-  RefDev<R> r;
-  r.lam = (R)ref[0];
-  r.mu = (R)ref[1];
-  r.kap = (R)ref[2];
-  r.alpha = (R)ref[3];
-  r.beta = (R)ref[4];
-  r.gamma = (R)ref[5];
-  return r;
-}
-
-}  // namespace
+}  // namespace mp
 
 // ------------------------------------------------------------------ cell state
 struct mp_rve {
@@ -430,6 +366,8 @@ mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
   MP_CK(ctx, cudaMemcpyAsync(r->phases.ptr, ph.data(), sizeof(PhaseDev<R>) * ph.size(),
                              cudaMemcpyHostToDevice, st));
   r->L = make_launch_cfg<R>(c, ctx->nsm);
+  c.rows_a = r->L.rows;
+  c.items_a = r->L.items_a;
   if ((s = dalloc(ctx, r->partials, sizeof(double) * kErrPartials * (size_t)r->L.grid_a)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->avgpart, sizeof(double) * kAvgPartials * (size_t)r->L.grid_v)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->errout, sizeof(double) * 8)) != MP_OK) return s;
@@ -487,7 +425,7 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
     mark(MP_KC_REDUCE, 0);
     MP_CK(ctx, launch_reduce_err<R>(r->L, c, parts, r->err_kind, eout, st));
     mark(MP_KC_REDUCE, 1);
-    MP_CK(ctx, cudaMemcpyAsync(r->err_host, r->errout.ptr, sizeof(double) * 5, cudaMemcpyDeviceToHost, st));
+    MP_CK(ctx, cudaMemcpyAsync(r->err_host, r->errout.ptr, sizeof(double) * 6, cudaMemcpyDeviceToHost, st));
     MP_CK(ctx, cudaStreamSynchronize(st));
     if (ydo) {
       r->launches[MP_KC_FFT_Y_FWD]++;
@@ -523,7 +461,9 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
   const bool predict = (status == MP_OK) && (s < r->n_steps);
   const double ratio =
       predict ? (r->time[s + 1] - r->time[s]) / (r->time[s] - r->time[s - 1]) : 0.0;
-  MP_CK(ctx, launch_commit<R>(r->L, c, predict ? 1 : 0, ratio, reinterpret_cast<double*>(r->avgpart.ptr),
+  c.predict = predict ? 1 : 0;
+  c.ratio = ratio;
+  MP_CK(ctx, launch_commit<R>(r->L, c, reinterpret_cast<double*>(r->avgpart.ptr),
                               reinterpret_cast<double*>(r->steprows.ptr) + (size_t)kAvgPartials * (s - 1),
                               st));
   r->launches[MP_KC_COMMIT] += 2;
@@ -556,11 +496,6 @@ void rve_free(mp_rve* r) {
     }
 }
 
-mp_status use_device(mp_ctx* ctx) {
-  MP_CK(ctx, cudaSetDevice(ctx->device));
-  return MP_OK;
-}
-
 }  // namespace
 
 // ================================================================== C ABI
@@ -569,7 +504,7 @@ extern "C" {
 int32_t mp_abi_version(void) { return MP_ABI_VERSION; }
 
 const char* mp_last_error(const mp_ctx* ctx) {
-  return ctx ? ctx->last_error.c_str() : g_last_error.c_str();
+  return ctx ? ctx->last_error.c_str() : last_error_global();
 }
 
 mp_status mp_validate(const mp_problem* problem, char* message, size_t message_len) {
@@ -639,6 +574,7 @@ mp_status mp_rve_create(mp_ctx* ctx, const mp_problem* p, mp_rve** out, void* st
     delete r;
     return set_error(ctx, MP_E_CUDA, "cudaMallocHost: %s", cudaGetErrorString(e));
   }
+  for (int i = 0; i < 8; ++i) r->err_host[i] = 0.0;
   st = (r->precision == 0) ? rve_setup<double>(r, p, cs) : rve_setup<float>(r, p, cs);
   if (st != MP_OK) {
     rve_free(r);
@@ -870,6 +806,8 @@ mp_status green_apply_impl(mp_ctx* ctx, const int32_t n[3], double h, const doub
   if (st == MP_OK) {
     c.spec = reinterpret_cast<cpx<R>*>(spec.ptr);
     LaunchCfg L = make_launch_cfg<R>(c, ctx->nsm);
+    c.rows_a = L.rows;
+    c.items_a = L.items_a;
     cudaError_t e = launch_green_apply<R>(L, c, (const R*)tau, (const R*)mu, (R*)e_out, (R*)g_out, cs);
     int flag = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, stat.ptr, sizeof(int), cudaMemcpyDeviceToHost, cs);

@@ -46,6 +46,8 @@ struct PhaseDev {
   double tY, tH, mY, mH;                // eq. radius_1 / radius_2 (elastic: +inf yield)
   double ct, cm;                        // 2 a1 mu and b1 (gamma + beta) (eq. trial_stresses2)
   double inv_t, inv_m;                  // 1 / (tH + ct), 1 / (mH + cm)
+  double ct_inv, tH_inv;                // ct / (tH + ct), tH / (tH + ct)
+  double cm_inv, mH_inv;                // cm / (mH + cm), mH / (mH + cm)
   int elastic;
   int skew_m;                           // 1 when gamma > beta (b2 finite, skew part of m live)
 };
@@ -90,6 +92,26 @@ struct CellDev {
   AxisPlan<R> px, py, pz;
   R E[9], G[9];           // prescribed averages of the current step
   int* status;            // device status word: bit 0 = a bounded wait expired
+  // batched (multi-cell) execution
+  int rows_a;             // rows per pass-A work item
+  long long items_a;      // pass-A work items
+  double* ipart;          // [items_a][kErrPartials] per-item error partials
+  double* apart;          // [ceil(nvox / 256)][kAvgPartials] per-chunk commit partials
+  double* avg_out;        // row of this increment's homogenized averages
+  double* err_out;        // [8] error of the last iteration (err, per field, status)
+  int err_kind;           // eq. err metric: 0 = local (max), 1 = average
+  int predict;            // commit: write the next increment's predictor
+  double ratio;           // commit: (t_{n+1} - t_n) / (t_n - t_{n-1})
+};
+
+// The work of one multi-cell launch: entries e = 0..n_act-1 name cells
+// (slots of `cells`); entry e owns global work items pre[e] .. pre[e+1]-1.
+template <class R>
+struct Work {
+  const CellDev<R>* cells;
+  const int* act;
+  const long long* pre;
+  int n_act;
 };
 
 // Number of doubles in one block partial of the iteration error reduction:

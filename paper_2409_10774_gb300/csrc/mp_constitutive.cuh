@@ -20,14 +20,17 @@ namespace mp {
 
 // 1 / sqrt(x) in FP64 for x > 0 by Newton's method on f(y) = 1/y^2 - x,
 // y <- y (3 - x y^2) / 2, from the single-precision hardware estimate
-// (relative error ~1e-7; two steps give ~1e-16).  Arguments outside the
-// single-precision normal range take the FP64 library path.
+// (relative error ~1e-7).  One step leaves ~1e-14, below single precision
+// (enough when the result scales FP32 fields); two steps reach FP64 rounding.
+// Arguments outside the single-precision normal range take the FP64 library path.
+template <int STEPS>
 __device__ __forceinline__ double rsqrt_newton(double x) {
-  if (!(x > 1e-36 && x < 1e36)) return 1.0 / sqrt(x);
-  double y = (double)rsqrtf((float)x);
+  const float xf = (float)x;
+  if (!(xf > 1e-36f && xf < 1e36f)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf(xf);
   const double hx = 0.5 * x;
-  y = y * fma(-hx * y, y, 1.5);
-  y = y * fma(-hx * y, y, 1.5);
+#pragma unroll
+  for (int i = 0; i < STEPS; ++i) y = y * fma(-hx * y, y, 1.5);
   return y;
 }
 
@@ -128,35 +131,39 @@ __device__ __forceinline__ void radial_return(const PhaseDev<R>& P, const R* e, 
   ft = R(1);
   fm = R(1);
   if (!P.elastic) {
+    constexpr int kNewton = sizeof(R) == 4 ? 1 : 2;
     // macro level (eq. equiv_stress on the trial deviator)
     R s[9];
     const R vol = vol_of(t[0], t[4], t[8]);
 #pragma unroll
     for (int i = 0; i < 9; ++i) s[i] = t[i];
     s[0] -= vol; s[4] -= vol; s[8] -= vol;
-    const double teq2 = (double)eq_sq(s, P.a1, P.a2, true);
-    const double R1n = P.tY + P.tH * pn;
-    if (!(teq2 < R1n * R1n)) {          // plastic: t_eq^trial >= t_Y + t_H p_n
-      // eq. trial_stresses2 as p - p_n = (t_eq^trial - R1(p_n)) / (t_H + 2 a1 mu); the
-      // return factor R1 / (R1 + 2 a1 mu (p - p_n)) equals R1 / t_eq^trial, since
-      // R1(p) + 2 a1 mu (p - p_n) = t_eq^trial: no division is needed.
-      const double rinv = rsqrt_newton(teq2);
-      const double teq = teq2 * rinv;
-      const double dp = (teq - R1n) * P.inv_t;
-      p = pn + dp;
-      const double R1 = P.tY + P.tH * p;
-      ft = (R)(R1 * rinv);
+    const R teq2r = eq_sq(s, P.a1, P.a2, true);
+    const double R1n = fma(P.tH, pn, P.tY);
+    {
+      const double teq2 = (double)teq2r;
+      if (!(teq2 < R1n * R1n)) {          // plastic: t_eq^trial >= t_Y + t_H p_n
+        // eq. trial_stresses2: p - p_n = (t_eq^trial - R1(p_n)) / (t_H + 2 a1 mu).
+        // Since R1(p) + 2 a1 mu (p - p_n) = t_eq^trial, the return factor
+        // R1 / (R1 + 2 a1 mu (p - p_n)) = R1(p) / t_eq^trial
+        //   = [2 a1 mu R1(p_n) + t_H t_eq^trial] / [(t_H + 2 a1 mu) t_eq^trial].
+        const double rinv = rsqrt_newton<kNewton>(teq2);
+        const double teq = teq2 * rinv;
+        p = pn + (teq - R1n) * P.inv_t;
+        ft = (R)fma(P.ct_inv * R1n, rinv, P.tH_inv);
+      }
     }
     // micro level (eq. equiv_couple_stress on the trial couple stress)
-    const double meq2 = (double)eq_sq(m, P.b1, P.b2, P.skew_m != 0);
-    const double R2n = P.mY + P.mH * qn;
-    if (!(meq2 < R2n * R2n)) {
-      const double rinv = rsqrt_newton(meq2);
-      const double meq = meq2 * rinv;
-      const double dq = (meq - R2n) * P.inv_m;
-      q = qn + dq;
-      const double R2 = P.mY + P.mH * q;
-      fm = (R)(R2 * rinv);
+    const R meq2r = eq_sq(m, P.b1, P.b2, P.skew_m != 0);
+    const double R2n = fma(P.mH, qn, P.mY);
+    {
+      const double meq2 = (double)meq2r;
+      if (!(meq2 < R2n * R2n)) {
+        const double rinv = rsqrt_newton<kNewton>(meq2);
+        const double meq = meq2 * rinv;
+        q = qn + (meq - R2n) * P.inv_m;
+        fm = (R)fma(P.cm_inv * R2n, rinv, P.mH_inv);
+      }
     }
   }
   assemble(t, m, ft, fm);

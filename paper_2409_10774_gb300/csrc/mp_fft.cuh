@@ -73,6 +73,43 @@ __device__ __forceinline__ void dft8(cpx<R>* v) {
   v[7] = csub(e[3], o3);
 }
 
+// 16-point DFT as 4 x 4: 4-point DFTs over n1 of x[4 n1 + n2], twiddles
+// W_16^(n2 k1), 4-point DFTs over n2; output index k1 + 4 k2.
+template <class R, int DIR>
+__device__ __forceinline__ void dft16(cpx<R>* v) {
+  cpx<R> a[4][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    cpx<R> t[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+    dft4<R, DIR>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) a[n2][k1] = t[k1];
+  }
+  // W_16^m = cos(2 pi m / 16) + DIR i sin(2 pi m / 16), m = n2 k1 in {1, 2, 3, 4, 6, 9}
+  const R c1 = R(0.92387953251128675612818318939679);  // cos(pi/8)
+  const R s1 = R(0.38268343236508977172845998403040);  // sin(pi/8)
+  const R h = R(0.70710678118654752440084436210485);
+  auto rot = [&](cpx<R> x, R cr, R si) {  // x * (cr + DIR i si)
+    return cmake<R>(x.x * cr - DIR * x.y * si, x.y * cr + DIR * x.x * si);
+  };
+  a[1][1] = rot(a[1][1], c1, s1);
+  a[1][2] = rot(a[1][2], h, h);
+  a[1][3] = rot(a[1][3], s1, c1);
+  a[2][1] = rot(a[2][1], h, h);
+  a[2][2] = rot90<R, DIR>(a[2][2]);
+  a[2][3] = rot(a[2][3], -h, h);
+  a[3][1] = rot(a[3][1], s1, c1);
+  a[3][2] = rot(a[3][2], -h, h);
+  a[3][3] = rot(a[3][3], -c1, -s1);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    cpx<R> t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+    dft4<R, DIR>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+  }
+}
+
 // Tiles are stored component-interleaved ("AoS"): element (row rr, point n,
 // component c) of a tile with `rows` rows of M points lives at
 // base[(rr M + n) 18 + c], exactly as the spectral buffer stores a row.  A
@@ -81,13 +118,15 @@ __device__ __forceinline__ void dft8(cpx<R>* v) {
 // values: the stages are free of shared-memory bank conflicts and need no
 // transposition on load or store.
 //
-// One Stockham stage of radix R with Ns = product of the radices already
+// One Stockham stage of radix R (2, 3, 4, 8 or 16) with Ns = product of the radices already
 // applied: butterfly j of a line reads points j + r M / R (r < R), multiplies
 // point r by W_M^(r (j mod Ns) M / (Ns R)), takes the R-point DFT and writes
 // output r to point (j / Ns) Ns R + (j mod Ns) + r Ns.  The last stage leaves
 // natural order (no bit reversal).  The host orders radix-3 stages last, so
 // only those divide by a non-power-of-two Ns.
-template <class R, int DIR>
+// MAXR bounds the radices a kernel instantiates (8 keeps the 16-point
+// butterfly's registers out of kernels that never use it).
+template <class R, int DIR, int MAXR>
 __device__ void stage_aos(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out, int rows, int M,
                           int radix, int Ns, const cpx<R>* __restrict__ tw, int tstride) {
   const int nb = M / radix;
@@ -109,10 +148,10 @@ __device__ void stage_aos(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ ou
     const int kk = ns_pow2 ? (j & (Ns - 1)) : (j % Ns);
     const int jq = ns_pow2 ? (j >> ns_sh) : (j / Ns);
     const cpx<R>* src = in + rr * rs + c;
-    cpx<R> v[8];
+    cpx<R> v[MAXR];
     v[0] = src[j * 18];
 #pragma unroll
-    for (int r = 1; r < 8; ++r) {
+    for (int r = 1; r < MAXR; ++r) {
       if (r < radix) {
         cpx<R> x = src[(j + r * nb) * 18];
         const int e = r * kk * tstep;  // < M
@@ -123,11 +162,14 @@ __device__ void stage_aos(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ ou
       case 2: dft2<R, DIR>(v); break;
       case 3: dft3<R, DIR>(v); break;
       case 4: dft4<R, DIR>(v); break;
-      default: dft8<R, DIR>(v); break;
+      case 8: dft8<R, DIR>(v); break;
+      default:
+        if constexpr (MAXR >= 16) dft16<R, DIR>(v);
+        break;
     }
     cpx<R>* dst = out + rr * rs + c + (jq * Ns * radix + kk) * 18;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r < MAXR; ++r) {
       if (r < radix) dst[r * Ns * 18] = v[r];
     }
   }
@@ -135,13 +177,13 @@ __device__ void stage_aos(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ ou
 
 // Transform every line of an AoS tile; data starts in b0, the result pointer
 // (b0 or b1) is returned.  Ends with a barrier.
-template <class R, int DIR>
+template <class R, int DIR, int MAXR>
 __device__ cpx<R>* tile_fft(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R>& p) {
   cpx<R>* in = b0;
   cpx<R>* out = b1;
   int Ns = 1;
   for (int s = 0; s < p.nstages; ++s) {
-    stage_aos<R, DIR>(in, out, rows, p.m, p.radix[s], Ns, p.tw, p.tstride);
+    stage_aos<R, DIR, MAXR>(in, out, rows, p.m, p.radix[s], Ns, p.tw, p.tstride);
     Ns *= p.radix[s];
     __syncthreads();
     cpx<R>* t = in;

@@ -1,0 +1,119 @@
+// Host-side internals shared by the C-ABI translation units: the context,
+// device buffers, error reporting, problem validation and the per-phase /
+// per-axis tables the kernels read.  Nothing here is exported from the
+// library.
+#pragma once
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/micropolar.h"
+#include "mp_common.cuh"
+
+#define MP_HIDDEN __attribute__((visibility("hidden")))
+
+struct mp_ctx {
+  int device = 0;
+  int nsm = 1;
+  mp_alloc alloc{};
+  bool has_alloc = false;
+  std::string last_error;
+};
+
+namespace mp {
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// Records `fmt` as the last error of `ctx` (and of the calling thread) and returns `st`.
+MP_HIDDEN mp_status set_error(mp_ctx* ctx, mp_status st, const char* fmt, ...);
+MP_HIDDEN const char* last_error_global();
+// Device memory through the context's allocator callbacks, else cudaMalloc.
+MP_HIDDEN mp_status dalloc(mp_ctx* ctx, DevBuf& b, size_t bytes);
+MP_HIDDEN void dfree(mp_ctx* ctx, DevBuf& b);
+MP_HIDDEN mp_status use_device(mp_ctx* ctx);
+// eq. energetic_bounds and the yield parameters of one phase.
+MP_HIDDEN mp_status check_phase(const mp_phase& ph, int idx, std::string& msg);
+// Full problem validation; fills the phase counts and the reference medium.
+MP_HIDDEN mp_status validate_problem(const mp_problem* p, std::vector<long long>* counts_out, double ref[6],
+                                     std::string& msg);
+// Radix sequence of a complex transform of length m (allow16: radix-16 stages).
+MP_HIDDEN void radix_plan(int m, int* radix, int& nst, bool allow16);
+
+}  // namespace mp
+
+#define MP_CK(ctx, call)                                                                          \
+  do {                                                                                            \
+    cudaError_t _e = (call);                                                                      \
+    if (_e != cudaSuccess)                                                                        \
+      return ::mp::set_error((ctx), _e == cudaErrorMemoryAllocation ? MP_E_OOM : MP_E_CUDA,        \
+                             "%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__, __LINE__); \
+  } while (0)
+
+namespace mp {
+
+// Per-phase constants of Algorithm 1, prepared in FP64.
+template <class R>
+PhaseDev<R> phase_dev(const mp_phase& ph) {
+  PhaseDev<R> d{};
+  d.lam = (R)ph.lambda;
+  d.mu = (R)ph.mu;
+  d.kap = (R)ph.kappa;
+  d.alpha = (R)ph.alpha;
+  d.beta = (R)ph.beta;
+  d.gamma = (R)ph.gamma;
+  d.a1 = (R)ph.a1;
+  d.a2 = (R)(ph.a1 * ph.mu / ph.kappa);  // Alg. 1: a2 = a1 mu / kappa
+  d.b1 = (R)ph.b1;
+  d.skew_m = ph.gamma > ph.beta ? 1 : 0;
+  d.b2 = d.skew_m ? (R)(ph.b1 * (ph.gamma + ph.beta) / (ph.gamma - ph.beta)) : (R)0;
+  d.elastic = ph.elastic ? 1 : 0;
+  d.tY = ph.elastic ? INFINITY : ph.tY;
+  d.tH = ph.tH;
+  d.mY = ph.elastic ? INFINITY : ph.mY;
+  d.mH = ph.mH;
+  d.ct = 2.0 * ph.a1 * ph.mu;
+  d.cm = ph.b1 * (ph.gamma + ph.beta);
+  d.inv_t = 1.0 / (ph.tH + d.ct);
+  d.inv_m = 1.0 / (ph.mH + d.cm);
+  d.ct_inv = d.ct / (ph.tH + d.ct);
+  d.tH_inv = ph.tH / (ph.tH + d.ct);
+  d.cm_inv = d.cm / (ph.mH + d.cm);
+  d.mH_inv = ph.mH / (ph.mH + d.cm);
+  return d;
+}
+
+template <class R>
+RefDev<R> ref_dev(const double ref[6]) {
+  RefDev<R> r;
+  r.lam = (R)ref[0];
+  r.mu = (R)ref[1];
+  r.kap = (R)ref[2];
+  r.alpha = (R)ref[3];
+  r.beta = (R)ref[4];
+  r.gamma = (R)ref[5];
+  return r;
+}
+
+// FFT plan of one axis and its twiddle table W_N^k = exp(-2 pi i k / N),
+// k < N, computed in FP64 (p.tw is left for the caller to point at the
+// device copy of host_tw).
+template <class R>
+void axis_tables(int n, bool packed, AxisPlan<R>& p, std::vector<cpx<R>>& host_tw) {
+  p.n = n;
+  p.m = packed ? (n > 1 ? n / 2 : 1) : n;
+  p.tstride = packed ? 2 : 1;
+  radix_plan(p.m, p.radix, p.nstages, !packed);
+  host_tw.resize(n);
+  for (int k = 0; k < n; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)n;
+    host_tw[k].x = (R)std::cos(a);
+    host_tw[k].y = (R)(-std::sin(a));
+  }
+  p.tw = nullptr;
+}
+
+}  // namespace mp

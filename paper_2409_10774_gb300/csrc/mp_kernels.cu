@@ -45,7 +45,15 @@ __device__ __forceinline__ R signed_freq_scale(int k, int n, R two_pi_over_L) {
 // (16 K each), so with 2 blocks per SM (4 warps per sub-partition) a thread
 // may use up to 128 registers; a 9-warp block would cap it at 96.
 constexpr int kThreads = 256;
-constexpr size_t kSmemBudget = 227 * 1024;  // dynamic shared memory per block (sm_103a opt-in maximum)
+// The y / z column passes: 18 components x 16 butterflies per round (a radix-16
+// stage of a 256-point line is exactly one round); their registers stay low.
+constexpr int kThreadsYZ = 288;
+// Shared memory per block on sm_103a (opt-in maximum) and the part of it the
+// dynamic tiles may use: the multi-cell kernels also hold a cell descriptor
+// and a few reduction words in static shared memory.
+constexpr size_t kSmemOptin = 227 * 1024;
+constexpr size_t kSmemStaticReserve = 1024;
+constexpr size_t kSmemBudget = kSmemOptin - kSmemStaticReserve;
 
 // Cooperative copy of one tile column: `n` chunks of 18 complex values, chunk
 // i at g + i * stride (complex units), into / out of a contiguous AoS tile.
@@ -61,80 +69,141 @@ __device__ __forceinline__ void copy_column(cpx<R>* tile, cpx<R>* g, int n, long
   }
 }
 
+// ------------------------------------------------------------------ multi-cell plumbing
+// Entry owning global item g: the last e with pre[e] <= g (binary search).
+__device__ __forceinline__ int find_entry(const long long* pre, int n, long long g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Cooperative copy of a cell descriptor into shared memory (callers fence with
+// barriers on both sides).
+template <class R>
+__device__ __forceinline__ void load_cell(CellDev<R>& dst, const CellDev<R>* src) {
+  static_assert(sizeof(CellDev<R>) % 4 == 0, "descriptor size");
+  const int* s4 = reinterpret_cast<const int*>(src);
+  int* d4 = reinterpret_cast<int*>(&dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(CellDev<R>) / 4); i += blockDim.x) d4[i] = s4[i];
+}
+
+// Runs `body(cell, local_item)` over a launch's items: the single cell `c0`
+// (items 0..n0-1), or, for MULTI, every entry of `w` with its cell staged in
+// shared memory `cs` (reloaded when a block moves to the next cell).
+template <class R, bool MULTI, class Body>
+__device__ __forceinline__ void for_items(const CellDev<R>& c0, long long n0, const Work<R>& w,
+                                          CellDev<R>& cs, Body body) {
+  if constexpr (!MULTI) {
+    for (long long g = blockIdx.x; g < n0; g += gridDim.x) body(c0, g);
+  } else {
+    // contiguous ranges: a block's consecutive items mostly share a cell
+    const long long total = w.pre[w.n_act];
+    const long long per = (total + gridDim.x - 1) / gridDim.x;
+    const long long g0 = (long long)blockIdx.x * per;
+    const long long g1 = (g0 + per < total) ? g0 + per : total;
+    if (g0 >= g1) return;
+    int e = find_entry(w.pre, w.n_act, g0);
+    int cur = -1;
+    for (long long g = g0; g < g1; ++g) {
+      while (g >= w.pre[e + 1]) ++e;
+      const int slot = w.act[e];
+      if (slot != cur) {
+        __syncthreads();
+        load_cell(cs, w.cells + slot);
+        __syncthreads();
+        cur = slot;
+      }
+      body(cs, g - w.pre[e]);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ y pass
 // One tile = one (kz, kx) column: 18 lines of length N2.
 template <class R, int DIR>
-__global__ void __launch_bounds__(kThreads) k_fft_y(CellDev<R> c) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem_raw);
+__device__ __forceinline__ void fft_y_tile(const CellDev<R>& c, long long tile, unsigned char* smem) {
+  cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem);
   const int N = c.n2;
   cpx<R>* b1 = b0 + 18 * N;
-  const long long ntiles = (long long)c.n3 * c.kx;
   const long long stride = (long long)c.kx * 18;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int kz = (int)(tile / c.kx);
-    const int kx = (int)(tile - (long long)kz * c.kx);
-    cpx<R>* g = c.spec + ((long long)kz * N * c.kx + kx) * 18;
-    copy_column<R, true>(b0, g, N, stride);
-    __syncthreads();
-    cpx<R>* r = tile_fft<R, DIR>(b0, b1, 1, c.py);
-    copy_column<R, false>(r, g, N, stride);
-    __syncthreads();
-  }
+  const int kz = (int)(tile / c.kx);
+  const int kx = (int)(tile - (long long)kz * c.kx);
+  cpx<R>* g = c.spec + ((long long)kz * N * c.kx + kx) * 18;
+  copy_column<R, true>(b0, g, N, stride);
+  __syncthreads();
+  cpx<R>* r = tile_fft<R, DIR, 16>(b0, b1, 1, c.py);
+  copy_column<R, false>(r, g, N, stride);
+  __syncthreads();
+}
+
+template <class R, int DIR, bool MULTI>
+__global__ void __launch_bounds__(kThreadsYZ) k_fft_y(CellDev<R> c0, Work<R> w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ CellDev<R> cs;
+  for_items<R, MULTI>(c0, (long long)c0.n3 * c0.kx, w, cs,
+                      [&](const CellDev<R>& c, long long t) { fft_y_tile<R, DIR>(c, t, smem_raw); });
 }
 
 // ------------------------------------------------------------------ z pass + Green
 // One tile = one (ky, kx) column: 18 lines of length N3.
 template <class R>
-__global__ void __launch_bounds__(kThreads) k_green_z(CellDev<R> c) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem_raw);
+__device__ __forceinline__ void green_z_tile(const CellDev<R>& c, long long tile, unsigned char* smem) {
+  cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem);
   const int N = c.n3;
   cpx<R>* b1 = b0 + 18 * N;
-  const long long ntiles = (long long)c.n2 * c.kx;
   const long long stride = (long long)c.n2 * c.kx * 18;
   const R scale = (R)c.inv_nvox;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int ky = (int)(tile / c.kx);
-    const int kx = (int)(tile - (long long)ky * c.kx);
-    cpx<R>* g = c.spec + ((long long)ky * c.kx + kx) * 18;
-    const bool ny_nyq = (c.n2 % 2 == 0) && (ky == c.n2 / 2);
-    if (ny_nyq) {  // the whole column is on the Nyquist plane of y: zero fluctuation
-      constexpr int W = 18 * (int)sizeof(cpx<R>) / 16;
-      for (int i = threadIdx.x; i < N * W; i += blockDim.x) {
-        const int row = i / W, w = i - row * W;
-        reinterpret_cast<float4*>(g + row * stride)[w] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-      continue;  // uniform across the block
+  const int ky = (int)(tile / c.kx);
+  const int kx = (int)(tile - (long long)ky * c.kx);
+  cpx<R>* g = c.spec + ((long long)ky * c.kx + kx) * 18;
+  const bool ny_nyq = (c.n2 % 2 == 0) && (ky == c.n2 / 2);
+  if (ny_nyq) {  // the whole column is on the Nyquist plane of y: zero fluctuation
+    constexpr int W = 18 * (int)sizeof(cpx<R>) / 16;
+    for (int i = threadIdx.x; i < N * W; i += blockDim.x) {
+      const int row = i / W, w = i - row * W;
+      reinterpret_cast<float4*>(g + row * stride)[w] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    copy_column<R, true>(b0, g, N, stride);
-    __syncthreads();
-    cpx<R>* r = tile_fft<R, -1>(b0, b1, 1, c.pz);
-    const R x1 = c.n1 == 1 ? R(0) : c.two_pi_over_L[0] * (R)kx;
-    const R x2 = signed_freq_scale<R>(ky, c.n2, c.two_pi_over_L[1]);
-    for (int kz = threadIdx.x; kz < N; kz += blockDim.x) {
-      cpx<R> v[18];
-      cpx<R>* pt = r + kz * 18;
-#pragma unroll
-      for (int q = 0; q < 18; ++q) v[q] = pt[q];
-      const bool nz_nyq = (N % 2 == 0) && (kz == N / 2);
-      const bool zero = (kx == 0 && ky == 0 && kz == 0);
-      if (nz_nyq || zero) {
-#pragma unroll
-        for (int q = 0; q < 18; ++q) v[q] = cmake<R>(R(0), R(0));
-      } else {
-        const R x3 = signed_freq_scale<R>(kz, N, c.two_pi_over_L[2]);
-        green_point<R>(c.ref, x1, x2, x3, v, scale);
-      }
-#pragma unroll
-      for (int q = 0; q < 18; ++q) pt[q] = v[q];
-    }
-    __syncthreads();
-    cpx<R>* other = (r == b0) ? b1 : b0;
-    cpx<R>* o = tile_fft<R, +1>(r, other, 1, c.pz);
-    copy_column<R, false>(o, g, N, stride);
-    __syncthreads();
+    return;  // uniform across the block
   }
+  copy_column<R, true>(b0, g, N, stride);
+  __syncthreads();
+  cpx<R>* r = tile_fft<R, -1, 16>(b0, b1, 1, c.pz);
+  const R x1 = c.n1 == 1 ? R(0) : c.two_pi_over_L[0] * (R)kx;
+  const R x2 = signed_freq_scale<R>(ky, c.n2, c.two_pi_over_L[1]);
+  for (int kz = threadIdx.x; kz < N; kz += blockDim.x) {
+    cpx<R> v[18];
+    cpx<R>* pt = r + kz * 18;
+#pragma unroll
+    for (int q = 0; q < 18; ++q) v[q] = pt[q];
+    const bool nz_nyq = (N % 2 == 0) && (kz == N / 2);
+    const bool zero = (kx == 0 && ky == 0 && kz == 0);
+    if (nz_nyq || zero) {
+#pragma unroll
+      for (int q = 0; q < 18; ++q) v[q] = cmake<R>(R(0), R(0));
+    } else {
+      const R x3 = signed_freq_scale<R>(kz, N, c.two_pi_over_L[2]);
+      green_point<R>(c.ref, x1, x2, x3, v, scale);
+    }
+#pragma unroll
+    for (int q = 0; q < 18; ++q) pt[q] = v[q];
+  }
+  __syncthreads();
+  cpx<R>* other = (r == b0) ? b1 : b0;
+  cpx<R>* o = tile_fft<R, +1, 16>(r, other, 1, c.pz);
+  copy_column<R, false>(o, g, N, stride);
+  __syncthreads();
+}
+
+template <class R, bool MULTI>
+__global__ void __launch_bounds__(kThreadsYZ, 2) k_green_z(CellDev<R> c0, Work<R> w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ CellDev<R> cs;
+  for_items<R, MULTI>(c0, (long long)c0.n2 * c0.kx, w, cs,
+                      [&](const CellDev<R>& c, long long t) { green_z_tile<R>(c, t, smem_raw); });
 }
 
 // ------------------------------------------------------------------ x pass (pass A)
@@ -146,14 +215,16 @@ __global__ void __launch_bounds__(kThreads) k_green_z(CellDev<R> c) {
 // real for a real row and its imaginary part is ignored).  Tiles are AoS:
 // point k of line (rr, c) at [(rr M + k) 18 + c].
 
+__device__ __forceinline__ int div_m(int q, int M, int msh) { return msh >= 0 ? (q >> msh) : (q / M); }
+
 template <class R>
-__device__ __forceinline__ void x_inverse_pre(const cpx<R>* X, cpx<R>* Z, int rows, int M,
+__device__ __forceinline__ void x_inverse_pre(const cpx<R>* X, cpx<R>* Z, int rows, int M, int msh,
                                               const cpx<R>* tw) {
   const int total = rows * M * 18;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int c = idx % 18;
     const int q = idx / 18;          // rr * M + k
-    const int rr = q / M, k = q - rr * M;
+    const int rr = div_m(q, M, msh), k = q - rr * M;
     const cpx<R>* x = X + rr * M * 18 + c;
     cpx<R> a = x[k * 18];
     if (k == 0) a.y = R(0);
@@ -165,13 +236,13 @@ __device__ __forceinline__ void x_inverse_pre(const cpx<R>* X, cpx<R>* Z, int ro
 }
 
 template <class R>
-__device__ __forceinline__ void x_forward_post(const cpx<R>* Z, cpx<R>* X, int rows, int M,
+__device__ __forceinline__ void x_forward_post(const cpx<R>* Z, cpx<R>* X, int rows, int M, int msh,
                                                const cpx<R>* tw) {
   const int total = rows * M * 18;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int c = idx % 18;
     const int q = idx / 18;
-    const int rr = q / M, k = q - rr * M;
+    const int rr = div_m(q, M, msh), k = q - rr * M;
     const cpx<R>* z = Z + rr * M * 18 + c;
     cpx<R> a = z[k * 18];
     cpx<R> b = cconj(z[(k == 0 ? 0 : M - k) * 18]);
@@ -184,21 +255,25 @@ __device__ __forceinline__ void x_forward_post(const cpx<R>* Z, cpx<R>* X, int r
 
 enum PassMode { kIter = 0, kStart = 1, kXFwd = 2, kXInv = 3 };
 
-// Shared-memory plan of pass A for `rows` rows of N1 voxels.
+// Shared-memory plan of pass A: a fixed header (barriers, reduction scratch,
+// the block's error totals) then the buffers for `rows` rows of N1 voxels.
 template <class R>
 struct PassASmem {
-  size_t fft_bytes, prev_off, hist_off, pq_off, red_off, acc_off, dc_off, bar_off, total;
+  static constexpr size_t bar_off = 0;                                 // 2 mbarriers
+  static constexpr size_t red_off = 64;                                // [16 warps][8] doubles
+  static constexpr size_t acc_off = red_off + 16 * 8 * sizeof(double);  // [kErrPartials]
+  static constexpr size_t head = ((acc_off + kErrPartials * sizeof(double)) + 127) / 128 * 128;
+  size_t fft_bytes, b0_off, b1_off, prev_off, hist_off, pq_off, dc_off, total;
   __host__ __device__ PassASmem(int n1, int rows) {
     const int M = (n1 > 1) ? n1 / 2 : 1;
     const size_t nvi = (size_t)rows * n1;
     fft_bytes = (size_t)rows * M * 18 * sizeof(cpx<R>);  // multiple of 16
-    prev_off = 2 * fft_bytes;
+    b0_off = head;
+    b1_off = b0_off + fft_bytes;
+    prev_off = b1_off + fft_bytes;
     hist_off = prev_off + nvi * 20 * sizeof(R);
     pq_off = hist_off + nvi * 20 * sizeof(R);
-    red_off = pq_off + nvi * 2 * sizeof(double);
-    acc_off = red_off + 16 * 8 * sizeof(double);
-    bar_off = acc_off + kErrPartials * sizeof(double);
-    dc_off = bar_off + 2 * sizeof(uint64_t);
+    dc_off = pq_off + nvi * 2 * sizeof(double);
     total = dc_off + ((18 * (size_t)rows * sizeof(R) + 15) / 16) * 16;
   }
 };
@@ -208,96 +283,79 @@ __device__ __forceinline__ void flag_timeout(int* status) {
   if (threadIdx.x == 0 && status) atomicOr(status, 1);
 }
 
-// Work item = `rows` consecutive rows (y, z) of the cell = a contiguous range
-// of voxels and of spectral rows.  Rows, previous iterate, history and
-// plastic strains of an item move between global and shared memory by bulk
-// asynchronous copies (TMA); the spectral rows are loaded first so that the
-// inverse transform runs while the per-voxel data is still in flight.
+// One pass-A work item: `rows` consecutive rows (y, z) of a cell = a
+// contiguous range of voxels and of spectral rows.  Rows, previous iterate,
+// history and plastic strains move between global and shared memory by bulk
+// asynchronous copies (TMA); the spectral rows are requested first so that the
+// inverse transform runs while the per-voxel records are still in flight.
+// Leaves the item's 8 error maxima / sums in red[0..7] (thread 0..7 views, see
+// below) and its 36 row sums in `itm` (kIter only).  Returns false when a
+// bounded wait expired (uniform across the block).
 template <class R, int MODE>
-__global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
-    k_pass_a(CellDev<R> c, int rows, double* partials, const R* fin_tau, const R* fin_mu, R* fout_e,
-             R* fout_g) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item, unsigned char* smem_raw,
+                                            uint32_t& parity, double* itm, const R* fin_tau,
+                                            const R* fin_mu, R* fout_e, R* fout_g) {
+  const int rows = c.rows_a;
   const int N1 = c.n1;
   const int M = c.kx;                 // complex entries per row (N1 / 2, or 1)
+  const int msh = (M & (M - 1)) == 0 ? __ffs(M) - 1 : -1;
   const bool packed = (N1 > 1);
   const PassASmem<R> L(N1, rows);
-  cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem_raw);
-  cpx<R>* b1 = reinterpret_cast<cpx<R>*>(smem_raw + L.fft_bytes);
+  cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem_raw + L.b0_off);
+  cpx<R>* b1 = reinterpret_cast<cpx<R>*>(smem_raw + L.b1_off);
   R* prev_s = reinterpret_cast<R*>(smem_raw + L.prev_off);
   R* hist_s = reinterpret_cast<R*>(smem_raw + L.hist_off);
   double2* pq_s = reinterpret_cast<double2*>(smem_raw + L.pq_off);
-  double* red = reinterpret_cast<double*>(smem_raw + L.red_off);
-  double* acc = reinterpret_cast<double*>(smem_raw + L.acc_off);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + L.bar_off);
+  double* red = reinterpret_cast<double*>(smem_raw + PassASmem<R>::red_off);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + PassASmem<R>::bar_off);
   R* dcin = reinterpret_cast<R*>(smem_raw + L.dc_off);
   const long long nrows = (long long)c.n2 * c.n3;
-  const long long nitems = (nrows + rows - 1) / rows;
-  const int nwarp = blockDim.x >> 5;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool use_vox = (MODE == kIter || MODE == kStart);
   const bool use_spec_in = (MODE == kIter || MODE == kXInv);
 
+  const long long row0 = item * rows;
+  const int nr = (int)min((long long)rows, nrows - row0);
+  const int nvi = nr * N1;
+  const long long v0 = row0 * N1;
+  // ---------------------------------------------------------- issue loads
   if (threadIdx.x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    fence_barrier_init();
-  }
-  if (MODE == kIter)
-    for (int i = threadIdx.x; i < kErrPartials; i += blockDim.x) acc[i] = 0.0;
-  __syncthreads();
-
-  uint32_t parity = 0;
-  bool failed = false;
-  for (long long item = blockIdx.x; item < nitems; item += gridDim.x, parity ^= 1u) {
-    const long long row0 = item * rows;
-    const int nr = (int)min((long long)rows, nrows - row0);
-    const int nvi = nr * N1;
-    const long long v0 = row0 * N1;
-    // ---------------------------------------------------------- issue loads
-    if (threadIdx.x == 0) {
-      bulk_wait_read();     // the previous item's stores have read shared memory
-      fence_proxy_async();  // and every thread's reads of it precede the new loads
-      if (use_spec_in) {
-        const uint32_t bytes = (uint32_t)(nr * M * 18 * sizeof(cpx<R>));
-        mbar_arrive_expect_tx(&bars[0], bytes);
-        bulk_load(b0, c.spec + row0 * M * 18, bytes, &bars[0]);
-      }
-      if (use_vox) {
-        const uint32_t bp = (uint32_t)(nvi * 20 * sizeof(R));
-        const uint32_t bq = (uint32_t)(nvi * 2 * sizeof(double));
-        mbar_arrive_expect_tx(&bars[1], 2 * bp + bq);
-        bulk_load(prev_s, c.prev + v0 * 20, bp, &bars[1]);
-        bulk_load(hist_s, c.hist + v0 * 20, bp, &bars[1]);
-        bulk_load(pq_s, c.pq + v0 * 2, bq, &bars[1]);
-      }
-    }
-    cpx<R>* zbuf = b0;  // buffer holding the packed real rows
-    // ---------------------------------------------------------- inverse x
+    bulk_wait_read();     // the previous item's stores have read shared memory
+    fence_proxy_async();  // and every thread's reads of it precede the new loads
     if (use_spec_in) {
-      const bool ok = mbar_wait(&bars[0], parity);
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        break;
-      }
-      if (MODE == kIter)
-        for (int l = threadIdx.x; l < 18 * nr; l += blockDim.x) {
-          const int rr = l / 18, cc = l - rr * 18;
-          dcin[cc * rows + rr] = b0[rr * M * 18 + cc].x;
-        }
-      if (packed) {
-        x_inverse_pre<R>(b0, b1, nr, M, c.px.tw);
-        __syncthreads();
-        zbuf = tile_fft<R, +1>(b1, b0, nr, c.px);
-      }
+      const uint32_t bytes = (uint32_t)(nr * M * 18 * sizeof(cpx<R>));
+      mbar_arrive_expect_tx(&bars[0], bytes);
+      bulk_load(b0, c.spec + row0 * M * 18, bytes, &bars[0]);
     }
     if (use_vox) {
-      const bool ok = mbar_wait(&bars[1], parity);
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        break;
-      }
+      const uint32_t bp = (uint32_t)(nvi * 20 * sizeof(R));
+      const uint32_t bq = (uint32_t)(nvi * 2 * sizeof(double));
+      mbar_arrive_expect_tx(&bars[1], 2 * bp + bq);
+      bulk_load(prev_s, c.prev + v0 * 20, bp, &bars[1]);
+      bulk_load(hist_s, c.hist + v0 * 20, bp, &bars[1]);
+      bulk_load(pq_s, c.pq + v0 * 2, bq, &bars[1]);
     }
+  }
+  cpx<R>* zbuf = b0;  // buffer holding the packed real rows
+  // ---------------------------------------------------------- inverse x
+  if (use_spec_in) {
+    const bool ok = mbar_wait(&bars[0], parity);
+    if (__syncthreads_or(!ok)) return false;
+    if (MODE == kIter)
+      for (int l = threadIdx.x; l < 18 * nr; l += blockDim.x) {
+        const int rr = l / 18, cc = l - rr * 18;
+        dcin[cc * rows + rr] = b0[rr * M * 18 + cc].x;
+      }
+    if (packed) {
+      x_inverse_pre<R>(b0, b1, nr, M, msh, c.px.tw);
+      __syncthreads();
+      zbuf = tile_fft<R, +1, 8>(b1, b0, nr, c.px);
+    }
+  }
+  if (use_vox) {
+    const bool ok = mbar_wait(&bars[1], parity);
+    if (__syncthreads_or(!ok)) return false;
+  }
     // ---------------------------------------------------------- per voxel
     R dmax[4] = {R(0), R(0), R(0), R(0)};
     R dsum[4] = {R(0), R(0), R(0), R(0)};
@@ -412,80 +470,127 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
       }
     }
     if (MODE == kXInv) {
-      __syncthreads();
-      continue;
-    }
-    // the new iterate goes back to global memory while the forward transform runs
-    fence_proxy_async();
     __syncthreads();
-    if (use_vox && threadIdx.x == 0) {
-      bulk_store(c.prev + v0 * 20, prev_s, (uint32_t)(nvi * 20 * sizeof(R)));
-      bulk_commit();
-    }
-    // ---------------------------------------------------------- forward x
-    cpx<R>* X;
-    if (packed) {
-      cpx<R>* other = (zbuf == b0) ? b1 : b0;
-      cpx<R>* Z = tile_fft<R, -1>(zbuf, other, nr, c.px);
-      cpx<R>* dst = (Z == b0) ? b1 : b0;
-      x_forward_post<R>(Z, dst, nr, M, c.px.tw);
-      X = dst;
-    } else {
-      X = zbuf;
-    }
-    fence_proxy_async();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      bulk_store(c.spec + row0 * M * 18, X, (uint32_t)(nr * M * 18 * sizeof(cpx<R>)));
-      bulk_commit();
-    }
-    // ---------------------------------------------------------- error partials
-    if (MODE == kIter) {
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const double mx = shfl_max((double)dmax[a]);
-        const double sm = shfl_sum((double)dsum[a]);
-        if (lane == 0) {
-          red[warp * 8 + a] = mx;
-          red[warp * 8 + 4 + a] = sm;
-        }
-      }
-      __syncthreads();
-      if (threadIdx.x < 8) {
-        double a = acc[threadIdx.x];
-        for (int w = 0; w < nwarp; ++w) {
-          const double vv = red[w * 8 + threadIdx.x];
-          a = (threadIdx.x < 4) ? fmax(a, vv) : a + vv;
-        }
-        acc[threadIdx.x] = a;
-      } else if (threadIdx.x >= 32 && threadIdx.x < 32 + 36) {
-        // Row sums.  With the unnormalised inverse along x, sum_x e~ = N1 X_in[0],
-        // so sum_x e = N1 (E + X_in[0]); the forward DC is sum_x tau.
-        const int q = threadIdx.x - 32;
-        double a = 0.0;
-        if (q < 18) {
-          const double mean = (q < 9) ? (double)c.E[q] : (double)c.G[q - 9];
-          for (int rr = 0; rr < nr; ++rr) a += (double)N1 * (mean + (double)dcin[q * rows + rr]);
-        } else {
-          for (int rr = 0; rr < nr; ++rr) a += (double)X[rr * M * 18 + (q - 18)].x;
-        }
-        acc[8 + q] += a;  // each of these threads owns one entry of the CTA total
-      }
-    }
-    __syncthreads();
+    parity ^= 1u;
+    return true;
   }
+  // the new iterate goes back to global memory while the forward transform runs
+  fence_proxy_async();
+  __syncthreads();
+  if (use_vox && threadIdx.x == 0) {
+    bulk_store(c.prev + v0 * 20, prev_s, (uint32_t)(nvi * 20 * sizeof(R)));
+    bulk_commit();
+  }
+  // ---------------------------------------------------------- forward x
+  cpx<R>* X;
+  if (packed) {
+    cpx<R>* other = (zbuf == b0) ? b1 : b0;
+    cpx<R>* Z = tile_fft<R, -1, 8>(zbuf, other, nr, c.px);
+    cpx<R>* dst = (Z == b0) ? b1 : b0;
+    x_forward_post<R>(Z, dst, nr, M, msh, c.px.tw);
+    X = dst;
+  } else {
+    X = zbuf;
+  }
+  fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bulk_store(c.spec + row0 * M * 18, X, (uint32_t)(nr * M * 18 * sizeof(cpx<R>)));
+    bulk_commit();
+  }
+  // ---------------------------------------------------------- error partials of the item
+  if (MODE == kIter) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const double mx = shfl_max((double)dmax[a]);
+      const double sm = shfl_sum((double)dsum[a]);
+      if (lane == 0) {
+        red[warp * 8 + a] = mx;
+        red[warp * 8 + 4 + a] = sm;
+      }
+    }
+    __syncthreads();
+    const int nwarp = blockDim.x >> 5;
+    if (threadIdx.x < 8) {
+      double a = red[threadIdx.x];
+      for (int w = 1; w < nwarp; ++w) {
+        const double vv = red[w * 8 + threadIdx.x];
+        a = (threadIdx.x < 4) ? fmax(a, vv) : a + vv;
+      }
+      itm[threadIdx.x] = a;
+    } else if (threadIdx.x >= 32 && threadIdx.x < 32 + 36) {
+      // Row sums.  With the unnormalised inverse along x, sum_x e~ = N1 X_in[0],
+      // so sum_x e = N1 (E + X_in[0]); the forward DC is sum_x tau.
+      const int q = threadIdx.x - 32;
+      double a = 0.0;
+      if (q < 18) {
+        const double mean = (q < 9) ? (double)c.E[q] : (double)c.G[q - 9];
+        for (int rr = 0; rr < nr; ++rr) a += (double)N1 * (mean + (double)dcin[q * rows + rr]);
+      } else {
+        for (int rr = 0; rr < nr; ++rr) a += (double)X[rr * M * 18 + (q - 18)].x;
+      }
+      itm[8 + q] = a;
+    }
+  }
+  __syncthreads();
+  parity ^= 1u;
+  return true;
+}
+
+// Pass A over a cell (single: per-block error totals in `partials`) or over
+// the entries of a multi-cell launch (per-item partials in each cell's ipart).
+template <class R, int MODE, bool MULTI>
+__global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
+    k_pass_a(CellDev<R> c0, Work<R> w, double* partials, const R* fin_tau, const R* fin_mu,
+             R* fout_e, R* fout_g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ CellDev<R> cs;
+  __shared__ double itm[kErrPartials];
+  double* acc = reinterpret_cast<double*>(smem_raw + PassASmem<R>::acc_off);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + PassASmem<R>::bar_off);
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_barrier_init();
+  }
+  for (int i = threadIdx.x; i < kErrPartials; i += blockDim.x) acc[i] = 0.0;
+  __syncthreads();
+  uint32_t parity = 0;
+  bool failed = false;
+  int* status = c0.status;
+  for_items<R, MULTI>(c0, c0.items_a, w, cs, [&](const CellDev<R>& c, long long item) {
+    if (failed) {
+      flag_timeout(c.status);  // every cell with a skipped item reports the failure
+      return;
+    }
+    if (!pass_a_item<R, MODE>(c, item, smem_raw, parity, itm, fin_tau, fin_mu, fout_e, fout_g)) {
+      failed = true;
+      status = c.status;
+      return;
+    }
+    if (MODE == kIter) {
+      if constexpr (MULTI) {
+        for (int i = threadIdx.x; i < kErrPartials; i += blockDim.x)
+          c.ipart[item * kErrPartials + i] = itm[i];
+      } else if (threadIdx.x < kErrPartials) {
+        const int i = threadIdx.x;
+        acc[i] = (i < 4) ? fmax(acc[i], itm[i]) : acc[i] + itm[i];
+      }
+      __syncthreads();
+    }
+  });
   if (threadIdx.x == 0) bulk_wait_all();
   if (failed) {
     // wait (bounded) for this block's loads still in flight, then report
     if (threadIdx.x == 0) {
-      if (use_spec_in) mbar_wait(&bars[0], parity);
-      if (use_vox) mbar_wait(&bars[1], parity);
+      if (MODE == kIter || MODE == kXInv) mbar_wait(&bars[0], parity);
+      if (MODE == kIter || MODE == kStart) mbar_wait(&bars[1], parity);
     }
     __syncthreads();
-    flag_timeout(c.status);
+    flag_timeout(status);
     return;
   }
-  if (MODE == kIter) {
+  if (MODE == kIter && !MULTI) {
     for (int i = threadIdx.x; i < kErrPartials; i += blockDim.x)
       partials[(long long)blockIdx.x * kErrPartials + i] = acc[i];
   }
@@ -496,22 +601,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
 // ||<a>|| are floored by their dimensional partner through the voxel size h
 // (den_e >= h |<gamma>|, den_gamma >= |<e>| / h, den_t >= |<m>| / h,
 // den_m >= h |<t>|), since ||<gamma>|| = 0 whenever the mean curvature is zero.
-// out[0] = err, out[1..4] = err_e, err_t, err_gamma, err_m.
+// out[0] = err, out[1..4] = err_e, err_t, err_gamma, err_m, out[5] = status.
 template <class R>
-__global__ void k_reduce_err(CellDev<R> c, const double* partials, int nparts, int err_kind,
-                             double* out) {
-  __shared__ double s[kErrPartials];
-  if (threadIdx.x < kErrPartials) {
-    const int q = threadIdx.x;
-    double a = 0.0;
-    for (int b = 0; b < nparts; ++b) {
-      const double v = partials[(long long)b * kErrPartials + q];
-      a = (q < 4) ? fmax(a, v) : a + v;
-    }
-    s[q] = a;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+__device__ void finish_err(const CellDev<R>& c, const double* s, int err_kind, double* out) {
     const double iv = c.inv_nvox;
     double me[9], mg[9], mt[9], mm[9];
     for (int q = 0; q < 9; ++q) {
@@ -547,50 +639,104 @@ __global__ void k_reduce_err(CellDev<R> c, const double* partials, int nparts, i
     }
     out[0] = err;
     out[5] = c.status ? (double)(*c.status) : 0.0;
+}
+
+// Fixed-order FP64 fold of `nparts` partial records (max for the first four
+// entries, sums for the rest) by one block; the total lands in s[].
+__device__ __forceinline__ void fold_partials(const double* partials, long long nparts, double* s,
+                                              double (*wred)[kErrPartials]) {
+  double a[kErrPartials];
+#pragma unroll
+  for (int q = 0; q < kErrPartials; ++q) a[q] = 0.0;
+  for (long long b = threadIdx.x; b < nparts; b += blockDim.x) {
+    const double* src = partials + b * kErrPartials;
+#pragma unroll
+    for (int q = 0; q < kErrPartials; ++q) a[q] = (q < 4) ? fmax(a[q], src[q]) : a[q] + src[q];
   }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kErrPartials; ++q) {
+    const double v = (q < 4) ? shfl_max(a[q]) : shfl_sum(a[q]);
+    if (lane == 0) wred[warp][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kErrPartials) {
+    const int q = threadIdx.x;
+    double v = wred[0][q];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = (q < 4) ? fmax(v, wred[w][q]) : v + wred[w][q];
+    s[q] = v;
+  }
+  __syncthreads();
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_reduce_err(CellDev<R> c, const double* partials, int nparts,
+                                                    int err_kind, double* out) {
+  __shared__ double s[kErrPartials];
+  __shared__ double wred[8][kErrPartials];
+  fold_partials(partials, nparts, s, wred);
+  if (threadIdx.x == 0) finish_err<R>(c, s, err_kind, out);
+}
+
+// One block per entry: the cell's per-item partials in item order.
+template <class R>
+__global__ void __launch_bounds__(256) k_reduce_err_multi(Work<R> w) {
+  __shared__ double s[kErrPartials];
+  __shared__ double wred[8][kErrPartials];
+  __shared__ CellDev<R> cs;
+  load_cell(cs, w.cells + w.act[blockIdx.x]);
+  __syncthreads();
+  fold_partials(cs.ipart, cs.items_a, s, wred);
+  if (threadIdx.x == 0) finish_err<R>(cs, s, cs.err_kind, cs.err_out);
 }
 
 // ------------------------------------------------------------------ state set-up
 // Zero initial state (Algorithm 2 initialisation) and the first predictor
-// e = E, gamma = Gamma of the first load increment.
+// e = E, gamma = Gamma of the first load increment.  Items: 256-voxel chunks.
 template <class R>
-__global__ void k_init(CellDev<R> c) {
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < c.nvox;
-       v += (long long)gridDim.x * blockDim.x) {
-    R* pv = c.prev + v * 20;
-    R* hv = c.hist + v * 20;
-    R* el = c.elast + v * 18;
+__device__ __forceinline__ void init_chunk(const CellDev<R>& c, long long chunk) {
+  const long long v = chunk * 256 + threadIdx.x;
+  if (threadIdx.x >= 256 || v >= c.nvox) return;
+  R* pv = c.prev + v * 20;
+  R* hv = c.hist + v * 20;
+  R* el = c.elast + v * 18;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      pv[q] = c.E[q];
-      pv[9 + q] = c.G[q];
-    }
-    pv[18] = R(1);
-    pv[19] = R(1);
-#pragma unroll
-    for (int q = 0; q < 18; ++q) {
-      hv[q] = R(0);
-      el[q] = R(0);
-    }
-    hv[18] = (R)c.phase[v];  // phase id travels with the history record
-    hv[19] = R(0);
-    reinterpret_cast<double2*>(c.pq)[v] = make_double2(0.0, 0.0);
+  for (int q = 0; q < 9; ++q) {
+    pv[q] = c.E[q];
+    pv[9 + q] = c.G[q];
   }
+  pv[18] = R(1);
+  pv[19] = R(1);
+#pragma unroll
+  for (int q = 0; q < 18; ++q) {
+    hv[q] = R(0);
+    el[q] = R(0);
+  }
+  hv[18] = (R)c.phase[v];  // phase id travels with the history record
+  hv[19] = R(0);
+  reinterpret_cast<double2*>(c.pq)[v] = make_double2(0.0, 0.0);
+}
+
+template <class R, bool MULTI>
+__global__ void __launch_bounds__(256) k_init(CellDev<R> c0, Work<R> w) {
+  __shared__ CellDev<R> cs;
+  for_items<R, MULTI>(c0, (c0.nvox + 255) / 256, w, cs,
+                      [&](const CellDev<R>& c, long long chunk) { init_chunk<R>(c, chunk); });
 }
 
 // ------------------------------------------------------------------ commit
 // Algorithm 2, end of a load increment: the converged iterate becomes the
-// history of Algorithm 1; homogenized sums; optional linear-extrapolation
-// predictor of the next increment, e' = e_n + ratio (e_n - e_{n-1}).
-// partials[block][40]: sums of t (9), m (9), e (9), gamma (9), p, q, t_eq, m_eq.
+// history of Algorithm 1; homogenized sums; when c.predict, the linear-
+// extrapolation predictor of the next increment, e' = e_n + ratio (e_n - e_{n-1}).
+// Per 256-voxel chunk: sums of t (9), m (9), e (9), gamma (9), p, q, t_eq, m_eq.
 template <class R>
-__global__ void __launch_bounds__(256) k_commit(CellDev<R> c, int predict, R ratio,
-                                                double* partials) {
+__device__ __forceinline__ void commit_chunk(const CellDev<R>& c, long long chunk, double* out40,
+                                             double (*red)[kAvgPartials]) {
   double acc[kAvgPartials];
 #pragma unroll
   for (int i = 0; i < kAvgPartials; ++i) acc[i] = 0.0;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < c.nvox;
-       v += (long long)gridDim.x * blockDim.x) {
+  const long long v = chunk * 256 + threadIdx.x;
+  if (threadIdx.x < 256 && v < c.nvox) {
     R* pv = c.prev + v * 20;
     R* hv = c.hist + v * 20;
     R e[9], g[9], ht[9], hm[9];
@@ -601,7 +747,7 @@ __global__ void __launch_bounds__(256) k_commit(CellDev<R> c, int predict, R rat
       ht[q] = hv[q];
       hm[q] = hv[9 + q];
     }
-    const PhaseDev<R> P = c.phases[c.phase[v]];
+    const PhaseDev<R>& P = c.phases[(int)hv[18]];
     double2 pq = reinterpret_cast<const double2*>(c.pq)[v];
     R t[9], m[9];
     double p, q;
@@ -614,19 +760,20 @@ __global__ void __launch_bounds__(256) k_commit(CellDev<R> c, int predict, R rat
     for (int i = 0; i < 9; ++i) {
       hv[i] = t[i] - ae[i];
       hv[9 + i] = m[i] - bg[i];
-      acc[i] += (double)t[i];
-      acc[9 + i] += (double)m[i];
-      acc[18 + i] += (double)e[i];
-      acc[27 + i] += (double)g[i];
+      acc[i] = (double)t[i];
+      acc[9 + i] = (double)m[i];
+      acc[18 + i] = (double)e[i];
+      acc[27 + i] = (double)g[i];
     }
     reinterpret_cast<double2*>(c.pq)[v] = make_double2(p, q);
     double teq, meq;
     equivalents<R>(P, t, m, teq, meq);
-    acc[36] += p;
-    acc[37] += q;
-    acc[38] += teq;
-    acc[39] += meq;
-    if (predict) {
+    acc[36] = p;
+    acc[37] = q;
+    acc[38] = teq;
+    acc[39] = meq;
+    if (c.predict) {
+      const R ratio = (R)c.ratio;
       R* el = c.elast + v * 18;
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
@@ -638,19 +785,41 @@ __global__ void __launch_bounds__(256) k_commit(CellDev<R> c, int predict, R rat
       }
     }
   }
-  __shared__ double red[8][kAvgPartials];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < kAvgPartials; ++i) {
-    const double s = shfl_sum(acc[i]);
-    if (lane == 0) red[warp][i] = s;
+    const double sm = shfl_sum(acc[i]);
+    if (lane == 0) red[warp][i] = sm;
   }
   __syncthreads();
   if (threadIdx.x < kAvgPartials) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-    partials[(long long)blockIdx.x * kAvgPartials + threadIdx.x] = s;
+    double sm = 0.0;
+    for (int wq = 0; wq < (int)(blockDim.x >> 5); ++wq) sm += red[wq][threadIdx.x];
+    out40[threadIdx.x] = sm;
   }
+  __syncthreads();
+}
+
+// Single cell: per-block totals in partials[block][40] (a fixed grid gives a
+// fixed order).  Multi: per-chunk records in each cell's apart.
+template <class R, bool MULTI>
+__global__ void __launch_bounds__(256) k_commit(CellDev<R> c0, Work<R> w, double* partials) {
+  __shared__ CellDev<R> cs;
+  __shared__ double red[8][kAvgPartials];
+  __shared__ double chunk_sum[kAvgPartials];
+  __shared__ double block_sum[kAvgPartials];
+  if (threadIdx.x < kAvgPartials) block_sum[threadIdx.x] = 0.0;
+  __syncthreads();
+  for_items<R, MULTI>(c0, (c0.nvox + 255) / 256, w, cs, [&](const CellDev<R>& c, long long chunk) {
+    commit_chunk<R>(c, chunk, chunk_sum, red);
+    if (threadIdx.x < kAvgPartials) {
+      if constexpr (MULTI) c.apart[chunk * kAvgPartials + threadIdx.x] = chunk_sum[threadIdx.x];
+      else block_sum[threadIdx.x] += chunk_sum[threadIdx.x];
+    }
+    __syncthreads();
+  });
+  if (!MULTI && threadIdx.x < kAvgPartials)
+    partials[(long long)blockIdx.x * kAvgPartials + threadIdx.x] = block_sum[threadIdx.x];
 }
 
 // Sum of the commit partials in a fixed order, divided by the voxel count.
@@ -659,6 +828,20 @@ __global__ void k_reduce_avg(const double* partials, int nparts, double inv_nvox
     double s = 0.0;
     for (int b = 0; b < nparts; ++b) s += partials[(long long)b * kAvgPartials + threadIdx.x];
     out[threadIdx.x] = s * inv_nvox;
+  }
+}
+
+// One block per entry: the cell's chunk records in chunk order -> c.avg_out.
+template <class R>
+__global__ void k_reduce_avg_multi(Work<R> w) {
+  __shared__ CellDev<R> cs;
+  load_cell(cs, w.cells + w.act[blockIdx.x]);
+  __syncthreads();
+  if (threadIdx.x < kAvgPartials) {
+    const long long n = (cs.nvox + 255) / 256;
+    double s = 0.0;
+    for (long long b = 0; b < n; ++b) s += cs.apart[b * kAvgPartials + threadIdx.x];
+    cs.avg_out[threadIdx.x] = s * cs.inv_nvox;
   }
 }
 
@@ -738,22 +921,37 @@ size_t smem_line_pass(int n) { return 2ull * 18 * (size_t)n * sizeof(cpx<R>); }
 template <class R>
 size_t smem_pass_a(int n1, int rows) { return PassASmem<R>(n1, rows).total; }
 
+// Raise each kernel's dynamic shared-memory limit to what its static shared
+// memory leaves of the opt-in maximum (at least kSmemBudget).
 template <class R>
 static cudaError_t set_smem_attrs() {
   static bool done = false;
   if (done) return cudaSuccess;
-  const int maxs = (int)kSmemBudget;
   cudaError_t e = cudaSuccess;
-#define MP_ATTR(k) \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs)
-  MP_ATTR((k_fft_y<R, -1>));
-  MP_ATTR((k_fft_y<R, +1>));
-  MP_ATTR((k_green_z<R>));
-  MP_ATTR((k_pass_a<R, kIter>));
-  MP_ATTR((k_pass_a<R, kStart>));
-  MP_ATTR((k_pass_a<R, kXFwd>));
-  MP_ATTR((k_pass_a<R, kXInv>));
-#undef MP_ATTR
+  auto raise = [&](const void* fn) {
+    if (e != cudaSuccess) return;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return;
+    if (fa.sharedSizeBytes > kSmemStaticReserve) {
+      e = cudaErrorInvalidValue;
+      return;
+    }
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSmemOptin - fa.sharedSizeBytes));
+  };
+  raise((const void*)k_fft_y<R, -1, false>);
+  raise((const void*)k_fft_y<R, +1, false>);
+  raise((const void*)k_fft_y<R, -1, true>);
+  raise((const void*)k_fft_y<R, +1, true>);
+  raise((const void*)k_green_z<R, false>);
+  raise((const void*)k_green_z<R, true>);
+  raise((const void*)k_pass_a<R, kIter, false>);
+  raise((const void*)k_pass_a<R, kStart, false>);
+  raise((const void*)k_pass_a<R, kXFwd, false>);
+  raise((const void*)k_pass_a<R, kXInv, false>);
+  raise((const void*)k_pass_a<R, kIter, true>);
+  raise((const void*)k_pass_a<R, kStart, true>);
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -774,8 +972,8 @@ cudaError_t launch_fft_y(const LaunchCfg& L, const CellDev<R>& c, int dir, cudaS
   cudaError_t e = set_smem_attrs<R>();
   if (e != cudaSuccess) return e;
   if (c.n2 > 1) {
-    if (dir < 0) k_fft_y<R, -1><<<L.grid_y, kThreads, smem_line_pass<R>(c.n2), st>>>(c);
-    else k_fft_y<R, +1><<<L.grid_y, kThreads, smem_line_pass<R>(c.n2), st>>>(c);
+    if (dir < 0) k_fft_y<R, -1, false><<<L.grid_y, kThreadsYZ, smem_line_pass<R>(c.n2), st>>>(c, Work<R>{});
+    else k_fft_y<R, +1, false><<<L.grid_y, kThreadsYZ, smem_line_pass<R>(c.n2), st>>>(c, Work<R>{});
   }
   return cudaGetLastError();
 }
@@ -784,7 +982,7 @@ template <class R>
 cudaError_t launch_green_z(const LaunchCfg& L, const CellDev<R>& c, cudaStream_t st) {
   cudaError_t e = set_smem_attrs<R>();
   if (e != cudaSuccess) return e;
-  k_green_z<R><<<L.grid_z, kThreads, smem_line_pass<R>(c.n3), st>>>(c);
+  k_green_z<R, false><<<L.grid_z, kThreadsYZ, smem_line_pass<R>(c.n3), st>>>(c, Work<R>{});
   return cudaGetLastError();
 }
 
@@ -793,15 +991,15 @@ cudaError_t launch_pass_a_iter(const LaunchCfg& L, const CellDev<R>& c, double* 
                                cudaStream_t st) {
   cudaError_t e = set_smem_attrs<R>();
   if (e != cudaSuccess) return e;
-  k_pass_a<R, kIter><<<L.grid_a, kThreads, smem_pass_a<R>(c.n1, L.rows), st>>>(c, L.rows, partials, nullptr,
-                                                                           nullptr, nullptr, nullptr);
+  k_pass_a<R, kIter, false><<<L.grid_a, kThreads, smem_pass_a<R>(c.n1, c.rows_a), st>>>(
+      c, Work<R>{}, partials, nullptr, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 
 template <class R>
 cudaError_t launch_reduce_err(const LaunchCfg& L, const CellDev<R>& c, const double* partials,
                               int err_kind, double* err_out, cudaStream_t st) {
-  k_reduce_err<R><<<1, 64, 0, st>>>(c, partials, L.grid_a, err_kind, err_out);
+  k_reduce_err<R><<<1, 256, 0, st>>>(c, partials, L.grid_a, err_kind, err_out);
   return cudaGetLastError();
 }
 
@@ -820,18 +1018,67 @@ template <class R>
 cudaError_t launch_start(const LaunchCfg& L, const CellDev<R>& c, int first, cudaStream_t st) {
   cudaError_t e = set_smem_attrs<R>();
   if (e != cudaSuccess) return e;
-  if (first) k_init<R><<<L.grid_v, 256, 0, st>>>(c);
-  k_pass_a<R, kStart><<<L.grid_a, kThreads, smem_pass_a<R>(c.n1, L.rows), st>>>(c, L.rows, nullptr, nullptr,
-                                                                            nullptr, nullptr, nullptr);
+  if (first) k_init<R, false><<<L.grid_v, 256, 0, st>>>(c, Work<R>{});
+  k_pass_a<R, kStart, false><<<L.grid_a, kThreads, smem_pass_a<R>(c.n1, c.rows_a), st>>>(
+      c, Work<R>{}, nullptr, nullptr, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 
 template <class R>
-cudaError_t launch_commit(const LaunchCfg& L, const CellDev<R>& c, int predict, double ratio,
-                          double* partials, double* avg_out, cudaStream_t st) {
-  k_commit<R><<<L.grid_v, 256, 0, st>>>(c, predict, (R)ratio, partials);
+cudaError_t launch_commit(const LaunchCfg& L, const CellDev<R>& c, double* partials, double* avg_out,
+                          cudaStream_t st) {
+  k_commit<R, false><<<L.grid_v, 256, 0, st>>>(c, Work<R>{}, partials);
   k_reduce_avg<<<1, 64, 0, st>>>(partials, L.grid_v, c.inv_nvox, avg_out);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ multi-cell launches
+template <class R>
+cudaError_t launch_multi_iteration(const MultiCfg<R>& m, cudaStream_t st) {
+  cudaError_t e = set_smem_attrs<R>();
+  if (e != cudaSuccess) return e;
+  if (m.items_y > 0)
+    k_fft_y<R, -1, true><<<m.grid_y, kThreadsYZ, m.smem_y, st>>>(CellDev<R>{}, m.wy);
+  if (m.items_z > 0)
+    k_green_z<R, true><<<m.grid_z, kThreadsYZ, m.smem_z, st>>>(CellDev<R>{}, m.wz);
+  if (m.items_y > 0)
+    k_fft_y<R, +1, true><<<m.grid_y, kThreadsYZ, m.smem_y, st>>>(CellDev<R>{}, m.wy);
+  if (m.items_a > 0)
+    k_pass_a<R, kIter, true><<<m.grid_a, kThreads, m.smem_a, st>>>(CellDev<R>{}, m.wa, nullptr, nullptr,
+                                                                    nullptr, nullptr, nullptr);
+  if (m.wa.n_act > 0) k_reduce_err_multi<R><<<m.wa.n_act, 256, 0, st>>>(m.wa);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_multi_start(const MultiCfg<R>& m, cudaStream_t st) {
+  cudaError_t e = set_smem_attrs<R>();
+  if (e != cudaSuccess) return e;
+  if (m.items_v0 > 0) k_init<R, true><<<m.grid_v0, 256, 0, st>>>(CellDev<R>{}, m.wv0);
+  if (m.items_s > 0)
+    k_pass_a<R, kStart, true><<<m.grid_s, kThreads, m.smem_a, st>>>(CellDev<R>{}, m.ws, nullptr, nullptr,
+                                                                     nullptr, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_multi_commit(const MultiCfg<R>& m, cudaStream_t st) {
+  if (m.items_v > 0) k_commit<R, true><<<m.grid_v, 256, 0, st>>>(CellDev<R>{}, m.wv, nullptr);
+  if (m.wv.n_act > 0) k_reduce_avg_multi<R><<<m.wv.n_act, 64, 0, st>>>(m.wv);
+  return cudaGetLastError();
+}
+
+template <class R>
+void multi_grids(MultiCfg<R>& m, int nsm) {
+  set_smem_attrs<R>();
+  m.grid_y = grid_for<R>((const void*)k_fft_y<R, -1, true>, kThreadsYZ, m.smem_y, m.items_y, nsm);
+  m.grid_z = grid_for<R>((const void*)k_green_z<R, true>, kThreadsYZ, m.smem_z, m.items_z, nsm);
+  m.grid_a = grid_for<R>((const void*)k_pass_a<R, kIter, true>, kThreads, m.smem_a, m.items_a, nsm);
+  m.grid_s = grid_for<R>((const void*)k_pass_a<R, kStart, true>, kThreads, m.smem_a, m.items_s, nsm);
+  long long g = m.items_v < 8ll * nsm ? m.items_v : 8ll * nsm;
+  m.grid_v = (int)(g > 0 ? g : 1);
+  g = m.items_v0 < 8ll * nsm ? m.items_v0 : 8ll * nsm;
+  m.grid_v0 = (int)(g > 0 ? g : 1);
 }
 
 template <class R>
@@ -848,12 +1095,12 @@ cudaError_t launch_green_apply(const LaunchCfg& L, const CellDev<R>& c, const R*
                                R* e_out, R* g_out, cudaStream_t st) {
   cudaError_t e = set_smem_attrs<R>();
   if (e != cudaSuccess) return e;
-  const size_t sa = smem_pass_a<R>(c.n1, L.rows);
-  k_pass_a<R, kXFwd><<<L.grid_a, kThreads, sa, st>>>(c, L.rows, nullptr, tau, mu, nullptr, nullptr);
-  if (c.n2 > 1) k_fft_y<R, -1><<<L.grid_y, kThreads, smem_line_pass<R>(c.n2), st>>>(c);
-  k_green_z<R><<<L.grid_z, kThreads, smem_line_pass<R>(c.n3), st>>>(c);
-  if (c.n2 > 1) k_fft_y<R, +1><<<L.grid_y, kThreads, smem_line_pass<R>(c.n2), st>>>(c);
-  k_pass_a<R, kXInv><<<L.grid_a, kThreads, sa, st>>>(c, L.rows, nullptr, nullptr, nullptr, e_out, g_out);
+  const size_t sa = smem_pass_a<R>(c.n1, c.rows_a);
+  k_pass_a<R, kXFwd, false><<<L.grid_a, kThreads, sa, st>>>(c, Work<R>{}, nullptr, tau, mu, nullptr, nullptr);
+  if (c.n2 > 1) k_fft_y<R, -1, false><<<L.grid_y, kThreadsYZ, smem_line_pass<R>(c.n2), st>>>(c, Work<R>{});
+  k_green_z<R, false><<<L.grid_z, kThreadsYZ, smem_line_pass<R>(c.n3), st>>>(c, Work<R>{});
+  if (c.n2 > 1) k_fft_y<R, +1, false><<<L.grid_y, kThreadsYZ, smem_line_pass<R>(c.n2), st>>>(c, Work<R>{});
+  k_pass_a<R, kXInv, false><<<L.grid_a, kThreads, sa, st>>>(c, Work<R>{}, nullptr, nullptr, nullptr, e_out, g_out);
   return cudaGetLastError();
 }
 
@@ -882,10 +1129,12 @@ LaunchCfg make_launch_cfg(const CellDev<R>& c, int nsm) {
   L.rows = rows;
   const long long nrows = (long long)c.n2 * c.n3;
   const long long items = (nrows + rows - 1) / rows;
-  L.grid_a = grid_for<R>((const void*)k_pass_a<R, kIter>, kThreads, smem_pass_a<R>(c.n1, rows), items, nsm);
-  L.grid_y = grid_for<R>((const void*)k_fft_y<R, -1>, kThreads, smem_line_pass<R>(c.n2),
+  L.items_a = items;
+  L.grid_a = grid_for<R>((const void*)k_pass_a<R, kIter, false>, kThreads, smem_pass_a<R>(c.n1, rows), items,
+                         nsm);
+  L.grid_y = grid_for<R>((const void*)k_fft_y<R, -1, false>, kThreadsYZ, smem_line_pass<R>(c.n2),
                          (long long)c.n3 * c.kx, nsm);
-  L.grid_z = grid_for<R>((const void*)k_green_z<R>, kThreads, smem_line_pass<R>(c.n3),
+  L.grid_z = grid_for<R>((const void*)k_green_z<R, false>, kThreadsYZ, smem_line_pass<R>(c.n3),
                          (long long)c.n2 * c.kx, nsm);
   long long vb = (c.nvox + 255) / 256;
   L.grid_v = (int)(vb < 4ll * nsm ? vb : 4ll * nsm);
@@ -907,8 +1156,14 @@ bool sizes_fit(int n1, int n2, int n3) {
   template cudaError_t launch_iteration<R>(const LaunchCfg&, const CellDev<R>&, double*, double*, int, \
                                            cudaStream_t);                                            \
   template cudaError_t launch_start<R>(const LaunchCfg&, const CellDev<R>&, int, cudaStream_t);       \
-  template cudaError_t launch_commit<R>(const LaunchCfg&, const CellDev<R>&, int, double, double*,    \
-                                        double*, cudaStream_t);                                      \
+  template cudaError_t launch_commit<R>(const LaunchCfg&, const CellDev<R>&, double*, double*,        \
+                                        cudaStream_t);                                               \
+  template cudaError_t launch_multi_iteration<R>(const MultiCfg<R>&, cudaStream_t);                   \
+  template cudaError_t launch_multi_start<R>(const MultiCfg<R>&, cudaStream_t);                       \
+  template cudaError_t launch_multi_commit<R>(const MultiCfg<R>&, cudaStream_t);                      \
+  template void multi_grids<R>(MultiCfg<R>&, int);                                                   \
+  template size_t smem_pass_a<R>(int, int);                                                          \
+  template size_t smem_line_pass<R>(int);                                                            \
   template cudaError_t launch_fields<R>(const LaunchCfg&, const CellDev<R>&, int, double*, double*,   \
                                         double*, double*, double*, double*, cudaStream_t);           \
   template cudaError_t launch_green_apply<R>(const LaunchCfg&, const CellDev<R>&, const R*, const R*,  \

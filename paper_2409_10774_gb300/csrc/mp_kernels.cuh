@@ -7,6 +7,7 @@ namespace mp {
 
 struct LaunchCfg {
   int rows = 1;    // rows per pass-A work item
+  long long items_a = 1;
   int grid_a = 1;  // pass-A grid (persistent, one error partial per block)
   int grid_y = 1;
   int grid_z = 1;
@@ -37,10 +38,35 @@ cudaError_t launch_iteration(const LaunchCfg& L, const CellDev<R>& c, double* pa
 // Algorithm 1 at the predictor, polarizations, forward x transform.
 template <class R>
 cudaError_t launch_start(const LaunchCfg& L, const CellDev<R>& c, int first, cudaStream_t st);
-// Commit of a converged increment; avg_out[0..39] receives the homogenized averages.
+// Commit of a converged increment (c.predict / c.ratio select the predictor);
+// avg_out[0..39] receives the homogenized averages.
 template <class R>
-cudaError_t launch_commit(const LaunchCfg& L, const CellDev<R>& c, int predict, double ratio,
-                          double* partials, double* avg_out, cudaStream_t st);
+cudaError_t launch_commit(const LaunchCfg& L, const CellDev<R>& c, double* partials, double* avg_out,
+                          cudaStream_t st);
+
+// Multi-cell launches: each Work lists the entries (cells) and their item
+// prefix for one kernel family; the cells' descriptors live in device memory.
+template <class R>
+struct MultiCfg {
+  Work<R> wy, wz, wa;   // iterating cells: y columns, z columns, pass-A items
+  Work<R> ws;           // cells starting an increment: pass-A items
+  Work<R> wv, wv0;      // 256-voxel chunks: commit, first-increment initialisation
+  long long items_y = 0, items_z = 0, items_a = 0, items_s = 0, items_v = 0, items_v0 = 0;
+  size_t smem_y = 0, smem_z = 0, smem_a = 0;  // largest tile over the entries (smem_a: pass A, both modes)
+  int grid_y = 1, grid_z = 1, grid_a = 1, grid_s = 1, grid_v = 1, grid_v0 = 1;
+};
+template <class R>
+void multi_grids(MultiCfg<R>& m, int nsm);
+template <class R>
+cudaError_t launch_multi_iteration(const MultiCfg<R>& m, cudaStream_t st);
+template <class R>
+cudaError_t launch_multi_start(const MultiCfg<R>& m, cudaStream_t st);
+template <class R>
+cudaError_t launch_multi_commit(const MultiCfg<R>& m, cudaStream_t st);
+template <class R>
+size_t smem_pass_a(int n1, int rows);
+template <class R>
+size_t smem_line_pass(int n);
 template <class R>
 cudaError_t launch_fields(const LaunchCfg& L, const CellDev<R>& c, int from_elast, double* fe,
                           double* fg, double* ft, double* fm, double* fp, double* fq, cudaStream_t st);

@@ -74,15 +74,19 @@ bool axis_ok(int n) {
   return n == 1;
 }
 
-void radices(int m, int* radix, int& nst) {
+void radices(int m, int* radix, int& nst, bool allow16) {
   nst = 0;
   int k2 = 0, k3 = 0;
   while (m % 2 == 0) { m /= 2; ++k2; }
   while (m % 3 == 0) { m /= 3; ++k3; }
-  while (k2 >= 3 && k2 - 3 != 1) { radix[nst++] = 8; k2 -= 3; }
-  if (k2 == 4) { radix[nst++] = 4; radix[nst++] = 4; }
-  else if (k2 == 2) { radix[nst++] = 4; }
-  else if (k2 == 1) { radix[nst++] = 2; }
+  // powers of two: as few stages as possible, radix 16 only where it saves one
+  // (the x axis, transformed inside pass A, is limited to radix 8)
+  static const int kPlan2[10][4] = {{0}, {2}, {4}, {8}, {16}, {8, 4}, {8, 8}, {16, 8}, {16, 16}, {8, 8, 8}};
+  static const int kPlan2x[10][4] = {{0}, {2}, {4}, {8}, {4, 4}, {8, 4}, {8, 8}, {8, 4, 4}, {8, 8, 4}, {8, 8, 8}};
+  static const int kLen2[10] = {0, 1, 1, 1, 1, 2, 2, 2, 2, 3};
+  static const int kLen2x[10] = {0, 1, 1, 1, 2, 2, 2, 3, 3, 3};
+  const int len = allow16 ? kLen2[k2] : kLen2x[k2];
+  for (int i = 0; i < len; ++i) radix[nst++] = allow16 ? kPlan2[k2][i] : kPlan2x[k2][i];
   for (int i = 0; i < k3; ++i) radix[nst++] = 3;
 }
 
@@ -128,7 +132,7 @@ mp_status run(mp_ctx* ctx, const int32_t n[3], double h, const double ref[6], co
     p.n = n[a];
     p.m = packed ? (n[a] > 1 ? n[a] / 2 : 1) : n[a];
     p.tstride = packed ? 2 : 1;
-    radices(p.m, p.radix, p.nstages);
+    radices(p.m, p.radix, p.nstages, !packed);
     for (int k = 0; k < n[a]; ++k) {
       const double ang = 2.0 * M_PI * (double)k / (double)n[a];
       host_tw[a][k].x = (R)std::cos(ang);
@@ -145,6 +149,8 @@ mp_status run(mp_ctx* ctx, const int32_t n[3], double h, const double ref[6], co
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) {
       LaunchCfg L = make_launch_cfg<R>(c, nsm > 0 ? nsm : 1);
+      c.rows_a = L.rows;
+      c.items_a = L.items_a;
       e = launch_green_apply<R>(L, c, (const R*)tau, (const R*)mu, (R*)e_out, (R*)g_out, st);
     }
   }

@@ -386,6 +386,180 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+# ---------------------------------------------------------------- batched and served solves
+
+def _percentile(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
+
+
+def run_batch_leg(args):
+    """Batched dataset generation: `--batch-count` RVEs (default 512) of
+    uneven size solved in one mp_batch_solve call (FP32 fields, tolerance
+    1e-6), timed end to end (problem upload, all rounds, results download),
+    beside the plain single-instance FP64 GPU solver at the same tolerance on
+    the first `--fp64-sample` of the same RVEs, one after another."""
+    import numpy as np
+    import torch
+
+    import paper_2409_10774_gb300 as M
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    t_gen = time.perf_counter()
+    probs = W.workload_batch(count=args.batch_count)
+    t_gen = time.perf_counter() - t_gen
+    ctx = M.Context(0)
+    nvox = [int(np.prod(p["n"])) for p in probs]
+    # warm-up: module load, allocator pools, the multi-cell kernels
+    M.mp_batch_solve(ctx, probs[:16], precision=1, lockstep_iters=[[2] * 10] * 16, stream=stream)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = time.perf_counter()
+    res = M.mp_batch_solve(ctx, probs, precision=1, stream=stream)
+    torch.cuda.synchronize(dev)
+    secs = time.perf_counter() - t0
+    clocks = sampler.stop()
+    statuses = {}
+    for r in res:
+        statuses[r["status"]] = statuses.get(r["status"], 0) + 1
+    vox_it = float(sum(nv * int(np.sum(r["iters"])) for nv, r in zip(nvox, res)))
+    iters = np.array([int(np.sum(r["iters"])) for r in res])
+    # plain single-instance FP64 solver on a sample of the same RVEs
+    k = min(args.fp64_sample, len(probs))
+    fp64 = None
+    if k > 0:
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        vi64 = 0.0
+        st64 = {}
+        for p, nv in zip(probs[:k], nvox[:k]):
+            r = M.mp_solve(ctx, p, precision=0, stream=stream)
+            vi64 += nv * float(np.sum(r["iters"]))
+            st64[r["status"]] = st64.get(r["status"], 0) + 1
+        torch.cuda.synchronize(dev)
+        s64 = time.perf_counter() - t1
+        # the batch's own time for the same RVEs is not separable; compare rates
+        fp64 = {"solves_per_s": k / s64, "voxel_iters_per_s": vi64 / s64, "sample": k,
+                "seconds": s64, "statuses": st64}
+    line = {
+        "leg": "batch", "metric": "batched RVE solves/s", "value": len(probs) / secs, "unit": "solves/s",
+        "higher_is_better": True, "seconds": secs, "voxel_iters_per_s": vox_it / secs,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch{len(probs)}-N{{16,24,32,48}}", "rves": len(probs),
+                   "voxels_total": int(sum(nvox)), "increments": 10, "tol": 1e-6, "err": "local",
+                   "ref_medium": "midrange", "generation_s": t_gen},
+        "statuses": statuses,
+        "iterations_per_rve": {"p50": _percentile(iters, 50), "p90": _percentile(iters, 90),
+                               "max": int(iters.max())},
+        "fp64_single": fp64,
+        "speedup_vs_fp64_single": (len(probs) / secs) / fp64["solves_per_s"] if fp64 else None,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve_leg(args):
+    """Serving: requests (RSA spheres, N in {32,64,96,128}, 5-20 increments,
+    FP32, tolerance 1e-6) arrive as a Poisson process at each rate of
+    `--rates`; each is submitted to one mp_server at its arrival time and
+    waited for by its own thread; latency = result on the host - arrival.
+    Baseline: the same requests one by one with the plain single-instance
+    FP64 solver, queued FIFO at the same arrival times (their service times
+    measured, the queue computed)."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_2409_10774_gb300 as M
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ctx = M.Context(0)
+    n_req = args.requests
+    t_gen = time.perf_counter()
+    reqs = [W.workload_serving_request(i) for i in range(n_req)]
+    t_gen = time.perf_counter() - t_gen
+    # warm-up
+    M.mp_batch_solve(ctx, reqs[:2], precision=1, lockstep_iters=[[1] * (len(r["time"]) - 1) for r in reqs[:2]])
+    torch.cuda.synchronize(dev)
+    rates = [float(x) for x in args.rates.split(",")]
+    out = []
+    for rate in rates:
+        rng = np.random.Generator(np.random.PCG64(2409_10774 + int(rate * 1000)))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        done = [None] * n_req
+        status = [None] * n_req
+        srv = M.Server(ctx, budget_bytes=args.budget_gb << 30)
+        t0 = time.perf_counter()
+        threads = []
+
+        def waiter(i, ticket):
+            r = srv.wait(ticket)
+            done[i] = time.perf_counter() - t0
+            status[i] = r["status"]
+
+        sampler = ClockSampler(0)
+        sampler.start()
+        for i in range(n_req):
+            dt = arrivals[i] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tk = srv.submit(reqs[i], precision=1)
+            th = threading.Thread(target=waiter, args=(i, tk))
+            th.start()
+            threads.append(th)
+        for th in threads:
+            th.join()
+        clocks = sampler.stop()
+        st = srv.stats()
+        srv.close()
+        lat = np.array(done) - arrivals
+        span = max(done) - arrivals[0]
+        out.append({"rate_per_s": rate, "p50_s": _percentile(lat, 50), "p99_s": _percentile(lat, 99),
+                    "solves_per_s": n_req / span, "voxel_iters_per_s": st["voxel_iters"] / span,
+                    "peak_resident": st["peak_resident"], "rounds": st["rounds"],
+                    "statuses": {s_: status.count(s_) for s_ in set(status)}, "clocks": clocks})
+    # baseline: plain FP64 single-instance solves, one by one
+    service = []
+    for r in reqs[: args.fp64_sample]:
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        M.mp_solve(ctx, r, precision=0)
+        torch.cuda.synchronize(dev)
+        service.append(time.perf_counter() - t1)
+    base = []
+    if service:
+        m = len(service)
+        for rate in rates:
+            rng = np.random.Generator(np.random.PCG64(2409_10774 + int(rate * 1000)))
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))[:m]
+            free_at, lat = 0.0, []
+            for a, sv in zip(arrivals, service):
+                start = max(a, free_at)
+                free_at = start + sv
+                lat.append(free_at - a)
+            base.append({"rate_per_s": rate, "p50_s": _percentile(lat, 50), "p99_s": _percentile(lat, 99),
+                         "solves_per_s": m / (free_at - arrivals[0]), "requests": m})
+    line = {
+        "leg": "serve", "metric": "serving p50/p99 latency and solves/s", "unit": "s",
+        "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "requests RSA spheres r=6 vf0.3, N in {32,64,96,128}, 5-20 increments",
+                   "requests_per_rate": n_req, "tol": 1e-6, "budget_gb": args.budget_gb,
+                   "generation_s": t_gen},
+        "rates": out,
+        "fp64_one_by_one": {"service_s": service, "queue": base},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -398,12 +572,24 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--leg", choices=("single", "batch", "serve"), default="single",
+                    help="single: the 256^3 cell (the bench line); batch / serve: the batched and "
+                         "serving measurements")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--fp64-sample", type=int, default=16)
+    ap.add_argument("--rates", default="1,3,10")
+    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--budget-gb", type=int, default=64)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.leg == "batch":
+        return run_batch_leg(args)
+    if args.leg == "serve":
+        return run_serve_leg(args)
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -239,6 +239,15 @@ mp_status mp_server_wait(mp_server* server, uint64_t ticket, int32_t timeout_ms)
 mp_status mp_server_query(mp_server* server, mp_server_stats* stats);
 void mp_server_destroy(mp_server* server);
 
+/* Convergence trace: while enabled, mp_rve_run records one row of 7 doubles
+ * per fixed-point iteration: (increment, iteration, err, err_e, err_t,
+ * err_gamma, err_m) - eq. err and its four per-field terms.
+ * mp_rve_trace(rve, 0) stops and discards the trace.  mp_rve_trace_read
+ * copies up to `capacity` rows to `out` (may be NULL), returns the number of
+ * rows recorded (-1 for a NULL rve) and discards them when clear != 0. */
+mp_status mp_rve_trace(mp_rve* rve, int32_t enable);
+int64_t mp_rve_trace_read(mp_rve* rve, double* out, int64_t capacity, int32_t clear);
+
 /* Hot-path components on device buffers -----------------------------------
  * Real type of tensor buffers: double for precision 0, float for 1.
  *

@@ -30,7 +30,7 @@ EXPORTED = ("mp_abi_version", "mp_create", "mp_destroy", "mp_last_error", "mp_va
             "mp_solve", "mp_rve_create", "mp_rve_run", "mp_rve_results", "mp_rve_reset",
             "mp_rve_steps_done", "mp_rve_iterations", "mp_rve_destroy", "mp_rve_profile",
             "mp_rve_profile_read", "mp_radial_return", "mp_green_apply", "mp_green_apply_static",
-            "mp_batch_solve", "mp_server_create", "mp_server_submit", "mp_server_wait",
+            "mp_rve_trace", "mp_rve_trace_read", "mp_batch_solve", "mp_server_create", "mp_server_submit", "mp_server_wait",
             "mp_server_query", "mp_server_destroy")
 MP_STATIC_SCRATCH_BYTES = 8 * 1024 * 1024
 KERNEL_CLASSES = ("fft_y_fwd", "green_z", "fft_y_inv", "pass_a", "reduce", "start", "commit")
@@ -115,6 +115,8 @@ def _load():
         "mp_green_apply": (C.c_int, [V, C.c_int32, P(C.c_int32), C.c_double, P(C.c_double), V, V, V, V, V]),
         "mp_green_apply_static": (C.c_int, [V, C.c_int32, P(C.c_int32), C.c_double, P(C.c_double), V, V, V, V,
                                             V]),
+        "mp_rve_trace": (C.c_int, [V, C.c_int32]),
+        "mp_rve_trace_read": (C.c_int64, [V, P(C.c_double), C.c_int64, C.c_int32]),
         "mp_batch_solve": (C.c_int, [V, P(P(mp_problem)), C.c_int32, P(mp_result), P(C.c_int), V]),
         "mp_server_create": (C.c_int, [V, P(mp_server_opts), P(V)]),
         "mp_server_submit": (C.c_int, [V, P(mp_problem), P(mp_result), P(C.c_uint64)]),
@@ -342,6 +344,7 @@ class Rve:
         st = LIB.mp_rve_run(self.ptr, int(n_steps), _stream_handle(stream))
         if st in _HARD_ERRORS:
             raise MicropolarError(st, self.ctx.error())
+        self._run_status = st
         return st
 
     def results(self, fields=False, stream=None):
@@ -349,7 +352,7 @@ class Rve:
         st = LIB.mp_rve_results(self.ptr, C.byref(rs.st), _stream_handle(stream))
         if st != MP_OK:
             raise MicropolarError(st, self.ctx.error())
-        return rs.to_dict(MP_OK if rs.st.failed_step == 0 else 5)
+        return rs.to_dict(MP_OK if rs.st.failed_step == 0 else getattr(self, "_run_status", 4))
 
     def reset(self, stream=None):
         LIB.mp_rve_reset(self.ptr, _stream_handle(stream))
@@ -366,6 +369,18 @@ class Rve:
         ln = (C.c_int64 * k)()
         LIB.mp_rve_profile_read(self.ptr, ms, ln, 1 if reset else 0)
         return {name: (ms[i], ln[i]) for i, name in enumerate(KERNEL_CLASSES)}
+
+    def trace(self, enable=True):
+        """Record (increment, iteration, err, err_e, err_t, err_gamma, err_m) per iteration."""
+        st = LIB.mp_rve_trace(self.ptr, 1 if enable else 0)
+        if st != MP_OK:
+            raise MicropolarError(st, self.ctx.error())
+
+    def trace_read(self, clear=True):
+        n = LIB.mp_rve_trace_read(self.ptr, None, 0, 0)
+        buf = np.zeros((max(n, 1), 7))
+        LIB.mp_rve_trace_read(self.ptr, buf.ctypes.data_as(_DP), n, 1 if clear else 0)
+        return buf[:n]
 
     @property
     def steps_done(self):

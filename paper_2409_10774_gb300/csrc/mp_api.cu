@@ -309,6 +309,9 @@ struct mp_rve {
   long long launches[MP_KC_COUNT] = {0};
   double kernel_ms[MP_KC_COUNT] = {0};
   bool profiling = false;
+  // convergence trace: (step, iteration, err, err_e, err_t, err_gamma, err_m) per iteration
+  bool tracing = false;
+  std::vector<double> trace;
   cudaEvent_t ev[2 * MP_KC_COUNT] = {};
 };
 
@@ -353,6 +356,7 @@ mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
   c.phase = reinterpret_cast<const uint16_t*>(r->phase.ptr);
   c.phases = reinterpret_cast<const PhaseDev<R>*>(r->phases.ptr);
   c.status = reinterpret_cast<int*>(r->status.ptr);
+  c.err_kind = r->err_kind;
   MP_CK(ctx, cudaMemsetAsync(r->status.ptr, 0, r->status.bytes, st));
   c.ref = ref_dev<R>(r->ref);
   std::vector<PhaseDev<R>> ph(p->n_phases);
@@ -442,6 +446,11 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
       }
     }
     err = r->err_host[0];
+    if (r->tracing) {
+      const double rec[7] = {(double)s, (double)(it + 1), r->err_host[0], r->err_host[1], r->err_host[2],
+                             r->err_host[3], r->err_host[4]};
+      r->trace.insert(r->trace.end(), rec, rec + 7);
+    }
     ++it;
     if (r->err_host[5] != 0.0) {
       status = MP_E_TIMEOUT;
@@ -622,6 +631,24 @@ mp_status mp_rve_profile(mp_rve* r, int32_t enable) {
   }
   r->profiling = enable != 0;
   return MP_OK;
+}
+
+mp_status mp_rve_trace(mp_rve* r, int32_t enable) {
+  if (!r) return set_error(nullptr, MP_E_INVALID_ARG, "rve is NULL");
+  r->tracing = enable != 0;
+  if (!r->tracing) r->trace.clear();
+  return MP_OK;
+}
+
+int64_t mp_rve_trace_read(mp_rve* r, double* out, int64_t capacity, int32_t clear) {
+  if (!r) return -1;
+  const int64_t n = (int64_t)(r->trace.size() / 7);
+  if (out) {
+    const int64_t k = n < capacity ? n : capacity;
+    std::memcpy(out, r->trace.data(), sizeof(double) * 7 * (size_t)k);
+  }
+  if (clear) r->trace.clear();
+  return n;
 }
 
 mp_status mp_rve_profile_read(const mp_rve* r, double* ms, int64_t* launches, int32_t reset) {

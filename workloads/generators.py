@@ -89,6 +89,30 @@ def laminate_map(n, axis=0, fraction=0.5):
     return out
 
 
+def _paint_sphere(phase, n, c, radius, value=1):
+    """Set ``value`` at every voxel whose centre lies within ``radius`` of c
+    (minimum-image distance), visiting only the periodic box around c.
+    Returns the number of voxels that changed to ``value``."""
+    idx = []
+    for a in range(3):
+        lo = int(np.floor(c[a] - radius - 0.5)) - 1
+        hi = int(np.ceil(c[a] + radius + 0.5)) + 1
+        if hi - lo >= n[a]:
+            i = np.arange(n[a])
+        else:
+            i = np.arange(lo, hi + 1) % n[a]
+        d = (i + 0.5) - c[a]
+        d = d - n[a] * np.round(d / n[a])
+        idx.append((i, d * d))
+    (i1, d1), (i2, d2), (i3, d3) = idx
+    inside = (d3[:, None, None] + d2[None, :, None] + d1[None, None, :]) <= radius * radius
+    sub = phase[np.ix_(i3, i2, i1)]
+    changed = int(np.count_nonzero(inside & (sub != value)))
+    sub[inside] = value
+    phase[np.ix_(i3, i2, i1)] = sub
+    return changed
+
+
 def rsa_sphere_map(n, radius, volume_fraction, seed, max_tries=200000):
     """Random sequential addition of periodic, non-overlapping equal spheres.
 
@@ -99,26 +123,24 @@ def rsa_sphere_map(n, radius, volume_fraction, seed, max_tries=200000):
     rng = np.random.Generator(np.random.PCG64(seed))
     n = tuple(int(v) for v in n)
     L = np.array(n, dtype=np.float64)
-    centres = []
+    centres = np.empty((0, 3))
     phase = np.zeros((n[2], n[1], n[0]), dtype=np.uint16)
+    size = phase.size
+    filled = 0
     tries = 0
-    while phase.mean() < volume_fraction:
+    while filled / size < volume_fraction:
         tries += 1
         if tries > max_tries:
             raise RuntimeError("RSA did not reach the requested volume fraction")
         c = rng.uniform(0.0, 1.0, 3) * L
-        ok = True
-        for q in centres:
-            d = c - q
+        if len(centres):
+            d = c[None, :] - centres
             d -= L * np.round(d / L)
-            if np.dot(d, d) < (2.0 * radius) ** 2:
-                ok = False
-                break
-        if not ok:
-            continue
-        centres.append(c)
-        phase[_periodic_dist2(n, c) <= radius * radius] = 1
-    return phase, np.array(centres)
+            if np.any((d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]) < (2.0 * radius) ** 2):
+                continue
+        centres = np.vstack([centres, c[None, :]])
+        filled += _paint_sphere(phase, n, c, radius)
+    return phase, centres
 
 
 def voronoi_seeds(n_cells, box, seed):

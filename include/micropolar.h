@@ -107,6 +107,7 @@ typedef struct mp_result {
   double *T, *M, *Eavg, *Gavg;
   double *P, *Q, *Teq, *Meq, *err;
   int32_t* iters;
+  int32_t* iters_fp64;          /* per step: iterations run in FP64 (see mp_batch_solve)  */
   double *e, *g, *t, *m, *p, *q;
   int32_t steps_done;           /* out: steps committed                                   */
   int32_t failed_step;          /* out: 1-based step that failed, 0 if none               */

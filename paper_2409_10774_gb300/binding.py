@@ -65,6 +65,7 @@ _DP = C.POINTER(C.c_double)
 class mp_result(C.Structure):
     _fields_ = [("T", _DP), ("M", _DP), ("Eavg", _DP), ("Gavg", _DP), ("P", _DP), ("Q", _DP),
                 ("Teq", _DP), ("Meq", _DP), ("err", _DP), ("iters", C.POINTER(C.c_int32)),
+                ("iters_fp64", C.POINTER(C.c_int32)),
                 ("e", _DP), ("g", _DP), ("t", _DP), ("m", _DP), ("p", _DP), ("q", _DP),
                 ("steps_done", C.c_int32), ("failed_step", C.c_int32),
                 ("ref_moduli_used", C.c_double * 6)]
@@ -206,6 +207,7 @@ class _Result:
         self.arrs = {k: np.zeros((ns, 9)) for k in ("T", "M", "Eavg", "Gavg")}
         self.arrs.update({k: np.zeros(ns) for k in ("P", "Q", "Teq", "Meq", "err")})
         self.iters = np.zeros(ns, dtype=np.int32)
+        self.iters64 = np.zeros(ns, dtype=np.int32)
         self.fields = {}
         if fields:
             self.fields = {k: np.zeros((nv, 9)) for k in ("e", "g", "t", "m")}
@@ -214,6 +216,7 @@ class _Result:
         for k, a in self.arrs.items():
             setattr(self.st, k, _dptr(a))
         self.st.iters = self.iters.ctypes.data_as(C.POINTER(C.c_int32))
+        self.st.iters_fp64 = self.iters64.ctypes.data_as(C.POINTER(C.c_int32))
         for k, a in self.fields.items():
             setattr(self.st, k, _dptr(a))
         self.n = n
@@ -224,6 +227,7 @@ class _Result:
         for k in ("T", "M", "Eavg", "Gavg"):
             out[k] = out[k].reshape(ns, 3, 3)
         out["iters"] = self.iters[:ns].astype(np.int64)
+        out["iters_fp64"] = self.iters64[:ns].astype(np.int64)
         out["steps_done"] = ns
         out["failed_step"] = self.st.failed_step
         out["ref_moduli"] = tuple(self.st.ref_moduli_used)

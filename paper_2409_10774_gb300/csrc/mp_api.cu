@@ -724,6 +724,7 @@ mp_status mp_rve_results(mp_rve* r, mp_result* res, void* stream) {
     if (res->Meq) res->Meq[s] = row[39];
     if (res->err) res->err[s] = r->err_steps[s];
     if (res->iters) res->iters[s] = r->iters_steps[s];
+    if (res->iters_fp64) res->iters_fp64[s] = r->precision == 0 ? r->iters_steps[s] : 0;
   }
   res->steps_done = ns;
   res->failed_step = r->failed_step;

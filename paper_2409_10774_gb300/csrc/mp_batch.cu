@@ -184,13 +184,59 @@ struct ArenaLayout {
 };
 
 // ------------------------------------------------------------------ engine
+// Host-side progress of one cell through its load path (precision-free, so
+// it moves with the cell between the FP32 and FP64 engines).
+struct Progress {
+  enum State { kInit, kStart, kIter, kCommit, kFinished };
+  Request* req = nullptr;
+  State state = kInit;
+  int s = 1;  // current increment (1-based)
+  int it = 0;
+  double err = 0.0;
+  mp_status step_status = MP_OK;
+  bool predicted = false;
+  int steps_done = 0, failed_step = 0;
+  std::vector<double> err_steps;
+  std::vector<int> iters_steps, iters64_steps;
+  int it64 = 0;             // iterations of the current increment run in FP64
+  double ref_err = 0.0;     // stagnation watch (FP32): error level and iteration
+  int it_ref = 0;           //   at which it last halved
+  bool escalate = false;    // FP32 iteration stagnated: finish the increment in FP64
+  bool demote = false;      // FP64-finished increment committed: next one in FP32
+};
+
+// An FP32-mixed cell whose error has not halved in this many iterations while
+// still above the tolerance finishes the increment in FP64 (the FP32 fields
+// have reached their rounding floor, which for strongly heterogeneous
+// plastic cells can sit above the tolerance of the local error measure).
+constexpr int kStagnationIters = 64;
+
+template <class R>
+struct Slot {
+  Progress g;
+  unsigned char* arena = nullptr;
+  size_t bytes = 0;
+  CellDev<R> c{};
+  LaunchCfg L;
+  double* rows = nullptr;    // [n_steps][kAvgPartials] per-increment results
+  double* fields = nullptr;  // [38][nvox] FP64 final fields (when requested)
+};
+
+template <class R>
+class Engine;
+template <class RA, class RB>
+int migrate(Engine<RA>& from, Engine<RB>& to);
+
 // Round-based multi-cell driver for one precision.
 template <class R>
 class Engine {
+  template <class RA, class RB>
+  friend int migrate(Engine<RA>& from, Engine<RB>& to);
+
  public:
   Engine(mp_ctx* ctx, Pool* pool, cudaStream_t st) : ctx_(ctx), pool_(pool), st_(st) {}
   ~Engine() {
-    for (Slot& s : slots_) release(s);
+    for (Slot<R>& s : slots_) release(s);
     slots_.clear();
     free_meta();
   }
@@ -211,8 +257,156 @@ class Engine {
   // Allocates the cell's arena and uploads its tables.  MP_E_OOM when the
   // pool cannot hold it now (nothing is changed then).
   mp_status admit(Request* q) {
-    Slot s;
-    s.req = q;
+    Slot<R> s;
+    s.g.req = q;
+    mp_status st = build_slot(s, true);
+    if (st != MP_OK) return st;
+    s.g.state = Progress::kInit;
+    resident_ += s.bytes;
+    slots_.push_back(std::move(s));
+    return MP_OK;
+  }
+
+  // Drops every resident request as MP_E_CANCELLED (arenas released).
+  void cancel_all(std::vector<Request*>& finished) {
+    for (Slot<R>& s : slots_) {
+      s.g.req->status = MP_E_CANCELLED;
+      s.g.req->message = "cancelled: the server was destroyed";
+      finished.push_back(s.g.req);
+      release(s);
+    }
+    slots_.clear();
+  }
+
+  // One round.  Requests whose solve ended are appended to `finished` (their
+  // results written, their arenas released).  A CUDA failure fails every
+  // resident request and returns MP_E_CUDA.
+  mp_status round(std::vector<Request*>& finished) {
+    if (slots_.empty()) return MP_OK;
+    ++rounds_;
+    const int n = (int)slots_.size();
+    constexpr bool kFp64 = sizeof(R) == 8;
+    std::vector<int> l_commit, l_init, l_start, l_iter;
+    for (int i = 0; i < n; ++i) {
+      Slot<R>& sl = slots_[i];
+      Progress& g = sl.g;
+      CellDev<R>& c = sl.c;
+      const Request& q = *g.req;
+      c.err_out = nullptr;
+      if (g.state == Progress::kCommit) {
+        const bool predict = g.step_status == MP_OK && g.s < q.n_steps;
+        c.predict = predict ? 1 : 0;
+        c.ratio = predict ? (q.time[g.s + 1] - q.time[g.s]) / (q.time[g.s] - q.time[g.s - 1]) : 0.0;
+        c.avg_out = sl.rows + (size_t)kAvgPartials * (g.s - 1);
+        l_commit.push_back(i);
+        g.predicted = predict;
+        g.steps_done = g.s;
+        if (g.step_status != MP_OK) {
+          g.failed_step = g.s;
+          g.state = Progress::kFinished;
+        } else if (g.s == q.n_steps) {
+          g.state = Progress::kFinished;
+        } else {
+          g.s += 1;
+          g.state = Progress::kStart;
+          // an FP32-mixed cell that finished this increment in FP64 starts the
+          // next one in FP32 again (it moves after this round's commit)
+          if (kFp64 && q.precision == 1) {
+            g.demote = true;
+            continue;
+          }
+        }
+      }
+      if (g.state == Progress::kInit || g.state == Progress::kStart) {
+        for (int k = 0; k < 9; ++k) {
+          c.E[k] = (R)q.E[9 * g.s + k];
+          c.G[k] = (R)q.G[9 * g.s + k];
+        }
+        if (g.state == Progress::kInit) l_init.push_back(i);
+        l_start.push_back(i);
+        g.state = Progress::kIter;
+        g.it = 0;
+        g.it64 = 0;
+        g.err = 2.0 * q.tol;
+        g.ref_err = 0.0;
+        g.it_ref = 0;
+      }
+      if (g.state == Progress::kIter) l_iter.push_back(i);
+    }
+    mp_status st = upload_and_launch(l_commit, l_init, l_start, l_iter);
+    if (st != MP_OK) return fail_all(finished, st);
+    // decisions (Algorithm 2's loop test, per cell)
+    for (size_t k = 0; k < l_iter.size(); ++k) {
+      Slot<R>& sl = slots_[l_iter[k]];
+      Progress& g = sl.g;
+      const Request& q = *g.req;
+      const double* e = h_err_ + 8 * (size_t)l_iter[k];
+      g.err = e[0];
+      g.it += 1;
+      if (kFp64) g.it64 += 1;
+      voxel_iters_ += q.nvox;
+      const int target = q.lockstep.empty() ? -1 : q.lockstep[g.s - 1];
+      mp_status out = MP_OK;
+      bool leave = false;
+      if (e[5] != 0.0) {
+        out = MP_E_TIMEOUT;
+        leave = true;
+      } else if (!std::isfinite(g.err) || g.err > q.div_limit) {
+        out = MP_E_DIVERGED;
+        leave = true;
+      } else {
+        const bool more = target >= 0 ? g.it < target : g.err > q.tol;
+        if (!more) leave = true;
+        else if (target < 0 && g.it >= q.max_iter) {
+          out = MP_E_NOT_CONVERGED;
+          leave = true;
+        }
+      }
+      if (!leave) {
+        // FP32 stagnation watch (not under a prescribed iteration schedule)
+        if (!kFp64 && target < 0) {
+          if (g.it_ref == 0 || g.err < 0.5 * g.ref_err) {
+            g.ref_err = g.err;
+            g.it_ref = g.it;
+          } else if (g.it - g.it_ref >= kStagnationIters) {
+            g.escalate = true;
+          }
+        }
+        continue;
+      }
+      g.step_status = out;
+      if (out == MP_E_TIMEOUT) {
+        g.failed_step = g.s;
+        g.steps_done = g.s - 1;
+        g.state = Progress::kFinished;
+      } else {
+        g.err_steps.push_back(g.err);
+        g.iters_steps.push_back(g.it);
+        g.iters64_steps.push_back(g.it64);
+        g.state = Progress::kCommit;
+      }
+    }
+    // harvest
+    for (int i = 0; i < (int)slots_.size();) {
+      if (slots_[i].g.state != Progress::kFinished) {
+        ++i;
+        continue;
+      }
+      Slot<R>& s = slots_[i];
+      harvest(s);
+      finished.push_back(s.g.req);
+      release(s);
+      slots_[i] = std::move(slots_.back());
+      slots_.pop_back();
+    }
+    return MP_OK;
+  }
+
+ private:
+  // Arena and device tables of the slot's request at this precision (rows
+  // zeroed when fresh).
+  mp_status build_slot(Slot<R>& s, bool fresh) {
+    Request* q = s.g.req;
     s.c = shape_of(*q);
     s.L = make_launch_cfg<R>(s.c, ctx_->nsm);
     const ArenaLayout<R> A(*q, s.L.items_a);
@@ -237,6 +431,10 @@ class Engine {
     s.fields = q->want_fields ? reinterpret_cast<double*>(b + A.fields) : nullptr;
     c.ref = ref_dev<R>(q->ref);
     c.err_kind = q->err_kind;
+    for (int k = 0; k < 9; ++k) {  // load of the current increment (a cell may move mid-increment)
+      c.E[k] = (R)q->E[9 * s.g.s + k];
+      c.G[k] = (R)q->G[9 * s.g.s + k];
+    }
     std::vector<PhaseDev<R>> ph(q->phases.size());
     for (size_t k = 0; k < ph.size(); ++k) ph[k] = phase_dev<R>(q->phases[k]);
     AxisPlan<R>* plans[3] = {&c.px, &c.py, &c.pz};
@@ -253,156 +451,17 @@ class Engine {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(b + A.phases, ph.data(), sizeof(PhaseDev<R>) * ph.size(), cudaMemcpyHostToDevice, st_);
     if (e == cudaSuccess) e = cudaMemsetAsync(b + A.status, 0, sizeof(int) * 4, st_);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s.rows, 0, sizeof(double) * kAvgPartials * q->n_steps, st_);
+    if (e == cudaSuccess && fresh) e = cudaMemsetAsync(s.rows, 0, sizeof(double) * kAvgPartials * q->n_steps, st_);
     // the host tables above are locals: the copies must have read them
     if (e == cudaSuccess) e = cudaStreamSynchronize(st_);
     if (e != cudaSuccess) {
       pool_->give(s.arena, s.bytes);
+      s.arena = nullptr;
       q->message = std::string("admission: ") + cudaGetErrorString(e);
       return MP_E_CUDA;
     }
-    s.state = Slot::kInit;
-    resident_ += s.bytes;
-    slots_.push_back(std::move(s));
     return MP_OK;
   }
-
-  // Drops every resident request as MP_E_CANCELLED (arenas released).
-  void cancel_all(std::vector<Request*>& finished) {
-    for (Slot& s : slots_) {
-      s.req->status = MP_E_CANCELLED;
-      s.req->message = "cancelled: the server was destroyed";
-      finished.push_back(s.req);
-      release(s);
-    }
-    slots_.clear();
-  }
-
-  // One round.  Requests whose solve ended are appended to `finished` (their
-  // results written, their arenas released).  A CUDA failure fails every
-  // resident request and returns MP_E_CUDA.
-  mp_status round(std::vector<Request*>& finished) {
-    if (slots_.empty()) return MP_OK;
-    ++rounds_;
-    const int n = (int)slots_.size();
-    std::vector<int> l_commit, l_init, l_start, l_iter;
-    for (int i = 0; i < n; ++i) {
-      Slot& s = slots_[i];
-      CellDev<R>& c = s.c;
-      c.err_out = nullptr;
-      if (s.state == Slot::kCommit) {
-        const Request& q = *s.req;
-        const bool predict = s.step_status == MP_OK && s.s < q.n_steps;
-        c.predict = predict ? 1 : 0;
-        c.ratio = predict ? (q.time[s.s + 1] - q.time[s.s]) / (q.time[s.s] - q.time[s.s - 1]) : 0.0;
-        c.avg_out = s.rows + (size_t)kAvgPartials * (s.s - 1);
-        l_commit.push_back(i);
-        s.predicted = predict;
-        s.steps_done = s.s;
-        if (s.step_status != MP_OK) {
-          s.failed_step = s.s;
-          s.state = Slot::kFinished;
-        } else if (s.s == q.n_steps) {
-          s.state = Slot::kFinished;
-        } else {
-          s.s += 1;
-          s.state = Slot::kStart;
-        }
-      }
-      if (s.state == Slot::kInit || s.state == Slot::kStart) {
-        const Request& q = *s.req;
-        for (int k = 0; k < 9; ++k) {
-          c.E[k] = (R)q.E[9 * s.s + k];
-          c.G[k] = (R)q.G[9 * s.s + k];
-        }
-        if (s.state == Slot::kInit) l_init.push_back(i);
-        l_start.push_back(i);
-        s.state = Slot::kIter;
-        s.it = 0;
-        s.err = 2.0 * q.tol;
-      }
-      if (s.state == Slot::kIter) {
-        c.err_out = nullptr;  // set below once the table index is known
-        l_iter.push_back(i);
-      }
-    }
-    mp_status st = upload_and_launch(l_commit, l_init, l_start, l_iter);
-    if (st != MP_OK) return fail_all(finished, st);
-    // decisions (Algorithm 2's loop test, per cell)
-    for (size_t k = 0; k < l_iter.size(); ++k) {
-      Slot& s = slots_[l_iter[k]];
-      const Request& q = *s.req;
-      const double* e = h_err_ + 8 * (size_t)l_iter[k];
-      s.err = e[0];
-      s.it += 1;
-      voxel_iters_ += q.nvox;
-      const int target = q.lockstep.empty() ? -1 : q.lockstep[s.s - 1];
-      mp_status out = MP_OK;
-      bool leave = false;
-      if (e[5] != 0.0) {
-        out = MP_E_TIMEOUT;
-        leave = true;
-      } else if (!std::isfinite(s.err) || s.err > q.div_limit) {
-        out = MP_E_DIVERGED;
-        leave = true;
-      } else {
-        const bool more = target >= 0 ? s.it < target : s.err > q.tol;
-        if (!more) leave = true;
-        else if (target < 0 && s.it >= q.max_iter) {
-          out = MP_E_NOT_CONVERGED;
-          leave = true;
-        }
-      }
-      if (!leave) continue;
-      s.step_status = out;
-      s.err_steps.push_back(s.err);
-      s.iters_steps.push_back(s.it);
-      if (out == MP_E_TIMEOUT) {
-        s.failed_step = s.s;
-        s.steps_done = s.s - 1;
-        s.err_steps.pop_back();
-        s.iters_steps.pop_back();
-        s.state = Slot::kFinished;
-      } else {
-        s.state = Slot::kCommit;
-      }
-    }
-    // harvest
-    for (int i = 0; i < (int)slots_.size();) {
-      if (slots_[i].state != Slot::kFinished) {
-        ++i;
-        continue;
-      }
-      Slot& s = slots_[i];
-      harvest(s);
-      finished.push_back(s.req);
-      release(s);
-      slots_[i] = std::move(slots_.back());
-      slots_.pop_back();
-    }
-    return MP_OK;
-  }
-
- private:
-  struct Slot {
-    enum State { kInit, kStart, kIter, kCommit, kFinished };
-    Request* req = nullptr;
-    unsigned char* arena = nullptr;
-    size_t bytes = 0;
-    CellDev<R> c{};
-    LaunchCfg L;
-    double* rows = nullptr;    // [n_steps][kAvgPartials] per-increment results
-    double* fields = nullptr;  // [38][nvox] FP64 final fields (when requested)
-    State state = kInit;
-    int s = 1;  // current increment (1-based)
-    int it = 0;
-    double err = 0.0;
-    mp_status step_status = MP_OK;
-    bool predicted = false;
-    int steps_done = 0, failed_step = 0;
-    std::vector<double> err_steps;
-    std::vector<int> iters_steps;
-  };
 
   CellDev<R> shape_of(const Request& q) const {
     CellDev<R> c{};
@@ -418,7 +477,7 @@ class Engine {
     return c;
   }
 
-  void release(Slot& s) {
+  void release(Slot<R>& s) {
     if (s.arena) {
       pool_->give(s.arena, s.bytes);
       resident_ -= s.bytes;
@@ -509,12 +568,12 @@ class Engine {
       w.n_act = k;
       *items[f] = pre[k];
     };
-    fill(kFY, l_iter, [](const Slot& s) { return s.c.n2 > 1 ? (long long)s.c.n3 * s.c.kx : 0ll; });
-    fill(kFZ, l_iter, [](const Slot& s) { return (long long)s.c.n2 * s.c.kx; });
-    fill(kFA, l_iter, [](const Slot& s) { return s.c.items_a; });
-    fill(kFS, l_start, [](const Slot& s) { return s.c.items_a; });
-    fill(kFV, l_commit, [](const Slot& s) { return (s.c.nvox + 255) / 256; });
-    fill(kFV0, l_init, [](const Slot& s) { return (s.c.nvox + 255) / 256; });
+    fill(kFY, l_iter, [](const Slot<R>& s) { return s.c.n2 > 1 ? (long long)s.c.n3 * s.c.kx : 0ll; });
+    fill(kFZ, l_iter, [](const Slot<R>& s) { return (long long)s.c.n2 * s.c.kx; });
+    fill(kFA, l_iter, [](const Slot<R>& s) { return s.c.items_a; });
+    fill(kFS, l_start, [](const Slot<R>& s) { return s.c.items_a; });
+    fill(kFV, l_commit, [](const Slot<R>& s) { return (s.c.nvox + 255) / 256; });
+    fill(kFV0, l_init, [](const Slot<R>& s) { return (s.c.nvox + 255) / 256; });
     for (int i : l_iter) {
       const CellDev<R>& c = slots_[i].c;
       m.smem_y = std::max(m.smem_y, c.n2 > 1 ? smem_line_pass<R>(c.n2) : (size_t)0);
@@ -537,21 +596,22 @@ class Engine {
     return MP_OK;
   }
 
-  void harvest(Slot& s) {
-    Request& q = *s.req;
+  void harvest(Slot<R>& s) {
+    const Progress& g = s.g;
+    Request& q = *g.req;
     mp_result* res = q.res;
-    q.status = (s.failed_step && s.step_status != MP_OK) ? s.step_status : MP_OK;
+    q.status = (g.failed_step && g.step_status != MP_OK) ? g.step_status : MP_OK;
     if (q.status != MP_OK) {
       char buf[256];
       if (q.status == MP_E_TIMEOUT)
-        std::snprintf(buf, sizeof(buf), "load increment %d: a bounded device wait expired", s.failed_step);
+        std::snprintf(buf, sizeof(buf), "load increment %d: a bounded device wait expired", g.failed_step);
       else
-        std::snprintf(buf, sizeof(buf), "load increment %d %s after %d iterations (err %.3e)", s.failed_step,
-                      q.status == MP_E_DIVERGED ? "diverged" : "did not converge", s.it, s.err);
+        std::snprintf(buf, sizeof(buf), "load increment %d %s after %d iterations (err %.3e)", g.failed_step,
+                      q.status == MP_E_DIVERGED ? "diverged" : "did not converge", g.it, g.err);
       q.message = buf;
     }
     if (!res) return;
-    const int ns = s.steps_done;
+    const int ns = g.steps_done;
     std::vector<double> rows((size_t)kAvgPartials * (ns > 0 ? ns : 1));
     cudaError_t e = cudaSuccess;
     if (ns > 0)
@@ -560,7 +620,7 @@ class Engine {
       const size_t nv = (size_t)q.nvox;
       double* b = s.fields;
       double *fe = b, *fg = b + 9 * nv, *ft = b + 18 * nv, *fm = b + 27 * nv, *fp = b + 36 * nv, *fq = b + 37 * nv;
-      e = launch_fields<R>(s.L, s.c, s.predicted ? 1 : 0, fe, fg, ft, fm, fp, fq, st_);
+      e = launch_fields<R>(s.L, s.c, g.predicted ? 1 : 0, fe, fg, ft, fm, fp, fq, st_);
       struct {
         double* dst;
         double* src;
@@ -589,20 +649,21 @@ class Engine {
       if (res->Q) res->Q[k] = row[37];
       if (res->Teq) res->Teq[k] = row[38];
       if (res->Meq) res->Meq[k] = row[39];
-      if (res->err) res->err[k] = s.err_steps[k];
-      if (res->iters) res->iters[k] = s.iters_steps[k];
+      if (res->err) res->err[k] = g.err_steps[k];
+      if (res->iters) res->iters[k] = g.iters_steps[k];
+      if (res->iters_fp64) res->iters_fp64[k] = g.iters64_steps[k];
     }
     res->steps_done = ns;
-    res->failed_step = s.failed_step;
+    res->failed_step = g.failed_step;
     for (int i = 0; i < 6; ++i) res->ref_moduli_used[i] = q.ref[i];
   }
 
   mp_status fail_all(std::vector<Request*>& finished, mp_status st) {
     cudaStreamSynchronize(st_);  // no kernel of this round may still use an arena
-    for (Slot& s : slots_) {
-      s.req->status = st;
-      s.req->message = "device failure during a batched round: " + last_cuda_;
-      finished.push_back(s.req);
+    for (Slot<R>& s : slots_) {
+      s.g.req->status = st;
+      s.g.req->message = "device failure during a batched round: " + last_cuda_;
+      finished.push_back(s.g.req);
       release(s);
     }
     slots_.clear();
@@ -612,7 +673,7 @@ class Engine {
   mp_ctx* ctx_;
   Pool* pool_;
   cudaStream_t st_;
-  std::vector<Slot> slots_;
+  std::vector<Slot<R>> slots_;
   size_t resident_ = 0;
   int64_t voxel_iters_ = 0, rounds_ = 0;
   void* d_meta_ = nullptr;
@@ -623,7 +684,66 @@ class Engine {
   std::string last_cuda_;
 };
 
+// Moves the flagged cells of `from` (FP32 cells whose iteration stagnated, or
+// FP64-finished FP32-mixed cells about to start their next increment) to the
+// engine of the other precision: the arena is rebuilt there and the state
+// (iterate, history, plastic strains, predictor, result rows and, mid-
+// increment, the polarization spectrum) is converted on the device.  A cell
+// whose new arena does not fit stays where it is.  Returns the number moved.
+template <class RA, class RB>
+int migrate(Engine<RA>& from, Engine<RB>& to) {
+  int moved = 0;
+  for (size_t i = 0; i < from.slots_.size();) {
+    Slot<RA>& src = from.slots_[i];
+    const bool flagged = (sizeof(RA) == 4) ? src.g.escalate : src.g.demote;
+    if (!flagged) {
+      ++i;
+      continue;
+    }
+    Slot<RB> dst;
+    dst.g = src.g;
+    dst.g.escalate = dst.g.demote = false;
+    if (to.build_slot(dst, false) != MP_OK) {
+      src.g.escalate = src.g.demote = false;
+      src.g.it_ref = src.g.it;  // watch again before the next attempt
+      ++i;
+      continue;
+    }
+    const Request& q = *src.g.req;
+    const long long nv = q.nvox;
+    cudaStream_t st = to.st_;
+    const int nsm = to.ctx_->nsm;
+    cudaError_t e = launch_convert<RA, RB>(src.c.prev, dst.c.prev, 20 * nv, nsm, st);
+    if (e == cudaSuccess) e = launch_convert<RA, RB>(src.c.hist, dst.c.hist, 20 * nv, nsm, st);
+    if (e == cudaSuccess) e = launch_convert<RA, RB>(src.c.elast, dst.c.elast, 18 * nv, nsm, st);
+    if (e == cudaSuccess && src.g.state == Progress::kIter)
+      e = launch_convert<RA, RB>(reinterpret_cast<const RA*>(src.c.spec), reinterpret_cast<RB*>(dst.c.spec),
+                                 36 * src.c.nspec, nsm, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dst.c.pq, src.c.pq, sizeof(double) * 2 * nv, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dst.rows, src.rows, sizeof(double) * kAvgPartials * q.n_steps, cudaMemcpyDeviceToDevice,
+                          st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      to.pool_->give(dst.arena, dst.bytes);
+      src.g.escalate = src.g.demote = false;
+      src.g.it_ref = src.g.it;
+      ++i;
+      continue;
+    }
+    to.resident_ += dst.bytes;
+    to.slots_.push_back(std::move(dst));
+    from.release(src);
+    from.slots_[i] = std::move(from.slots_.back());
+    from.slots_.pop_back();
+    ++moved;
+  }
+  return moved;
+}
+
 }  // namespace
+
 
 // ================================================================== server
 struct mp_server {
@@ -683,6 +803,8 @@ void server_loop(mp_server* S) {
     std::vector<Request*> fin;
     S->ef->round(fin);
     S->ed->round(fin);
+    migrate(*S->ef, *S->ed);
+    migrate(*S->ed, *S->ef);
     lk.lock();
     for (Request* q : fin) q->done = true;
     S->completed += (int64_t)fin.size();
@@ -745,6 +867,10 @@ mp_status mp_batch_solve(mp_ctx* ctx, const mp_problem* const* problems, int32_t
       }
       std::vector<Request*> fin;
       if (ef.round(fin) == MP_E_CUDA || ed.round(fin) == MP_E_CUDA) broken = true;
+      if (!broken) {
+        migrate(ef, ed);
+        migrate(ed, ef);
+      }
     }
     for (Request* q : pending) {
       q->status = MP_E_CUDA;

@@ -1118,6 +1118,25 @@ cudaError_t launch_radial_return(int nsm, long long count, const uint16_t* phase
   return cudaGetLastError();
 }
 
+// Element-wise precision conversion of device state (cells moving between
+// the FP32 and FP64 engines).
+template <class S, class D>
+__global__ void k_convert(const S* __restrict__ src, D* __restrict__ dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (D)src[i];
+}
+
+template <class S, class D>
+cudaError_t launch_convert(const S* src, D* dst, long long n, int nsm, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 8ll * nsm) blocks = 8ll * nsm;
+  k_convert<S, D><<<(int)blocks, 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_convert<float, double>(const float*, double*, long long, int, cudaStream_t);
+template cudaError_t launch_convert<double, float>(const double*, float*, long long, int, cudaStream_t);
+
 template <class R>
 LaunchCfg make_launch_cfg(const CellDev<R>& c, int nsm) {
   set_smem_attrs<R>();

@@ -80,4 +80,8 @@ cudaError_t launch_radial_return(int nsm, long long count, const uint16_t* phase
                                  const double* q_n, R* t, R* m, double* p, double* q,
                                  cudaStream_t st);
 
+// dst[i] = (D) src[i], i < n (state of a cell changing precision).
+template <class S, class D>
+cudaError_t launch_convert(const S* src, D* dst, long long n, int nsm, cudaStream_t st);
+
 }  // namespace mp

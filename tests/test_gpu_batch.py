@@ -186,11 +186,11 @@ def test_server_concurrent_submitters(ctx):
 def test_server_budget_bounds_residency(ctx):
     import paper_2409_10774_gb300 as M
     from paper_2409_10774_gb300 import binding as B
-    probs = _small_batch(3, (32,), 2, 1e-6, seed=W.seed_for(4) + 19)
-    alone = M.mp_batch_solve(ctx, probs, precision=1)
-    # one 32^3 FP32 cell needs ~11 MB: a 16 MiB budget holds one at a time
-    with M.Server(ctx, budget_bytes=16 << 20) as srv:
-        ts = [srv.submit(p, precision=1) for p in probs]
+    probs = _small_batch(3, (16,), 2, 1e-8, seed=W.seed_for(4) + 19)
+    alone = M.mp_batch_solve(ctx, probs, precision=0)
+    # one 16^3 FP64 cell needs ~2.7 MB: a 4 MiB budget holds one at a time
+    with M.Server(ctx, budget_bytes=4 << 20) as srv:
+        ts = [srv.submit(p, precision=0) for p in probs]
         got = [srv.wait(t) for t in ts]
         st = srv.stats()
         big = W.workload_serving_request(1, sizes=(64,))
@@ -199,6 +199,7 @@ def test_server_budget_bounds_residency(ctx):
         assert ei.value.status == 6
     assert st["peak_resident"] == 1
     for g, a in zip(got, alone):
+        assert g["status"] == "ok"
         _assert_identical(g, a, fields=False)
 
 
@@ -217,3 +218,31 @@ def test_server_wait_timeout_and_cancel(ctx):
     for _ in range(3):
         srv.submit(req, precision=1)
     srv.close()
+
+
+def _truncate(problem, n_steps):
+    p = dict(problem)
+    p["time"] = problem["time"][: n_steps + 1]
+    p["E"] = problem["E"][: n_steps + 1]
+    p["G"] = problem["G"][: n_steps + 1]
+    return p
+
+
+def test_batch_fp32_escalates_stagnating_cells(ctx):
+    """A strongly plastic cell whose FP32 iteration stalls above the tolerance
+    of the local error measure finishes those increments in FP64 and
+    converges; it agrees with the plain FP64 solve to the tolerance's level and
+    is the same alone and beside another cell."""
+    import paper_2409_10774_gb300 as M
+    p = _truncate(W.workload_serving_request(0), 3)
+    r32 = M.mp_batch_solve(ctx, [p], precision=1)[0]
+    r64 = M.mp_batch_solve(ctx, [p], precision=0)[0]
+    assert r32["status"] == "ok" and r64["status"] == "ok"
+    assert r32["iters_fp64"].sum() > 0
+    assert np.all(r32["iters_fp64"] <= r32["iters"])
+    assert list(r64["iters_fp64"]) == list(r64["iters"])
+    assert np.all(r32["err"] <= p["tol"])
+    assert _rel(r32["T"], r64["T"]) <= 1e-5
+    other = _small_batch(1, (16,), 3, 1e-6, seed=W.seed_for(4) + 23)[0]
+    mix = M.mp_batch_solve(ctx, [other, p], precision=1)
+    _assert_identical(mix[1], r32, fields=False)

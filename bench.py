@@ -419,7 +419,8 @@ def run_batch_leg(args):
     sampler = ClockSampler(0)
     sampler.start()
     t0 = time.perf_counter()
-    res = M.mp_batch_solve(ctx, probs, precision=1, stream=stream)
+    bstats = {}
+    res = M.mp_batch_solve(ctx, probs, precision=1, stream=stream, stats=bstats)
     torch.cuda.synchronize(dev)
     secs = time.perf_counter() - t0
     clocks = sampler.stop()
@@ -453,6 +454,7 @@ def run_batch_leg(args):
                    "voxels_total": int(sum(nvox)), "increments": 10, "tol": 1e-6, "err": "local",
                    "ref_medium": "midrange", "generation_s": t_gen},
         "statuses": statuses,
+        "engine": bstats,
         "iterations_per_rve": {"p50": _percentile(iters, 50), "p90": _percentile(iters, 90),
                                "max": int(iters.max())},
         "fp64_single": fp64,

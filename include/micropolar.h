@@ -201,8 +201,16 @@ mp_status mp_rve_profile_read(const mp_rve* rve, double* ms, int64_t* launches, 
  * mp_last_error(ctx)).  Device memory for each cell is taken from the
  * context's allocator when the cell is admitted and released when it ends;
  * cells that do not fit wait until earlier ones finish. */
+typedef struct mp_batch_stats {
+  int64_t rounds;              /* rounds of the FP32 and of the FP64 engine                 */
+  int64_t rounds_fp64;
+  int64_t voxel_iters;         /* voxels x fixed-point iterations, all cells               */
+  int64_t voxel_iters_fp64;    /* ... of them run in FP64                                  */
+  int64_t escalations;         /* FP32 increments finished in FP64                         */
+} mp_batch_stats;
+/* stats (may be NULL) receives the work counters of the call. */
 mp_status mp_batch_solve(mp_ctx* ctx, const mp_problem* const* problems, int32_t count,
-                         mp_result* results, mp_status* per_item, void* stream);
+                         mp_result* results, mp_status* per_item, void* stream, mp_batch_stats* stats);
 
 /* Serving (continuous batching) ---------------------------------------------
  * A server owns one block of device memory (its HBM budget), one stream and

@@ -79,6 +79,11 @@ class mp_alloc(C.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
 
 
+class mp_batch_stats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("rounds", "rounds_fp64", "voxel_iters", "voxel_iters_fp64",
+                                         "escalations")]
+
+
 class mp_server_opts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_resident", C.c_int32), ("reserved", C.c_int32)]
 
@@ -118,7 +123,8 @@ def _load():
                                             V]),
         "mp_rve_trace": (C.c_int, [V, C.c_int32]),
         "mp_rve_trace_read": (C.c_int64, [V, P(C.c_double), C.c_int64, C.c_int32]),
-        "mp_batch_solve": (C.c_int, [V, P(P(mp_problem)), C.c_int32, P(mp_result), P(C.c_int), V]),
+        "mp_batch_solve": (C.c_int, [V, P(P(mp_problem)), C.c_int32, P(mp_result), P(C.c_int), V,
+                                     P(mp_batch_stats)]),
         "mp_server_create": (C.c_int, [V, P(mp_server_opts), P(V)]),
         "mp_server_submit": (C.c_int, [V, P(mp_problem), P(mp_result), P(C.c_uint64)]),
         "mp_server_wait": (C.c_int, [V, C.c_uint64, C.c_int32]),
@@ -495,11 +501,12 @@ def _per_item(value, count):
 
 
 def mp_batch_solve(ctx, problems, precision=None, fields=False, lockstep_iters=None, div_limit=0.0,
-                   stream=None):
+                   stream=None, stats=None):
     """Solve many cells together (mp_batch_solve).  `precision`, `fields`,
     `lockstep_iters` and `div_limit` are one value for all problems or a list
     with one entry per problem.  Returns one result dict per problem, shaped
-    like mp_solve's, each with its own 'status'."""
+    like mp_solve's, each with its own 'status'; a dict passed as `stats`
+    receives the call's work counters."""
     count = len(problems)
     precs = _per_item(precision, count)
     fl = _per_item(fields, count)
@@ -513,7 +520,10 @@ def mp_batch_solve(ctx, problems, precision=None, fields=False, lockstep_iters=N
     for i, rs in enumerate(rss):
         rarr[i] = rs.st
     status = (C.c_int * max(count, 1))()
-    st = LIB.mp_batch_solve(ctx.ptr, parr, count, rarr, status, _stream_handle(stream))
+    bst = mp_batch_stats()
+    st = LIB.mp_batch_solve(ctx.ptr, parr, count, rarr, status, _stream_handle(stream), C.byref(bst))
+    if stats is not None:
+        stats.update({k: getattr(bst, k) for k, _ in mp_batch_stats._fields_})
     if st == 1 and count and all(status[i] == 0 for i in range(count)):
         raise MicropolarError(st, ctx.error())
     out = []

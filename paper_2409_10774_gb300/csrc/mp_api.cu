@@ -294,7 +294,7 @@ struct mp_rve {
   double div_limit = 1e6;
   double ref[6] = {0, 0, 0, 0, 0, 0};
   DevBuf spec, prev, hist, pq, elast, phase, phases, twx, twy, twz, partials, avgpart, errout, steprows,
-      status;
+      status, tmean;
   CellDev<float> cf{};
   CellDev<double> cd{};
   LaunchCfg L;
@@ -344,6 +344,7 @@ mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
   if ((s = dalloc(ctx, r->prev, sizeof(R) * 20 * (size_t)c.nvox)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->hist, sizeof(R) * 20 * (size_t)c.nvox)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->status, sizeof(int) * 4)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->tmean, sizeof(double) * 18)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->pq, sizeof(double) * 2 * (size_t)c.nvox)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->elast, sizeof(R) * 18 * (size_t)c.nvox)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->phase, sizeof(uint16_t) * (size_t)c.nvox)) != MP_OK) return s;
@@ -356,8 +357,10 @@ mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
   c.phase = reinterpret_cast<const uint16_t*>(r->phase.ptr);
   c.phases = reinterpret_cast<const PhaseDev<R>*>(r->phases.ptr);
   c.status = reinterpret_cast<int*>(r->status.ptr);
+  c.tmean = reinterpret_cast<double*>(r->tmean.ptr);
   c.err_kind = r->err_kind;
   MP_CK(ctx, cudaMemsetAsync(r->status.ptr, 0, r->status.bytes, st));
+  MP_CK(ctx, cudaMemsetAsync(r->tmean.ptr, 0, r->tmean.bytes, st));
   c.ref = ref_dev<R>(r->ref);
   std::vector<PhaseDev<R>> ph(p->n_phases);
   for (int k = 0; k < p->n_phases; ++k) ph[k] = phase_dev<R>(p->phases[k]);
@@ -494,7 +497,7 @@ void rve_free(mp_rve* r) {
   mp_ctx* ctx = r->ctx;
   DevBuf* bufs[] = {&r->spec, &r->prev, &r->hist, &r->pq, &r->elast, &r->phase, &r->phases,
                     &r->twx, &r->twy, &r->twz, &r->partials, &r->avgpart, &r->errout, &r->steprows,
-                    &r->status};
+                    &r->status, &r->tmean};
   for (DevBuf* b : bufs) dfree(ctx, *b);
   if (r->err_host) cudaFreeHost(r->err_host);
   r->err_host = nullptr;

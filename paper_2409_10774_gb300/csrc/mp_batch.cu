@@ -154,7 +154,7 @@ struct BlockPool final : Pool {
 // ------------------------------------------------------------------ cell arena layout
 template <class R>
 struct ArenaLayout {
-  size_t spec, prev, hist, pq, elast, phase, phases, tw[3], status, ipart, apart, rows, fields, total;
+  size_t spec, prev, hist, pq, elast, phase, phases, tw[3], status, tmean, ipart, apart, rows, fields, total;
   ArenaLayout(const Request& q, long long items_a) {
     const long long kx = q.n[0] > 1 ? q.n[0] / 2 : 1;
     const size_t nspec = (size_t)kx * q.n[1] * q.n[2];
@@ -175,6 +175,7 @@ struct ArenaLayout {
     phases = put(sizeof(PhaseDev<R>) * q.phases.size());
     for (int a = 0; a < 3; ++a) tw[a] = put(sizeof(cpx<R>) * q.n[a]);
     status = put(sizeof(int) * 4);
+    tmean = put(sizeof(double) * 18);
     ipart = put(sizeof(double) * kErrPartials * (size_t)items_a);
     apart = put(sizeof(double) * kAvgPartials * chunks);
     rows = put(sizeof(double) * kAvgPartials * (size_t)q.n_steps);
@@ -423,6 +424,7 @@ class Engine {
     c.phase = reinterpret_cast<const uint16_t*>(b + A.phase);
     c.phases = reinterpret_cast<const PhaseDev<R>*>(b + A.phases);
     c.status = reinterpret_cast<int*>(b + A.status);
+    c.tmean = reinterpret_cast<double*>(b + A.tmean);
     c.ipart = reinterpret_cast<double*>(b + A.ipart);
     c.apart = reinterpret_cast<double*>(b + A.apart);
     c.rows_a = s.L.rows;
@@ -451,6 +453,7 @@ class Engine {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(b + A.phases, ph.data(), sizeof(PhaseDev<R>) * ph.size(), cudaMemcpyHostToDevice, st_);
     if (e == cudaSuccess) e = cudaMemsetAsync(b + A.status, 0, sizeof(int) * 4, st_);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b + A.tmean, 0, sizeof(double) * 18, st_);
     if (e == cudaSuccess && fresh) e = cudaMemsetAsync(s.rows, 0, sizeof(double) * kAvgPartials * q->n_steps, st_);
     // the host tables above are locals: the copies must have read them
     if (e == cudaSuccess) e = cudaStreamSynchronize(st_);
@@ -722,6 +725,8 @@ int migrate(Engine<RA>& from, Engine<RB>& to) {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dst.c.pq, src.c.pq, sizeof(double) * 2 * nv, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dst.c.tmean, src.c.tmean, sizeof(double) * 18, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
       e = cudaMemcpyAsync(dst.rows, src.rows, sizeof(double) * kAvgPartials * q.n_steps, cudaMemcpyDeviceToDevice,
                           st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -833,7 +838,8 @@ void server_loop(mp_server* S) {
 extern "C" {
 
 mp_status mp_batch_solve(mp_ctx* ctx, const mp_problem* const* problems, int32_t count, mp_result* results,
-                         mp_status* per_item, void* stream) {
+                         mp_status* per_item, void* stream, mp_batch_stats* stats) {
+  if (stats) std::memset(stats, 0, sizeof(*stats));
   if (!ctx) return set_error(nullptr, MP_E_INVALID_ARG, "ctx is NULL");
   if (count < 0 || (count > 0 && !problems)) return set_error(ctx, MP_E_INVALID_ARG, "invalid problem list");
   if (count == 0) return MP_OK;
@@ -853,6 +859,7 @@ mp_status mp_batch_solve(mp_ctx* ctx, const mp_problem* const* problems, int32_t
     Engine<float> ef(ctx, &pool, cs);
     Engine<double> ed(ctx, &pool, cs);
     bool broken = false;
+    int64_t escalations = 0;
     while (!broken && (!pending.empty() || !ef.idle() || !ed.idle())) {
       while (!pending.empty()) {
         Request* q = pending.front();
@@ -868,9 +875,16 @@ mp_status mp_batch_solve(mp_ctx* ctx, const mp_problem* const* problems, int32_t
       std::vector<Request*> fin;
       if (ef.round(fin) == MP_E_CUDA || ed.round(fin) == MP_E_CUDA) broken = true;
       if (!broken) {
-        migrate(ef, ed);
+        escalations += migrate(ef, ed);
         migrate(ed, ef);
       }
+    }
+    if (stats) {
+      stats->rounds = ef.rounds();
+      stats->rounds_fp64 = ed.rounds();
+      stats->voxel_iters = ef.voxel_iters() + ed.voxel_iters();
+      stats->voxel_iters_fp64 = ed.voxel_iters();
+      stats->escalations = escalations;
     }
     for (Request* q : pending) {
       q->status = MP_E_CUDA;

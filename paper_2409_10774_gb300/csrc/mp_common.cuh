@@ -100,6 +100,7 @@ struct CellDev {
   double* avg_out;        // row of this increment's homogenized averages
   double* err_out;        // [8] error of the last iteration (err, per field, status)
   int err_kind;           // eq. err metric: 0 = local (max), 1 = average
+  double* tmean;          // [18] <t>, <m> of the last iteration (constants subtracted before transforms)
   int predict;            // commit: write the next increment's predictor
   double ratio;           // commit: (t_{n+1} - t_n) / (t_n - t_{n-1})
 };

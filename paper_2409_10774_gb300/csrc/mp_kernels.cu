@@ -52,7 +52,7 @@ constexpr int kThreadsYZ = 288;
 // dynamic tiles may use: the multi-cell kernels also hold a cell descriptor
 // and a few reduction words in static shared memory.
 constexpr size_t kSmemOptin = 227 * 1024;
-constexpr size_t kSmemStaticReserve = 1024;
+constexpr size_t kSmemStaticReserve = 2048;
 constexpr size_t kSmemBudget = kSmemOptin - kSmemStaticReserve;
 
 // Cooperative copy of one tile column: `n` chunks of 18 complex values, chunk
@@ -293,7 +293,7 @@ __device__ __forceinline__ void flag_timeout(int* status) {
 // bounded wait expired (uniform across the block).
 template <class R, int MODE>
 __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item, unsigned char* smem_raw,
-                                            uint32_t& parity, double* itm, const R* fin_tau,
+                                            uint32_t& parity, double* itm, R* tms, const R* fin_tau,
                                             const R* fin_mu, R* fout_e, R* fout_g) {
   const int rows = c.rows_a;
   const int N1 = c.n1;
@@ -319,6 +319,7 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
   const int nvi = nr * N1;
   const long long v0 = row0 * N1;
   // ---------------------------------------------------------- issue loads
+  if (use_vox && threadIdx.x < 18) tms[threadIdx.x] = (R)c.tmean[threadIdx.x];
   if (threadIdx.x == 0) {
     bulk_wait_read();     // the previous item's stores have read shared memory
     fence_proxy_async();  // and every thread's reads of it precede the new loads
@@ -410,6 +411,34 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
           gm[q] = pv[9 + q];
         }
       }
+      // A0 (e - E), B0 (gamma - Gamma) go to this voxel's output slots now (the
+      // fluctuations val, or the predictor less the load, are at hand here);
+      // the polarization below completes them
+      {
+        R de[9], dg[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          de[q] = (MODE == kIter) ? val[q] : e[q] - c.E[q];
+          dg[q] = (MODE == kIter) ? val[9 + q] : gm[q] - c.G[q];
+        }
+        const R tre = de[0] + de[4] + de[8], trg = dg[0] + dg[4] + dg[8];
+        const R a = c.ref.mu + c.ref.kap, b = c.ref.mu - c.ref.kap;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+          for (int l = 0; l < 3; ++l) {
+            const int i = 3 * k + l, j = 3 * l + k;
+            R ae = a * de[i] + b * de[j];
+            R bg = c.ref.beta * dg[i] + c.ref.gamma * dg[j];
+            if (k == l) {
+              ae += c.ref.lam * tre;
+              bg += c.ref.alpha * trg;
+            }
+            zr[2 * i] = ae;
+            zr[2 * (9 + i)] = bg;
+          }
+        }
+      }
       const PhaseDev<R>& P = c.phases[(int)hv[18]];
       const double2 pq = pq_s[lv];
       R t[9], m[9];
@@ -448,25 +477,15 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
       }
       pv[18] = ft;
       pv[19] = fm;
-      // polarizations (eq. micropolar_polarizatons): tau = t - A0 e, mu = m - B0 gamma
-      {
-        const R tre = e[0] + e[4] + e[8], trg = gm[0] + gm[4] + gm[8];
-        const R a = c.ref.mu + c.ref.kap, b = c.ref.mu - c.ref.kap;
+      // polarizations (eq. micropolar_polarizatons): tau = t - A0 e, mu = m - B0 gamma,
+      // transformed less the constants tau_c = <t>_prev - A0 E, mu_c = <m>_prev - B0 Gamma
+      // (a constant only changes the k = 0 term, which the Green operator drops):
+      // tau - tau_c = (t - <t>_prev) - A0 (e - E) is made of fluctuations, so the
+      // transforms' rounding, relative to the size of their input, is smaller
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-#pragma unroll
-          for (int l = 0; l < 3; ++l) {
-            const int i = 3 * k + l, j = 3 * l + k;
-            R ae = a * e[i] + b * e[j];
-            R bg = c.ref.beta * gm[i] + c.ref.gamma * gm[j];
-            if (k == l) {
-              ae += c.ref.lam * tre;
-              bg += c.ref.alpha * trg;
-            }
-            zr[2 * i] = t[i] - ae;
-            zr[2 * (9 + i)] = m[i] - bg;
-          }
-        }
+      for (int q = 0; q < 9; ++q) {
+        zr[2 * q] = (t[q] - tms[q]) - zr[2 * q];
+        zr[2 * (9 + q)] = (m[q] - tms[9 + q]) - zr[2 * (9 + q)];
       }
     }
     if (MODE == kXInv) {
@@ -546,6 +565,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ CellDev<R> cs;
   __shared__ double itm[kErrPartials];
+  __shared__ R tms[18];  // <t>, <m> of the cell's previous iteration (subtracted constants)
   double* acc = reinterpret_cast<double*>(smem_raw + PassASmem<R>::acc_off);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + PassASmem<R>::bar_off);
   if (threadIdx.x == 0) {
@@ -563,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
       flag_timeout(c.status);  // every cell with a skipped item reports the failure
       return;
     }
-    if (!pass_a_item<R, MODE>(c, item, smem_raw, parity, itm, fin_tau, fin_mu, fout_e, fout_g)) {
+    if (!pass_a_item<R, MODE>(c, item, smem_raw, parity, itm, tms, fin_tau, fin_mu, fout_e, fout_g)) {
       failed = true;
       status = c.status;
       return;
@@ -610,17 +630,28 @@ __device__ void finish_err(const CellDev<R>& c, const double* s, int err_kind, d
       me[q] = s[8 + q] * iv;
       mg[q] = s[17 + q] * iv;
     }
-    // <t> = <tau> + A0 <e>, <m> = <mu> + B0 <gamma>  (linearity of the polarization)
+    // The transformed polarization was tau - tau_c = (t - T_c) - A0 (e - E) (T_c =
+    // c.tmean as read by pass A), so <t> = <tau - tau_c> + T_c + A0 (<e> - E) and
+    // likewise <m>; <t>, <m> then become the constants of the next iteration.
     const double lam = c.ref.lam, mu = c.ref.mu, kap = c.ref.kap;
     const double al = c.ref.alpha, be = c.ref.beta, ga = c.ref.gamma;
-    const double tre = me[0] + me[4] + me[8], trg = mg[0] + mg[4] + mg[8];
+    double xe[9], xg[9];
+    for (int q = 0; q < 9; ++q) {
+      xe[q] = me[q] - (double)c.E[q];
+      xg[q] = mg[q] - (double)c.G[q];
+    }
+    const double tre = xe[0] + xe[4] + xe[8], trg = xg[0] + xg[4] + xg[8];
     for (int k = 0; k < 3; ++k)
       for (int l = 0; l < 3; ++l) {
-        mt[3 * k + l] = s[26 + 3 * k + l] * iv + (mu + kap) * me[3 * k + l] + (mu - kap) * me[3 * l + k] +
-                        (k == l ? lam * tre : 0.0);
-        mm[3 * k + l] = s[35 + 3 * k + l] * iv + be * mg[3 * k + l] + ga * mg[3 * l + k] +
-                        (k == l ? al * trg : 0.0);
+        const int i = 3 * k + l, j = 3 * l + k;
+        mt[i] = s[26 + i] * iv + (double)(R)c.tmean[i] + (mu + kap) * xe[i] + (mu - kap) * xe[j] +
+                (k == l ? lam * tre : 0.0);
+        mm[i] = s[35 + i] * iv + (double)(R)c.tmean[9 + i] + be * xg[i] + ga * xg[j] + (k == l ? al * trg : 0.0);
       }
+    for (int q = 0; q < 9; ++q) {
+      c.tmean[q] = mt[q];
+      c.tmean[9 + q] = mm[q];
+    }
     double ne = 0, ng = 0, nt = 0, nm = 0;
     for (int q = 0; q < 9; ++q) {
       ne += me[q] * me[q]; ng += mg[q] * mg[q]; nt += mt[q] * mt[q]; nm += mm[q] * mm[q];

@@ -167,6 +167,21 @@ int32_t mp_rve_steps_done(const mp_rve* rve);
 int64_t mp_rve_iterations(const mp_rve* rve);
 void mp_rve_destroy(mp_rve* rve);
 
+/* Checkpoint / resume of a device-resident cell between load increments.
+ * The committed state of Algorithm 2 is the checkpoint: history h_t, h_m,
+ * plastic strains p, q, the next increment's predictor and the converged
+ * iterate it extrapolates from, the transform constants, the per-increment
+ * result rows, errors and iteration counts, and the increment count.
+ * mp_checkpoint with host_buf == NULL stores the required size in *bytes;
+ * otherwise it writes the image (at most *bytes) and stores its size.
+ * mp_resume loads an image into a cell created from the same problem (grid,
+ * precision, phases, load path, tolerance and reference medium are checked
+ * through a digest; MP_E_INVALID_ARG otherwise); mp_rve_run then continues
+ * exactly as the checkpointed cell would have (bit-identical results).
+ * The image is host-endian and tied to this library version. */
+mp_status mp_checkpoint(mp_rve* rve, void* host_buf, size_t* bytes, void* stream);
+mp_status mp_resume(mp_rve* rve, const void* host_buf, size_t bytes, void* stream);
+
 /* Kernel classes of the per-increment work, for launch counts and timings. */
 #define MP_KC_FFT_Y_FWD 0 /* y-direction forward transform pass                        */
 #define MP_KC_GREEN_Z 1   /* z forward + Green operator + z inverse pass                */

@@ -30,7 +30,8 @@ EXPORTED = ("mp_abi_version", "mp_create", "mp_destroy", "mp_last_error", "mp_va
             "mp_solve", "mp_rve_create", "mp_rve_run", "mp_rve_results", "mp_rve_reset",
             "mp_rve_steps_done", "mp_rve_iterations", "mp_rve_destroy", "mp_rve_profile",
             "mp_rve_profile_read", "mp_radial_return", "mp_green_apply", "mp_green_apply_static",
-            "mp_rve_trace", "mp_rve_trace_read", "mp_batch_solve", "mp_server_create", "mp_server_submit", "mp_server_wait",
+            "mp_rve_trace", "mp_rve_trace_read", "mp_checkpoint", "mp_resume", "mp_batch_solve",
+            "mp_server_create", "mp_server_submit", "mp_server_wait",
             "mp_server_query", "mp_server_destroy")
 MP_STATIC_SCRATCH_BYTES = 8 * 1024 * 1024
 KERNEL_CLASSES = ("fft_y_fwd", "green_z", "fft_y_inv", "pass_a", "reduce", "start", "commit")
@@ -122,6 +123,8 @@ def _load():
         "mp_green_apply_static": (C.c_int, [V, C.c_int32, P(C.c_int32), C.c_double, P(C.c_double), V, V, V, V,
                                             V]),
         "mp_rve_trace": (C.c_int, [V, C.c_int32]),
+        "mp_checkpoint": (C.c_int, [V, V, P(C.c_size_t), V]),
+        "mp_resume": (C.c_int, [V, V, C.c_size_t, V]),
         "mp_rve_trace_read": (C.c_int64, [V, P(C.c_double), C.c_int64, C.c_int32]),
         "mp_batch_solve": (C.c_int, [V, P(P(mp_problem)), C.c_int32, P(mp_result), P(C.c_int), V,
                                      P(mp_batch_stats)]),
@@ -379,6 +382,25 @@ class Rve:
         ln = (C.c_int64 * k)()
         LIB.mp_rve_profile_read(self.ptr, ms, ln, 1 if reset else 0)
         return {name: (ms[i], ln[i]) for i, name in enumerate(KERNEL_CLASSES)}
+
+    def checkpoint(self, stream=None):
+        """The cell's committed state as bytes (mp_checkpoint)."""
+        n = C.c_size_t(0)
+        st = LIB.mp_checkpoint(self.ptr, None, C.byref(n), _stream_handle(stream))
+        if st != MP_OK:
+            raise MicropolarError(st, self.ctx.error())
+        buf = C.create_string_buffer(n.value)
+        st = LIB.mp_checkpoint(self.ptr, buf, C.byref(n), _stream_handle(stream))
+        if st != MP_OK:
+            raise MicropolarError(st, self.ctx.error())
+        return buf.raw[: n.value]
+
+    def resume(self, image, stream=None):
+        """Load a checkpoint image taken from a cell of the same problem (mp_resume)."""
+        buf = C.create_string_buffer(bytes(image), len(image))
+        st = LIB.mp_resume(self.ptr, buf, len(image), _stream_handle(stream))
+        if st != MP_OK:
+            raise MicropolarError(st, self.ctx.error())
 
     def trace(self, enable=True):
         """Record (increment, iteration, err, err_e, err_t, err_gamma, err_m) per iteration."""

@@ -305,6 +305,7 @@ struct mp_rve {
   std::vector<double> err_steps;
   std::vector<int> iters_steps;
   double* err_host = nullptr;  // pinned, 8 doubles
+  uint64_t digest = 0;         // of the problem the cell was created from (checkpoint check)
   // per-kernel-class launch counters and (when profiling) CUDA-event timings
   long long launches[MP_KC_COUNT] = {0};
   double kernel_ms[MP_KC_COUNT] = {0};
@@ -493,6 +494,46 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
   return MP_OK;
 }
 
+// FNV-1a (64-bit) over the bytes that define a cell's problem: a checkpoint
+// records it and a resume refuses another problem.
+struct Fnv {
+  uint64_t h = 1469598103934665603ull;
+  void add(const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  }
+};
+
+uint64_t problem_digest(const mp_problem* p, const double ref[6]) {
+  Fnv f;
+  f.add(p->n, sizeof(p->n));
+  f.add(&p->h, sizeof(p->h));
+  f.add(&p->precision, sizeof(p->precision));
+  const long long nvox = (long long)p->n[0] * p->n[1] * p->n[2];
+  f.add(p->phase, sizeof(uint16_t) * (size_t)nvox);
+  f.add(p->phases, sizeof(mp_phase) * (size_t)p->n_phases);
+  f.add(&p->n_steps, sizeof(p->n_steps));
+  f.add(p->time, sizeof(double) * (size_t)(p->n_steps + 1));
+  f.add(p->E, sizeof(double) * 9 * (size_t)(p->n_steps + 1));
+  f.add(p->G, sizeof(double) * 9 * (size_t)(p->n_steps + 1));
+  f.add(&p->tol, sizeof(p->tol));
+  f.add(&p->err_kind, sizeof(p->err_kind));
+  f.add(ref, sizeof(double) * 6);
+  return f.h;
+}
+
+// Checkpoint image: header, then the device arrays in this order.
+struct CkptHeader {
+  char magic[8];  // "MPCKPT1\0"
+  int32_t precision, n[3], n_steps, steps_done, predicted, failed_step;
+  int64_t total_iters;
+  uint64_t digest;
+  uint64_t bytes_prev, bytes_hist, bytes_pq, bytes_elast, bytes_tmean, bytes_rows;
+};
+
 void rve_free(mp_rve* r) {
   mp_ctx* ctx = r->ctx;
   DevBuf* bufs[] = {&r->spec, &r->prev, &r->hist, &r->pq, &r->elast, &r->phase, &r->phases,
@@ -587,6 +628,7 @@ mp_status mp_rve_create(mp_ctx* ctx, const mp_problem* p, mp_rve** out, void* st
     return set_error(ctx, MP_E_CUDA, "cudaMallocHost: %s", cudaGetErrorString(e));
   }
   for (int i = 0; i < 8; ++i) r->err_host[i] = 0.0;
+  r->digest = problem_digest(p, ref);
   st = (r->precision == 0) ? rve_setup<double>(r, p, cs) : rve_setup<float>(r, p, cs);
   if (st != MP_OK) {
     rve_free(r);
@@ -599,13 +641,121 @@ mp_status mp_rve_create(mp_ctx* ctx, const mp_problem* p, mp_rve** out, void* st
 
 mp_status mp_rve_reset(mp_rve* r, void* stream) {
   if (!r) return set_error(nullptr, MP_E_INVALID_ARG, "rve is NULL");
-  (void)stream;
+  mp_status st = use_device(r->ctx);
+  if (st != MP_OK) return st;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  // the transform constants start from zero as in a fresh cell
+  MP_CK(r->ctx, cudaMemsetAsync(r->tmean.ptr, 0, r->tmean.bytes, cs));
+  MP_CK(r->ctx, cudaMemsetAsync(r->status.ptr, 0, r->status.bytes, cs));
   r->steps_done = 0;
   r->predicted = false;
   r->total_iters = 0;
   r->failed_step = 0;
   r->err_steps.clear();
   r->iters_steps.clear();
+  return MP_OK;
+}
+
+mp_status mp_checkpoint(mp_rve* r, void* host_buf, size_t* bytes, void* stream) {
+  if (!r || !bytes) return set_error(r ? r->ctx : nullptr, MP_E_INVALID_ARG, "NULL argument");
+  CkptHeader h{};
+  std::memcpy(h.magic, "MPCKPT1", 8);
+  h.precision = r->precision;
+  for (int j = 0; j < 3; ++j) h.n[j] = r->n[j];
+  h.n_steps = r->n_steps;
+  h.steps_done = r->steps_done;
+  h.predicted = r->predicted ? 1 : 0;
+  h.failed_step = r->failed_step;
+  h.total_iters = r->total_iters;
+  h.digest = r->digest;
+  h.bytes_prev = r->prev.bytes;
+  h.bytes_hist = r->hist.bytes;
+  h.bytes_pq = r->pq.bytes;
+  h.bytes_elast = r->elast.bytes;
+  h.bytes_tmean = r->tmean.bytes;
+  h.bytes_rows = r->steprows.bytes;
+  const size_t host_bytes = sizeof(double) * r->err_steps.size() + sizeof(int32_t) * r->iters_steps.size();
+  const size_t need = sizeof(h) + h.bytes_prev + h.bytes_hist + h.bytes_pq + h.bytes_elast + h.bytes_tmean +
+                      h.bytes_rows + host_bytes;
+  if (!host_buf) {
+    *bytes = need;
+    return MP_OK;
+  }
+  if (*bytes < need) {
+    *bytes = need;
+    return set_error(r->ctx, MP_E_INVALID_ARG, "checkpoint buffer too small (%zu bytes needed)", need);
+  }
+  mp_status st = use_device(r->ctx);
+  if (st != MP_OK) return st;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  unsigned char* out = static_cast<unsigned char*>(host_buf);
+  std::memcpy(out, &h, sizeof(h));
+  size_t o = sizeof(h);
+  const DevBuf* arrs[6] = {&r->prev, &r->hist, &r->pq, &r->elast, &r->tmean, &r->steprows};
+  for (const DevBuf* b : arrs) {
+    MP_CK(r->ctx, cudaMemcpyAsync(out + o, b->ptr, b->bytes, cudaMemcpyDeviceToHost, cs));
+    o += b->bytes;
+  }
+  MP_CK(r->ctx, cudaStreamSynchronize(cs));
+  for (size_t k = 0; k < r->err_steps.size(); ++k) {
+    std::memcpy(out + o, &r->err_steps[k], sizeof(double));
+    o += sizeof(double);
+  }
+  for (size_t k = 0; k < r->iters_steps.size(); ++k) {
+    const int32_t it = r->iters_steps[k];
+    std::memcpy(out + o, &it, sizeof(int32_t));
+    o += sizeof(int32_t);
+  }
+  *bytes = o;
+  return MP_OK;
+}
+
+mp_status mp_resume(mp_rve* r, const void* host_buf, size_t bytes, void* stream) {
+  if (!r || !host_buf) return set_error(r ? r->ctx : nullptr, MP_E_INVALID_ARG, "NULL argument");
+  CkptHeader h;
+  if (bytes < sizeof(h)) return set_error(r->ctx, MP_E_INVALID_ARG, "checkpoint truncated");
+  std::memcpy(&h, host_buf, sizeof(h));
+  if (std::memcmp(h.magic, "MPCKPT1", 8) != 0)
+    return set_error(r->ctx, MP_E_INVALID_ARG, "not a checkpoint of this library");
+  if (h.digest != r->digest || h.precision != r->precision || h.n_steps != r->n_steps ||
+      h.n[0] != r->n[0] || h.n[1] != r->n[1] || h.n[2] != r->n[2])
+    return set_error(r->ctx, MP_E_INVALID_ARG, "checkpoint belongs to another problem or precision");
+  if (h.bytes_prev != r->prev.bytes || h.bytes_hist != r->hist.bytes || h.bytes_pq != r->pq.bytes ||
+      h.bytes_elast != r->elast.bytes || h.bytes_tmean != r->tmean.bytes || h.bytes_rows != r->steprows.bytes ||
+      h.steps_done < 0 || h.steps_done > r->n_steps)
+    return set_error(r->ctx, MP_E_INVALID_ARG, "checkpoint layout does not match the cell");
+  const size_t nst = (size_t)h.steps_done;
+  const size_t need = sizeof(h) + h.bytes_prev + h.bytes_hist + h.bytes_pq + h.bytes_elast + h.bytes_tmean +
+                      h.bytes_rows + nst * (sizeof(double) + sizeof(int32_t));
+  if (bytes < need) return set_error(r->ctx, MP_E_INVALID_ARG, "checkpoint truncated");
+  mp_status st = use_device(r->ctx);
+  if (st != MP_OK) return st;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  const unsigned char* in = static_cast<const unsigned char*>(host_buf);
+  size_t o = sizeof(h);
+  DevBuf* arrs[6] = {&r->prev, &r->hist, &r->pq, &r->elast, &r->tmean, &r->steprows};
+  for (DevBuf* b : arrs) {
+    MP_CK(r->ctx, cudaMemcpyAsync(b->ptr, in + o, b->bytes, cudaMemcpyHostToDevice, cs));
+    o += b->bytes;
+  }
+  MP_CK(r->ctx, cudaMemsetAsync(r->status.ptr, 0, r->status.bytes, cs));
+  MP_CK(r->ctx, cudaStreamSynchronize(cs));
+  r->err_steps.assign(nst, 0.0);
+  r->iters_steps.assign(nst, 0);
+  for (size_t k = 0; k < nst; ++k) {
+    std::memcpy(&r->err_steps[k], in + o, sizeof(double));
+    o += sizeof(double);
+  }
+  for (size_t k = 0; k < nst; ++k) {
+    int32_t it;
+    std::memcpy(&it, in + o, sizeof(int32_t));
+    r->iters_steps[k] = it;
+    o += sizeof(int32_t);
+  }
+  r->steps_done = h.steps_done;
+  r->predicted = h.predicted != 0;
+  r->failed_step = h.failed_step;
+  r->total_iters = h.total_iters;
   return MP_OK;
 }
 

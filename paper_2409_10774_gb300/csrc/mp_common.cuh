@@ -44,6 +44,7 @@ struct PhaseDev {
   R lam, mu, kap, alpha, beta, gamma;   // eq. stiffnesses_iso
   R a1, a2, b1, b2;                     // eq. equiv_stress / equiv_couple_stress (b2 = 0 if gamma == beta)
   double tY, tH, mY, mH;                // eq. radius_1 / radius_2 (elastic: +inf yield)
+  float tYf, tHf, mYf, mHf;             // the same rounded to single precision (elastic-branch screen)
   double ct, cm;                        // 2 a1 mu and b1 (gamma + beta) (eq. trial_stresses2)
   double inv_t, inv_m;                  // 1 / (tH + ct), 1 / (mH + cm)
   double ct_inv, tH_inv;                // ct / (tH + ct), tH / (tH + ct)

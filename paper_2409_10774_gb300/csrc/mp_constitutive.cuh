@@ -23,15 +23,36 @@ namespace mp {
 // (relative error ~1e-7).  One step leaves ~1e-14, below single precision
 // (enough when the result scales FP32 fields); two steps reach FP64 rounding.
 // Arguments outside the single-precision normal range take the FP64 library path.
+// xf is x rounded to single precision (callers often have it at hand).
 template <int STEPS>
-__device__ __forceinline__ double rsqrt_newton(double x) {
-  const float xf = (float)x;
+__device__ __forceinline__ double rsqrt_newton(double x, float xf) {
   if (!(xf > 1e-36f && xf < 1e36f)) return 1.0 / sqrt(x);
   double y = (double)rsqrtf(xf);
   const double hx = 0.5 * x;
 #pragma unroll
   for (int i = 0; i < STEPS; ++i) y = y * fma(-hx * y, y, 1.5);
   return y;
+}
+
+// A single-precision lower bound of x >= 0 from the top word of its FP64 bit
+// pattern (mantissa truncated to 20 bits; 0 below the float normal range,
+// FLT_MAX above it), with integer operations only.
+__device__ __forceinline__ float float_below(double x) {
+  const int hi = __double2hiint(x);
+  const int ex = (hi >> 20) & 0x7ff;
+  if (hi <= 0 || ex < 1023 - 126) return 0.0f;
+  if (ex > 1023 + 127) return 3.402823466e38f;
+  return __int_as_float(((ex - 1023 + 127) << 23) | ((hi & 0xfffff) << 3));
+}
+
+// True when the single-precision trial value q2 = (t_eq^trial)^2 is certainly
+// below (Y + H p)^2 - i.e. the FP64 test of the elastic branch is certain to
+// pass - so that the FP64 test can be skipped.  Yf, Hf are Y, H rounded to
+// single precision and p is bounded from below, so the single-precision
+// radius is within a few ulps of the FP64 one; the 1e-5 margin covers that.
+__device__ __forceinline__ bool surely_inside(float q2, float Yf, float Hf, double p) {
+  const float r = fmaf(Hf, float_below(p), Yf);
+  return q2 < r * r * 0.99999f;
 }
 
 // t_kl = lam tr(e) d_kl + (mu + kappa) e_kl + (mu - kappa) e_lk  (eq. elast_constitutive_iso)
@@ -139,15 +160,17 @@ __device__ __forceinline__ void radial_return(const PhaseDev<R>& P, const R* e, 
     for (int i = 0; i < 9; ++i) s[i] = t[i];
     s[0] -= vol; s[4] -= vol; s[8] -= vol;
     const R teq2r = eq_sq(s, P.a1, P.a2, true);
+    // FP32 fields: a trial value far inside the yield surface needs no FP64 test
+    const bool in_t = sizeof(R) == 4 && surely_inside((float)teq2r, P.tYf, P.tHf, pn);
     const double R1n = fma(P.tH, pn, P.tY);
-    {
+    if (!in_t) {
       const double teq2 = (double)teq2r;
       if (!(teq2 < R1n * R1n)) {          // plastic: t_eq^trial >= t_Y + t_H p_n
         // eq. trial_stresses2: p - p_n = (t_eq^trial - R1(p_n)) / (t_H + 2 a1 mu).
         // Since R1(p) + 2 a1 mu (p - p_n) = t_eq^trial, the return factor
         // R1 / (R1 + 2 a1 mu (p - p_n)) = R1(p) / t_eq^trial
         //   = [2 a1 mu R1(p_n) + t_H t_eq^trial] / [(t_H + 2 a1 mu) t_eq^trial].
-        const double rinv = rsqrt_newton<kNewton>(teq2);
+        const double rinv = rsqrt_newton<kNewton>(teq2, (float)teq2r);
         const double teq = teq2 * rinv;
         p = pn + (teq - R1n) * P.inv_t;
         ft = (R)fma(P.ct_inv * R1n, rinv, P.tH_inv);
@@ -155,11 +178,12 @@ __device__ __forceinline__ void radial_return(const PhaseDev<R>& P, const R* e, 
     }
     // micro level (eq. equiv_couple_stress on the trial couple stress)
     const R meq2r = eq_sq(m, P.b1, P.b2, P.skew_m != 0);
+    const bool in_m = sizeof(R) == 4 && surely_inside((float)meq2r, P.mYf, P.mHf, qn);
     const double R2n = fma(P.mH, qn, P.mY);
-    {
+    if (!in_m) {
       const double meq2 = (double)meq2r;
       if (!(meq2 < R2n * R2n)) {
-        const double rinv = rsqrt_newton<kNewton>(meq2);
+        const double rinv = rsqrt_newton<kNewton>(meq2, (float)meq2r);
         const double meq = meq2 * rinv;
         q = qn + (meq - R2n) * P.inv_m;
         fm = (R)fma(P.cm_inv * R2n, rinv, P.mH_inv);

@@ -75,6 +75,10 @@ PhaseDev<R> phase_dev(const mp_phase& ph) {
   d.tH = ph.tH;
   d.mY = ph.elastic ? INFINITY : ph.mY;
   d.mH = ph.mH;
+  d.tYf = (float)d.tY;
+  d.tHf = (float)d.tH;
+  d.mYf = (float)d.mY;
+  d.mHf = (float)d.mH;
   d.ct = 2.0 * ph.a1 * ph.mu;
   d.cm = ph.b1 * (ph.gamma + ph.beta);
   d.inv_t = 1.0 / (ph.tH + d.ct);

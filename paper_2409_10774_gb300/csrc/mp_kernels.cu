@@ -57,6 +57,8 @@ constexpr size_t kSmemBudget = kSmemOptin - kSmemStaticReserve;
 
 // Cooperative copy of one tile column: `n` chunks of 18 complex values, chunk
 // i at g + i * stride (complex units), into / out of a contiguous AoS tile.
+// Loads are asynchronous 16-byte copies (cp.async), so every thread keeps all
+// of its loads in flight; the caller's barrier follows cp_async_wait_all.
 template <class R, bool TO_SMEM>
 __device__ __forceinline__ void copy_column(cpx<R>* tile, cpx<R>* g, int n, long long stride) {
   constexpr int W = 18 * (int)sizeof(cpx<R>) / 16;  // float4 per chunk
@@ -64,9 +66,10 @@ __device__ __forceinline__ void copy_column(cpx<R>* tile, cpx<R>* g, int n, long
   for (int i = threadIdx.x; i < n * W; i += blockDim.x) {
     const int row = i / W, w = i - row * W;
     float4* g4 = reinterpret_cast<float4*>(g + row * stride) + w;
-    if (TO_SMEM) t4[row * W + w] = *g4;
-    else *g4 = t4[row * W + w];
+    if (TO_SMEM) cp_async16(t4 + i, g4);
+    else *g4 = t4[i];
   }
+  if (TO_SMEM) cp_async_wait_all();
 }
 
 // ------------------------------------------------------------------ multi-cell plumbing

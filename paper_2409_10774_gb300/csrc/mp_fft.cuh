@@ -176,14 +176,17 @@ __device__ void stage_aos(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ ou
 }
 
 // Transform every line of an AoS tile; data starts in b0, the result pointer
-// (b0 or b1) is returned.  Ends with a barrier.
+// (b0 or b1) is returned.  Ends with a barrier.  `tw`, when given, is a copy
+// of the plan's twiddle table (e.g. in shared memory).
 template <class R, int DIR, int MAXR>
-__device__ cpx<R>* tile_fft(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R>& p) {
+__device__ cpx<R>* tile_fft(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R>& p,
+                            const cpx<R>* tw = nullptr) {
   cpx<R>* in = b0;
   cpx<R>* out = b1;
   int Ns = 1;
+  const cpx<R>* table = tw ? tw : p.tw;
   for (int s = 0; s < p.nstages; ++s) {
-    stage_aos<R, DIR, MAXR>(in, out, rows, p.m, p.radix[s], Ns, p.tw, p.tstride);
+    stage_aos<R, DIR, MAXR>(in, out, rows, p.m, p.radix[s], Ns, table, p.tstride);
     Ns *= p.radix[s];
     __syncthreads();
     cpx<R>* t = in;

@@ -25,6 +25,9 @@
 namespace mp {
 
 // In-place: v[0..8] = tau^ -> e^, v[9..17] = mu^ -> gamma^, times `scale`.
+// v may point to shared memory: every input is read before the first output
+// is written, and only the 12 reals of f, g and of u, phi are kept in
+// registers, never the 36 of the point itself.
 template <class R>
 __device__ __forceinline__ void green_point(const RefDev<R>& A0, R x1, R x2, R x3, cpx<R>* v,
                                             R scale) {
@@ -82,24 +85,29 @@ __device__ __forceinline__ void green_point(const RefDev<R>& A0, R x1, R x2, R x
     u[l] = cadd(cscale(xf, xi[l] * iL_u), cscale(tu, iD));
     ph[l] = cadd(cscale(xg, xi[l] * iL_p), cscale(tp, iD));
   }
-  // e^_kl = i xi_k u_l + eps_lkm phi_m ; gamma^_kl = i phi_k xi_l
+  // e^_kl = i xi_k u_l + eps_lkm phi_m ; gamma^_kl = i phi_k xi_l, scaled, each
+  // component written once.
+  // eps_lkm phi_m: (1,2) -phi3, (2,1) +phi3, (1,3) +phi2, (3,1) -phi2, (2,3) -phi1, (3,2) +phi1
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    u[i] = cscale(u[i], scale);
+    ph[i] = cscale(ph[i], scale);
+  }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-      v[3 * k + l] = cmuli(cscale(u[l], xi[k]));
+      cpx<R> ev = cmuli(cscale(u[l], xi[k]));
+      if (k == 0 && l == 1) ev = csub(ev, ph[2]);
+      if (k == 1 && l == 0) ev = cadd(ev, ph[2]);
+      if (k == 0 && l == 2) ev = cadd(ev, ph[1]);
+      if (k == 2 && l == 0) ev = csub(ev, ph[1]);
+      if (k == 1 && l == 2) ev = csub(ev, ph[0]);
+      if (k == 2 && l == 1) ev = cadd(ev, ph[0]);
+      v[3 * k + l] = ev;
       v[9 + 3 * k + l] = cmuli(cscale(ph[k], xi[l]));
     }
   }
-  // eps_lkm phi_m: (1,2) -phi3, (2,1) +phi3, (1,3) +phi2, (3,1) -phi2, (2,3) -phi1, (3,2) +phi1
-  v[1] = csub(v[1], ph[2]);
-  v[3] = cadd(v[3], ph[2]);
-  v[2] = cadd(v[2], ph[1]);
-  v[6] = csub(v[6], ph[1]);
-  v[5] = csub(v[5], ph[0]);
-  v[7] = cadd(v[7], ph[0]);
-#pragma unroll
-  for (int i = 0; i < 18; ++i) v[i] = cscale(v[i], scale);
 }
 
 }  // namespace mp

@@ -136,9 +136,11 @@ __device__ __forceinline__ void fft_y_tile(const CellDev<R>& c, long long tile, 
   const int kz = (int)(tile / c.kx);
   const int kx = (int)(tile - (long long)kz * c.kx);
   cpx<R>* g = c.spec + ((long long)kz * N * c.kx + kx) * 18;
+  cpx<R>* tws = b1 + 18 * N;  // the axis' twiddle table, read from shared memory
+  for (int k = threadIdx.x; k < N; k += blockDim.x) tws[k] = c.py.tw[k];
   copy_column<R, true>(b0, g, N, stride);
   __syncthreads();
-  cpx<R>* r = tile_fft<R, DIR, 16>(b0, b1, 1, c.py);
+  cpx<R>* r = tile_fft<R, DIR, 16>(b0, b1, 1, c.py, tws);
   copy_column<R, false>(r, g, N, stride);
   __syncthreads();
 }
@@ -172,31 +174,28 @@ __device__ __forceinline__ void green_z_tile(const CellDev<R>& c, long long tile
     }
     return;  // uniform across the block
   }
+  cpx<R>* tws = b1 + 18 * N;  // the axis' twiddle table, read from shared memory
+  for (int k = threadIdx.x; k < N; k += blockDim.x) tws[k] = c.pz.tw[k];
   copy_column<R, true>(b0, g, N, stride);
   __syncthreads();
-  cpx<R>* r = tile_fft<R, -1, 16>(b0, b1, 1, c.pz);
+  cpx<R>* r = tile_fft<R, -1, 16>(b0, b1, 1, c.pz, tws);
   const R x1 = c.n1 == 1 ? R(0) : c.two_pi_over_L[0] * (R)kx;
   const R x2 = signed_freq_scale<R>(ky, c.n2, c.two_pi_over_L[1]);
   for (int kz = threadIdx.x; kz < N; kz += blockDim.x) {
-    cpx<R> v[18];
-    cpx<R>* pt = r + kz * 18;
-#pragma unroll
-    for (int q = 0; q < 18; ++q) v[q] = pt[q];
+    cpx<R>* pt = r + kz * 18;  // the point's 18 values, updated in shared memory
     const bool nz_nyq = (N % 2 == 0) && (kz == N / 2);
     const bool zero = (kx == 0 && ky == 0 && kz == 0);
     if (nz_nyq || zero) {
 #pragma unroll
-      for (int q = 0; q < 18; ++q) v[q] = cmake<R>(R(0), R(0));
+      for (int q = 0; q < 18; ++q) pt[q] = cmake<R>(R(0), R(0));
     } else {
       const R x3 = signed_freq_scale<R>(kz, N, c.two_pi_over_L[2]);
-      green_point<R>(c.ref, x1, x2, x3, v, scale);
+      green_point<R>(c.ref, x1, x2, x3, pt, scale);
     }
-#pragma unroll
-    for (int q = 0; q < 18; ++q) pt[q] = v[q];
   }
   __syncthreads();
   cpx<R>* other = (r == b0) ? b1 : b0;
-  cpx<R>* o = tile_fft<R, +1, 16>(r, other, 1, c.pz);
+  cpx<R>* o = tile_fft<R, +1, 16>(r, other, 1, c.pz, tws);
   copy_column<R, false>(o, g, N, stride);
   __syncthreads();
 }
@@ -266,7 +265,7 @@ struct PassASmem {
   static constexpr size_t red_off = 64;                                // [16 warps][8] doubles
   static constexpr size_t acc_off = red_off + 16 * 8 * sizeof(double);  // [kErrPartials]
   static constexpr size_t head = ((acc_off + kErrPartials * sizeof(double)) + 127) / 128 * 128;
-  size_t fft_bytes, b0_off, b1_off, prev_off, hist_off, pq_off, dc_off, total;
+  size_t fft_bytes, b0_off, b1_off, prev_off, hist_off, pq_off, dc_off, tw_off, total;
   __host__ __device__ PassASmem(int n1, int rows) {
     const int M = (n1 > 1) ? n1 / 2 : 1;
     const size_t nvi = (size_t)rows * n1;
@@ -277,9 +276,45 @@ struct PassASmem {
     hist_off = prev_off + nvi * 20 * sizeof(R);
     pq_off = hist_off + nvi * 20 * sizeof(R);
     dc_off = pq_off + nvi * 2 * sizeof(double);
-    total = dc_off + ((18 * (size_t)rows * sizeof(R) + 15) / 16) * 16;
+    tw_off = dc_off + ((18 * (size_t)rows * sizeof(R) + 15) / 16) * 16;  // x twiddles W_N1^k, k < N1
+    total = tw_off + ((n1 * sizeof(cpx<R>) + 15) / 16) * 16;
   }
 };
+
+// A voxel's 20-value record (previous iterate or history) between shared
+// memory and registers in 16-byte pieces: records are 80 (FP32) / 160 (FP64)
+// bytes apart, so per-value accesses by consecutive threads would hit the
+// same banks four (two) ways; 16-byte accesses of 8 threads cover all 32 banks.
+__device__ __forceinline__ void load_rec(const float* p, float* r) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const float4 a = q[k];
+    r[4 * k] = a.x;
+    r[4 * k + 1] = a.y;
+    r[4 * k + 2] = a.z;
+    r[4 * k + 3] = a.w;
+  }
+}
+__device__ __forceinline__ void load_rec(const double* p, double* r) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    const double2 a = q[k];
+    r[2 * k] = a.x;
+    r[2 * k + 1] = a.y;
+  }
+}
+__device__ __forceinline__ void store_rec(float* p, const float* r) {
+  float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) q[k] = make_float4(r[4 * k], r[4 * k + 1], r[4 * k + 2], r[4 * k + 3]);
+}
+__device__ __forceinline__ void store_rec(double* p, const double* r) {
+  double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+  for (int k = 0; k < 10; ++k) q[k] = make_double2(r[2 * k], r[2 * k + 1]);
+}
 
 // Record a timeout and leave: the caller has seen a bounded wait fail.
 __device__ __forceinline__ void flag_timeout(int* status) {
@@ -294,10 +329,11 @@ __device__ __forceinline__ void flag_timeout(int* status) {
 // Leaves the item's 8 error maxima / sums in red[0..7] (thread 0..7 views, see
 // below) and its 36 row sums in `itm` (kIter only).  Returns false when a
 // bounded wait expired (uniform across the block).
-template <class R, int MODE>
+template <class R, int MODE, bool MULTI>
 __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item, unsigned char* smem_raw,
-                                            uint32_t& parity, double* itm, R* tms, const R* fin_tau,
-                                            const R* fin_mu, R* fout_e, R* fout_g) {
+                                            uint32_t& parity, double* itm, R* tms, R (&tmax)[4],
+                                            double (&tsum)[4], const R* fin_tau, const R* fin_mu, R* fout_e,
+                                            R* fout_g) {
   const int rows = c.rows_a;
   const int N1 = c.n1;
   const int M = c.kx;                 // complex entries per row (N1 / 2, or 1)
@@ -312,6 +348,7 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
   double* red = reinterpret_cast<double*>(smem_raw + PassASmem<R>::red_off);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + PassASmem<R>::bar_off);
   R* dcin = reinterpret_cast<R*>(smem_raw + L.dc_off);
+  cpx<R>* tws = reinterpret_cast<cpx<R>*>(smem_raw + L.tw_off);
   const long long nrows = (long long)c.n2 * c.n3;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool use_vox = (MODE == kIter || MODE == kStart);
@@ -323,6 +360,8 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
   const long long v0 = row0 * N1;
   // ---------------------------------------------------------- issue loads
   if (use_vox && threadIdx.x < 18) tms[threadIdx.x] = (R)c.tmean[threadIdx.x];
+  // the x twiddle table, read many times per item, from shared memory
+  for (int k = threadIdx.x; k < N1; k += blockDim.x) tws[k] = c.px.tw[k];
   if (threadIdx.x == 0) {
     bulk_wait_read();     // the previous item's stores have read shared memory
     fence_proxy_async();  // and every thread's reads of it precede the new loads
@@ -351,9 +390,9 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
         dcin[cc * rows + rr] = b0[rr * M * 18 + cc].x;
       }
     if (packed) {
-      x_inverse_pre<R>(b0, b1, nr, M, msh, c.px.tw);
+      x_inverse_pre<R>(b0, b1, nr, M, msh, tws);
       __syncthreads();
-      zbuf = tile_fft<R, +1, 8>(b1, b0, nr, c.px);
+      zbuf = tile_fft<R, +1, 8>(b1, b0, nr, c.px, tws);
     }
   }
   if (use_vox) {
@@ -399,7 +438,8 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
         continue;
       }
       R* pv = prev_s + lv * 20;
-      const R* hv = hist_s + lv * 20;
+      R hr[20];  // history record: h_t, h_m, phase id
+      load_rec(hist_s + lv * 20, hr);
       R e[9], gm[9];
       if (MODE == kIter) {
 #pragma unroll
@@ -442,29 +482,32 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
           }
         }
       }
-      const PhaseDev<R>& P = c.phases[(int)hv[18]];
+      const PhaseDev<R>& P = c.phases[(int)hr[18]];
       const double2 pq = pq_s[lv];
       R t[9], m[9];
       double p, qq;
       R ft, fm;
-      radial_return<R>(P, e, gm, hv, hv + 9, pq.x, pq.y, t, m, p, qq, ft, fm);
+      radial_return<R>(P, e, gm, hr, hr + 9, pq.x, pq.y, t, m, p, qq, ft, fm);
       if (MODE == kIter) {
         // previous iterate: e, gamma stored; t, m rebuilt component by component
         // from the stored scale factors (t = tr/3 d + f_t dev(t_trial), m = f_m m_trial)
-        const R fto = pv[18], fmo = pv[19];
-        const R tre = (pv[0] + pv[4]) + pv[8], trg = (pv[9] + pv[13]) + pv[17];
-        const R vol = vol_of(trial_t(P, hv[0], pv[0], pv[0], true, tre),
-                             trial_t(P, hv[4], pv[4], pv[4], true, tre),
-                             trial_t(P, hv[8], pv[8], pv[8], true, tre));
+        R pr[20];
+        load_rec(pv, pr);
+        const R* hv = hr;
+        const R fto = pr[18], fmo = pr[19];
+        const R tre = (pr[0] + pr[4]) + pr[8], trg = (pr[9] + pr[13]) + pr[17];
+        const R vol = vol_of(trial_t(P, hv[0], pr[0], pr[0], true, tre),
+                             trial_t(P, hv[4], pr[4], pr[4], true, tre),
+                             trial_t(P, hv[8], pr[8], pr[8], true, tre));
         R de = R(0), dt = R(0), dg = R(0), dm = R(0);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
 #pragma unroll
           for (int l = 0; l < 3; ++l) {
             const int i = 3 * k + l, j = 3 * l + k;
-            const R to = scaled_t(trial_t(P, hv[i], pv[i], pv[j], k == l, tre), k == l, vol, fto);
-            const R mo = trial_m(P, hv[9 + i], pv[9 + i], pv[9 + j], k == l, trg) * fmo;
-            const R d1 = e[i] - pv[i], d2 = t[i] - to, d3 = gm[i] - pv[9 + i], d4 = m[i] - mo;
+            const R to = scaled_t(trial_t(P, hv[i], pr[i], pr[j], k == l, tre), k == l, vol, fto);
+            const R mo = trial_m(P, hv[9 + i], pr[9 + i], pr[9 + j], k == l, trg) * fmo;
+            const R d1 = e[i] - pr[i], d2 = t[i] - to, d3 = gm[i] - pr[9 + i], d4 = m[i] - mo;
             de += d1 * d1; dt += d2 * d2; dg += d3 * d3; dm += d4 * d4;
           }
         }
@@ -472,14 +515,18 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
         dmax[0] = max(dmax[0], de); dmax[1] = max(dmax[1], dt);
         dmax[2] = max(dmax[2], dg); dmax[3] = max(dmax[3], dm);
         dsum[0] += de; dsum[1] += dt; dsum[2] += dg; dsum[3] += dm;
+      }
+      {
+        R out[20];
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-          pv[q] = e[q];
-          pv[9 + q] = gm[q];
+          out[q] = e[q];
+          out[9 + q] = gm[q];
         }
+        out[18] = ft;
+        out[19] = fm;
+        store_rec(pv, out);
       }
-      pv[18] = ft;
-      pv[19] = fm;
       // polarizations (eq. micropolar_polarizatons): tau = t - A0 e, mu = m - B0 gamma,
       // transformed less the constants tau_c = <t>_prev - A0 E, mu_c = <m>_prev - B0 Gamma
       // (a constant only changes the k = 0 term, which the Green operator drops):
@@ -507,9 +554,9 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
   cpx<R>* X;
   if (packed) {
     cpx<R>* other = (zbuf == b0) ? b1 : b0;
-    cpx<R>* Z = tile_fft<R, -1, 8>(zbuf, other, nr, c.px);
+    cpx<R>* Z = tile_fft<R, -1, 8>(zbuf, other, nr, c.px, tws);
     cpx<R>* dst = (Z == b0) ? b1 : b0;
-    x_forward_post<R>(Z, dst, nr, M, msh, c.px.tw);
+    x_forward_post<R>(Z, dst, nr, M, msh, tws);
     X = dst;
   } else {
     X = zbuf;
@@ -522,18 +569,31 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
   }
   // ---------------------------------------------------------- error partials of the item
   if (MODE == kIter) {
+    // the sums only enter the average measure (eq. err_average)
+    const bool want_sum = c.err_kind != 0;
+    if constexpr (MULTI) {
+      // per-item record: maxima reduced in the field type (exact), sums in FP64
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const double mx = shfl_max((double)dmax[a]);
-      const double sm = shfl_sum((double)dsum[a]);
-      if (lane == 0) {
-        red[warp * 8 + a] = mx;
-        red[warp * 8 + 4 + a] = sm;
+      for (int a = 0; a < 4; ++a) {
+        const R mx = shfl_max(dmax[a]);
+        const double sm = want_sum ? shfl_sum((double)dsum[a]) : 0.0;
+        if (lane == 0) {
+          red[warp * 8 + a] = (double)mx;
+          red[warp * 8 + 4 + a] = sm;
+        }
+      }
+    } else {
+      // single cell: each thread carries its maxima and FP64 sums across the
+      // block's items; the block combines them once, at the end of the kernel
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        tmax[a] = max(tmax[a], dmax[a]);
+        if (want_sum) tsum[a] += (double)dsum[a];
       }
     }
     __syncthreads();
     const int nwarp = blockDim.x >> 5;
-    if (threadIdx.x < 8) {
+    if (MULTI && threadIdx.x < 8) {
       double a = red[threadIdx.x];
       for (int w = 1; w < nwarp; ++w) {
         const double vv = red[w * 8 + threadIdx.x];
@@ -581,12 +641,15 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
   uint32_t parity = 0;
   bool failed = false;
   int* status = c0.status;
+  R tmax[4] = {R(0), R(0), R(0), R(0)};
+  double tsum[4] = {0.0, 0.0, 0.0, 0.0};
   for_items<R, MULTI>(c0, c0.items_a, w, cs, [&](const CellDev<R>& c, long long item) {
     if (failed) {
       flag_timeout(c.status);  // every cell with a skipped item reports the failure
       return;
     }
-    if (!pass_a_item<R, MODE>(c, item, smem_raw, parity, itm, tms, fin_tau, fin_mu, fout_e, fout_g)) {
+    if (!pass_a_item<R, MODE, MULTI>(c, item, smem_raw, parity, itm, tms, tmax, tsum, fin_tau, fin_mu, fout_e,
+                                     fout_g)) {
       failed = true;
       status = c.status;
       return;
@@ -595,13 +658,36 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
       if constexpr (MULTI) {
         for (int i = threadIdx.x; i < kErrPartials; i += blockDim.x)
           c.ipart[item * kErrPartials + i] = itm[i];
-      } else if (threadIdx.x < kErrPartials) {
-        const int i = threadIdx.x;
-        acc[i] = (i < 4) ? fmax(acc[i], itm[i]) : acc[i] + itm[i];
+      } else if (threadIdx.x >= 8 && threadIdx.x < kErrPartials) {
+        acc[threadIdx.x] += itm[threadIdx.x];  // row sums; the error terms are carried per thread
       }
       __syncthreads();
     }
   });
+  if (MODE == kIter && !MULTI && !failed) {
+    // the block's error maxima and sums from the per-thread carries
+    double* red = reinterpret_cast<double*>(smem_raw + PassASmem<R>::red_off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const R mx = shfl_max(tmax[a]);
+      const double sm = shfl_sum(tsum[a]);
+      if (lane == 0) {
+        red[warp * 8 + a] = (double)mx;
+        red[warp * 8 + 4 + a] = sm;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      double a = red[threadIdx.x];
+      for (int wi = 1; wi < (int)(blockDim.x >> 5); ++wi) {
+        const double vv = red[wi * 8 + threadIdx.x];
+        a = (threadIdx.x < 4) ? fmax(a, vv) : a + vv;
+      }
+      acc[threadIdx.x] = a;
+    }
+    __syncthreads();
+  }
   if (threadIdx.x == 0) bulk_wait_all();
   if (failed) {
     // wait (bounded) for this block's loads still in flight, then report
@@ -950,7 +1036,7 @@ __global__ void __launch_bounds__(256) k_radial_return_points(
 
 // ------------------------------------------------------------------ launchers
 template <class R>
-size_t smem_line_pass(int n) { return 2ull * 18 * (size_t)n * sizeof(cpx<R>); }
+size_t smem_line_pass(int n) { return (2ull * 18 + 1) * (size_t)n * sizeof(cpx<R>); }  // 2 tiles + twiddles
 
 template <class R>
 size_t smem_pass_a(int n1, int rows) { return PassASmem<R>(n1, rows).total; }

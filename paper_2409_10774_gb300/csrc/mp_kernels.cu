@@ -316,6 +316,37 @@ __device__ __forceinline__ void store_rec(double* p, const double* r) {
   for (int k = 0; k < 10; ++k) q[k] = make_double2(r[2 * k], r[2 * k + 1]);
 }
 
+// 18-value records (the predictor base elast) are 72 / 144 bytes apart: 8- /
+// 16-byte pieces.
+__device__ __forceinline__ void load_rec18(const float* p, float* r) {
+  const float2* q = reinterpret_cast<const float2*>(p);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const float2 a = q[k];
+    r[2 * k] = a.x;
+    r[2 * k + 1] = a.y;
+  }
+}
+__device__ __forceinline__ void load_rec18(const double* p, double* r) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const double2 a = q[k];
+    r[2 * k] = a.x;
+    r[2 * k + 1] = a.y;
+  }
+}
+__device__ __forceinline__ void store_rec18(float* p, const float* r) {
+  float2* q = reinterpret_cast<float2*>(p);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) q[k] = make_float2(r[2 * k], r[2 * k + 1]);
+}
+__device__ __forceinline__ void store_rec18(double* p, const double* r) {
+  double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) q[k] = make_double2(r[2 * k], r[2 * k + 1]);
+}
+
 // Record a timeout and leave: the caller has seen a bounded wait fail.
 __device__ __forceinline__ void flag_timeout(int* status) {
   if (threadIdx.x == 0 && status) atomicOr(status, 1);
@@ -849,42 +880,43 @@ __global__ void __launch_bounds__(256) k_init(CellDev<R> c0, Work<R> w) {
 // history of Algorithm 1; homogenized sums; when c.predict, the linear-
 // extrapolation predictor of the next increment, e' = e_n + ratio (e_n - e_{n-1}).
 // Per 256-voxel chunk: sums of t (9), m (9), e (9), gamma (9), p, q, t_eq, m_eq.
-template <class R>
+// COLS: instead of reducing the chunk, add the thread's values to its own
+// column of `cols` ([kAvgPartials][blockDim] doubles; single-cell commit).
+template <class R, bool COLS>
 __device__ __forceinline__ void commit_chunk(const CellDev<R>& c, long long chunk, double* out40,
-                                             double (*red)[kAvgPartials]) {
+                                             double (*red)[kAvgPartials], double* cols) {
   double acc[kAvgPartials];
 #pragma unroll
   for (int i = 0; i < kAvgPartials; ++i) acc[i] = 0.0;
   const long long v = chunk * 256 + threadIdx.x;
   if (threadIdx.x < 256 && v < c.nvox) {
+    // records move in 16- / 8-byte pieces (they are 80 / 72 bytes apart)
     R* pv = c.prev + v * 20;
     R* hv = c.hist + v * 20;
-    R e[9], g[9], ht[9], hm[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      e[q] = pv[q];
-      g[q] = pv[9 + q];
-      ht[q] = hv[q];
-      hm[q] = hv[9 + q];
-    }
-    const PhaseDev<R>& P = c.phases[(int)hv[18]];
+    R pr[20], hr[20];
+    load_rec(pv, pr);
+    load_rec(hv, hr);
+    const R* e = pr;
+    const R* g = pr + 9;
+    const PhaseDev<R>& P = c.phases[(int)hr[18]];
     double2 pq = reinterpret_cast<const double2*>(c.pq)[v];
     R t[9], m[9];
     double p, q;
     R ft, fm;
-    radial_return<R>(P, e, g, ht, hm, pq.x, pq.y, t, m, p, q, ft, fm);
+    radial_return<R>(P, e, g, hr, hr + 9, pq.x, pq.y, t, m, p, q, ft, fm);
     R ae[9], bg[9];
     apply_A<R>(P.lam, P.mu, P.kap, e, ae);
     apply_B<R>(P.alpha, P.beta, P.gamma, g, bg);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      hv[i] = t[i] - ae[i];
-      hv[9 + i] = m[i] - bg[i];
       acc[i] = (double)t[i];
       acc[9 + i] = (double)m[i];
       acc[18 + i] = (double)e[i];
       acc[27 + i] = (double)g[i];
+      hr[i] = t[i] - ae[i];
+      hr[9 + i] = m[i] - bg[i];
     }
+    store_rec(hv, hr);
     reinterpret_cast<double2*>(c.pq)[v] = make_double2(p, q);
     double teq, meq;
     equivalents<R>(P, t, m, teq, meq);
@@ -895,15 +927,19 @@ __device__ __forceinline__ void commit_chunk(const CellDev<R>& c, long long chun
     if (c.predict) {
       const R ratio = (R)c.ratio;
       R* el = c.elast + v * 18;
+      R old[18];
+      load_rec18(el, old);
+      store_rec18(el, pr);  // e, gamma (the first 18 values of the iterate record)
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const R eo = el[i], go = el[9 + i];
-        el[i] = e[i];
-        el[9 + i] = g[i];
-        pv[i] = e[i] + ratio * (e[i] - eo);
-        pv[9 + i] = g[i] + ratio * (g[i] - go);
-      }
+      for (int i = 0; i < 18; ++i) pr[i] = pr[i] + ratio * (pr[i] - old[i]);
+      store_rec(pv, pr);    // the predictor, with the last scale factors
     }
+  }
+  if constexpr (COLS) {
+    // thread-private columns: no cross-thread work per chunk
+#pragma unroll
+    for (int i = 0; i < kAvgPartials; ++i) cols[i * blockDim.x + threadIdx.x] += acc[i];
+    return;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -920,26 +956,37 @@ __device__ __forceinline__ void commit_chunk(const CellDev<R>& c, long long chun
   __syncthreads();
 }
 
-// Single cell: per-block totals in partials[block][40] (a fixed grid gives a
-// fixed order).  Multi: per-chunk records in each cell's apart.
+// Single: each thread accumulates its voxels' values in FP64 in its own
+// shared-memory column across the block's chunks; the block folds the columns
+// once into partials[block][40] (a fixed grid gives a fixed order).  Multi:
+// per-chunk records in each cell's apart.
 template <class R, bool MULTI>
 __global__ void __launch_bounds__(256) k_commit(CellDev<R> c0, Work<R> w, double* partials) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];  // single: [kAvgPartials][256] doubles
   __shared__ CellDev<R> cs;
   __shared__ double red[8][kAvgPartials];
   __shared__ double chunk_sum[kAvgPartials];
-  __shared__ double block_sum[kAvgPartials];
-  if (threadIdx.x < kAvgPartials) block_sum[threadIdx.x] = 0.0;
-  __syncthreads();
+  double* cols = reinterpret_cast<double*>(smem_raw);
+  if constexpr (!MULTI) {
+    for (int i = threadIdx.x; i < kAvgPartials * (int)blockDim.x; i += blockDim.x) cols[i] = 0.0;
+  }
   for_items<R, MULTI>(c0, (c0.nvox + 255) / 256, w, cs, [&](const CellDev<R>& c, long long chunk) {
-    commit_chunk<R>(c, chunk, chunk_sum, red);
-    if (threadIdx.x < kAvgPartials) {
-      if constexpr (MULTI) c.apart[chunk * kAvgPartials + threadIdx.x] = chunk_sum[threadIdx.x];
-      else block_sum[threadIdx.x] += chunk_sum[threadIdx.x];
+    commit_chunk<R, !MULTI>(c, chunk, chunk_sum, red, cols);
+    if constexpr (MULTI) {
+      if (threadIdx.x < kAvgPartials) c.apart[chunk * kAvgPartials + threadIdx.x] = chunk_sum[threadIdx.x];
+      __syncthreads();
     }
-    __syncthreads();
   });
-  if (!MULTI && threadIdx.x < kAvgPartials)
-    partials[(long long)blockIdx.x * kAvgPartials + threadIdx.x] = block_sum[threadIdx.x];
+  if constexpr (!MULTI) {
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < kAvgPartials; i += nw) {
+      double sm = 0.0;
+      for (int k = lane; k < (int)blockDim.x; k += 32) sm += cols[i * blockDim.x + k];
+      sm = shfl_sum(sm);
+      if (lane == 0) partials[(long long)blockIdx.x * kAvgPartials + i] = sm;
+    }
+  }
 }
 
 // Sum of the commit partials in a fixed order, divided by the voxel count.
@@ -1041,6 +1088,8 @@ size_t smem_line_pass(int n) { return (2ull * 18 + 1) * (size_t)n * sizeof(cpx<R
 template <class R>
 size_t smem_pass_a(int n1, int rows) { return PassASmem<R>(n1, rows).total; }
 
+constexpr size_t kCommitSmem = (size_t)kAvgPartials * 256 * sizeof(double);  // single-cell commit columns
+
 // Raise each kernel's dynamic shared-memory limit to what its static shared
 // memory leaves of the opt-in maximum (at least kSmemBudget).
 template <class R>
@@ -1048,12 +1097,14 @@ static cudaError_t set_smem_attrs() {
   static bool done = false;
   if (done) return cudaSuccess;
   cudaError_t e = cudaSuccess;
-  auto raise = [&](const void* fn) {
+  // tiles: kernels whose tiles may take up to kSmemBudget (their static shared
+  // memory must fit the reserve)
+  auto raise = [&](const void* fn, bool tiles = true) {
     if (e != cudaSuccess) return;
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return;
-    if (fa.sharedSizeBytes > kSmemStaticReserve) {
+    if (tiles && fa.sharedSizeBytes > kSmemStaticReserve) {
       e = cudaErrorInvalidValue;
       return;
     }
@@ -1072,6 +1123,7 @@ static cudaError_t set_smem_attrs() {
   raise((const void*)k_pass_a<R, kXInv, false>);
   raise((const void*)k_pass_a<R, kIter, true>);
   raise((const void*)k_pass_a<R, kStart, true>);
+  raise((const void*)k_commit<R, false>, false);
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -1147,7 +1199,7 @@ cudaError_t launch_start(const LaunchCfg& L, const CellDev<R>& c, int first, cud
 template <class R>
 cudaError_t launch_commit(const LaunchCfg& L, const CellDev<R>& c, double* partials, double* avg_out,
                           cudaStream_t st) {
-  k_commit<R, false><<<L.grid_v, 256, 0, st>>>(c, Work<R>{}, partials);
+  k_commit<R, false><<<L.grid_v, 256, kCommitSmem, st>>>(c, Work<R>{}, partials);
   k_reduce_avg<<<1, 64, 0, st>>>(partials, L.grid_v, c.inv_nvox, avg_out);
   return cudaGetLastError();
 }

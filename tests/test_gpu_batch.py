@@ -113,8 +113,18 @@ def test_batch_agrees_with_single_solve(ctx):
             assert s["status"] == b["status"] == "ok"
             for k in _FIELD_KEYS:
                 assert np.array_equal(s["final"][k], b["final"][k]), (precision, k)
-            for k in ("T", "M", "Eavg", "Gavg", "P", "Q", "Teq", "Meq"):
-                assert _rel(b[k], s[k]) <= 1e-12, (precision, k)
+            # each quantity against its own scale or its dimensional partner's
+            # (a couple stress, curvature or micro-plastic strain that the load
+            # leaves at zero is pure rounding in both)
+            h = p["h"]
+            scale = {"T": np.abs(s["T"]).max(), "Eavg": np.abs(s["Eavg"]).max(), "P": np.abs(s["P"]).max(),
+                     "Teq": np.abs(s["Teq"]).max()}
+            scale["M"] = max(np.abs(s["M"]).max(), h * scale["T"])
+            scale["Gavg"] = max(np.abs(s["Gavg"]).max(), scale["Eavg"] / h)
+            scale["Q"] = max(np.abs(s["Q"]).max(), scale["P"])
+            scale["Meq"] = max(np.abs(s["Meq"]).max(), h * scale["Teq"])
+            for k, sc in scale.items():
+                assert np.abs(b[k] - s[k]).max() <= 1e-12 * sc, (precision, k)
 
 
 def test_batch_failures_stay_per_item(ctx):

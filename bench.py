@@ -69,7 +69,7 @@ def _source_hash():
 def _traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "traffic_pass_a_voronoi256.txt")
     try:
         data = json.load(open(path))
     except (OSError, ValueError):

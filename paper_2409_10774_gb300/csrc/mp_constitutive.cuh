@@ -106,22 +106,6 @@ __device__ __forceinline__ R trial_m(const PhaseDev<R>& P, R h, R gi, R gj, bool
   return diag ? fma(P.alpha, tr, v) : v;
 }
 
-template <class R>
-__device__ __forceinline__ void trial(const PhaseDev<R>& P, const R* e, const R* g, const R* ht,
-                                      const R* hm, R* t, R* m) {
-  const R tre = (e[0] + e[4]) + e[8];
-  const R trg = (g[0] + g[4]) + g[8];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-#pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      const int i = 3 * k + l, j = 3 * l + k;
-      t[i] = trial_t(P, ht[i], e[i], e[j], k == l, tre);
-      m[i] = trial_m(P, hm[i], g[i], g[j], k == l, trg);
-    }
-  }
-}
-
 // Final stresses from the trial ones and the two scale factors:
 // t = tr(t_trial)/3 d + f_t dev(t_trial), m = f_m m_trial.
 template <class R>
@@ -131,31 +115,26 @@ __device__ __forceinline__ R scaled_t(R ttr, bool diag, R vol, R ft) {
   return diag ? fma(ft, ttr - vol, vol) : ttr * ft;
 }
 
+// Algorithm 1, one level at a time: the macro level maps e (with the history
+// ht, p_n) to t, p and the scale factor ft; the micro level maps gamma (hm,
+// q_n) to m, q, fm.  The two levels share nothing but the phase, so a caller
+// short of registers can run them one after the other.
 template <class R>
-__device__ __forceinline__ void assemble(R* t, R* m, R ft, R fm) {
-  const R vol = vol_of(t[0], t[4], t[8]);
+__device__ __forceinline__ void return_macro(const PhaseDev<R>& P, const R* e, const R* ht, double pn, R* t,
+                                             double& p, R& ft) {
+  const R tre = (e[0] + e[4]) + e[8];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) t[i] = scaled_t(t[i], i % 4 == 0, vol, ft);
+  for (int k = 0; k < 3; ++k) {
 #pragma unroll
-  for (int i = 0; i < 9; ++i) m[i] *= fm;
-}
-
-// Algorithm 1.  In: e, g (gamma), history ht, hm, p_n, q_n.  Out: t, m (final
-// stresses), p, q and the scale factors ft, fm (1 on elastic branches).
-template <class R>
-__device__ __forceinline__ void radial_return(const PhaseDev<R>& P, const R* e, const R* g,
-                                              const R* ht, const R* hm, double pn, double qn, R* t,
-                                              R* m, double& p, double& q, R& ft, R& fm) {
-  trial(P, e, g, ht, hm, t, m);
+    for (int l = 0; l < 3; ++l) t[3 * k + l] = trial_t(P, ht[3 * k + l], e[3 * k + l], e[3 * l + k], k == l, tre);
+  }
   p = pn;
-  q = qn;
   ft = R(1);
-  fm = R(1);
+  const R vol = vol_of(t[0], t[4], t[8]);
   if (!P.elastic) {
     constexpr int kNewton = sizeof(R) == 4 ? 1 : 2;
-    // macro level (eq. equiv_stress on the trial deviator)
+    // eq. equiv_stress on the trial deviator
     R s[9];
-    const R vol = vol_of(t[0], t[4], t[8]);
 #pragma unroll
     for (int i = 0; i < 9; ++i) s[i] = t[i];
     s[0] -= vol; s[4] -= vol; s[8] -= vol;
@@ -176,7 +155,25 @@ __device__ __forceinline__ void radial_return(const PhaseDev<R>& P, const R* e, 
         ft = (R)fma(P.ct_inv * R1n, rinv, P.tH_inv);
       }
     }
-    // micro level (eq. equiv_couple_stress on the trial couple stress)
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) t[i] = scaled_t(t[i], i % 4 == 0, vol, ft);
+}
+
+template <class R>
+__device__ __forceinline__ void return_micro(const PhaseDev<R>& P, const R* g, const R* hm, double qn, R* m,
+                                             double& q, R& fm) {
+  const R trg = (g[0] + g[4]) + g[8];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int l = 0; l < 3; ++l) m[3 * k + l] = trial_m(P, hm[3 * k + l], g[3 * k + l], g[3 * l + k], k == l, trg);
+  }
+  q = qn;
+  fm = R(1);
+  if (!P.elastic) {
+    constexpr int kNewton = sizeof(R) == 4 ? 1 : 2;
+    // eq. equiv_couple_stress on the trial couple stress
     const R meq2r = eq_sq(m, P.b1, P.b2, P.skew_m != 0);
     const bool in_m = sizeof(R) == 4 && surely_inside((float)meq2r, P.mYf, P.mHf, qn);
     const double R2n = fma(P.mH, qn, P.mY);
@@ -190,7 +187,18 @@ __device__ __forceinline__ void radial_return(const PhaseDev<R>& P, const R* e, 
       }
     }
   }
-  assemble(t, m, ft, fm);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) m[i] *= fm;
+}
+
+// Algorithm 1.  In: e, g (gamma), history ht, hm, p_n, q_n.  Out: t, m (final
+// stresses), p, q and the scale factors ft, fm (1 on elastic branches).
+template <class R>
+__device__ __forceinline__ void radial_return(const PhaseDev<R>& P, const R* e, const R* g,
+                                              const R* ht, const R* hm, double pn, double qn, R* t,
+                                              R* m, double& p, double& q, R& ft, R& fm) {
+  return_macro<R>(P, e, ht, pn, t, p, ft);
+  return_micro<R>(P, g, hm, qn, m, q, fm);
 }
 
 // eq_sq for a full (non-deviatoric) couple stress: m_eq^2 uses m itself.

@@ -437,19 +437,14 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
       const int rr = lv / N1, x = lv - rr * N1;
       const int zb = (rr * M + (packed ? (x >> 1) : 0)) * 18;  // first comp of the voxel's complex
       const long long v = v0 + lv;
-      R val[18];
-      if (use_spec_in) {
-#pragma unroll
-        for (int q = 0; q < 18; ++q) {
-          const cpx<R> z = zbuf[zb + q];
-          val[q] = (packed && (x & 1)) ? z.y : z.x;
-        }
-      }
+      // value q of the inverse-transformed row at this voxel (read where it is
+      // used, so that only one level's values are in registers at a time)
+      const R* zv = reinterpret_cast<const R*>(zbuf + zb) + ((packed && (x & 1)) ? 1 : 0);
       if (MODE == kXInv) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-          fout_e[v * 9 + q] = val[q];
-          fout_g[v * 9 + q] = val[9 + q];
+          fout_e[v * 9 + q] = zv[2 * q];
+          fout_g[v * 9 + q] = zv[2 * (9 + q)];
         }
         continue;
       }
@@ -468,105 +463,164 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
         }
         continue;
       }
+      // The voxel's two levels (Algorithm 1's macro level: e, t, f_t; micro
+      // level: gamma, m, f_m) are independent: they run one after the other so
+      // that only one level's tensors are held in registers at a time.  Records
+      // (80 bytes apart) move in 16-byte pieces:
+      //   previous iterate  {e0-3} {e4-7} {e8 g0 g1 g2} {g3-6} {g7 g8 f_t f_m}
+      //   history           {ht0-3} {ht4-7} {ht8 hm0 hm1 hm2} {hm3-6} {hm7 hm8 phase 0}
+      float4* pv4 = reinterpret_cast<float4*>(prev_s + lv * 20);
+      const float4* hv4 = reinterpret_cast<const float4*>(hist_s + lv * 20);
       R* pv = prev_s + lv * 20;
-      R hr[20];  // history record: h_t, h_m, phase id
-      load_rec(hist_s + lv * 20, hr);
-      R e[9], gm[9];
-      if (MODE == kIter) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-          e[q] = c.E[q] + val[q];
-          gm[q] = c.G[q] + val[9 + q];
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-          e[q] = pv[q];
-          gm[q] = pv[9 + q];
-        }
-      }
-      // A0 (e - E), B0 (gamma - Gamma) go to this voxel's output slots now (the
-      // fluctuations val, or the predictor less the load, are at hand here);
-      // the polarization below completes them
-      {
-        R de[9], dg[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-          de[q] = (MODE == kIter) ? val[q] : e[q] - c.E[q];
-          dg[q] = (MODE == kIter) ? val[9 + q] : gm[q] - c.G[q];
-        }
-        const R tre = de[0] + de[4] + de[8], trg = dg[0] + dg[4] + dg[8];
-        const R a = c.ref.mu + c.ref.kap, b = c.ref.mu - c.ref.kap;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-#pragma unroll
-          for (int l = 0; l < 3; ++l) {
-            const int i = 3 * k + l, j = 3 * l + k;
-            R ae = a * de[i] + b * de[j];
-            R bg = c.ref.beta * dg[i] + c.ref.gamma * dg[j];
-            if (k == l) {
-              ae += c.ref.lam * tre;
-              bg += c.ref.alpha * trg;
-            }
-            zr[2 * i] = ae;
-            zr[2 * (9 + i)] = bg;
-          }
-        }
-      }
-      const PhaseDev<R>& P = c.phases[(int)hr[18]];
+      const R* hv = hist_s + lv * 20;
+      const PhaseDev<R>& P = c.phases[(int)hv[18]];
       const double2 pq = pq_s[lv];
-      R t[9], m[9];
-      double p, qq;
-      R ft, fm;
-      radial_return<R>(P, e, gm, hr, hr + 9, pq.x, pq.y, t, m, p, qq, ft, fm);
-      if (MODE == kIter) {
-        // previous iterate: e, gamma stored; t, m rebuilt component by component
-        // from the stored scale factors (t = tr/3 d + f_t dev(t_trial), m = f_m m_trial)
-        R pr[20];
-        load_rec(pv, pr);
-        const R* hv = hr;
-        const R fto = pr[18], fmo = pr[19];
-        const R tre = (pr[0] + pr[4]) + pr[8], trg = (pr[9] + pr[13]) + pr[17];
-        const R vol = vol_of(trial_t(P, hv[0], pr[0], pr[0], true, tre),
-                             trial_t(P, hv[4], pr[4], pr[4], true, tre),
-                             trial_t(P, hv[8], pr[8], pr[8], true, tre));
-        R de = R(0), dt = R(0), dg = R(0), dm = R(0);
+      const R fto = pv[18], fmo = pv[19];
+      const R a0 = c.ref.mu + c.ref.kap, b0 = c.ref.mu - c.ref.kap;
+      R ft, fm, e8;
+      // ---- macro level
+      {
+        R e[9], eo[9], ht[9], t[9];
+        if constexpr (sizeof(R) == 4) {
+          const float4 q0 = pv4[0], q1 = pv4[1], q2 = pv4[2];
+          const float4 h0 = hv4[0], h1 = hv4[1], h2 = hv4[2];
+          eo[0] = q0.x; eo[1] = q0.y; eo[2] = q0.z; eo[3] = q0.w;
+          eo[4] = q1.x; eo[5] = q1.y; eo[6] = q1.z; eo[7] = q1.w; eo[8] = q2.x;
+          ht[0] = h0.x; ht[1] = h0.y; ht[2] = h0.z; ht[3] = h0.w;
+          ht[4] = h1.x; ht[5] = h1.y; ht[6] = h1.z; ht[7] = h1.w; ht[8] = h2.x;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 9; ++q) {
+            eo[q] = pv[q];
+            ht[q] = hv[q];
+          }
+        }
+#pragma unroll
+        R val[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) val[q] = (MODE == kIter) ? zv[2 * q] : R(0);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) e[q] = (MODE == kIter) ? c.E[q] + val[q] : eo[q];
+        double pn = pq.x;
+        return_macro<R>(P, e, ht, pn, t, pn, ft);
+        if (MODE == kIter) {
+          // previous stresses rebuilt from the stored strains and scale factor
+          // (t = tr/3 d + f_t dev(t_trial)), in the same operation order
+          const R tre = (eo[0] + eo[4]) + eo[8];
+          const R vol = vol_of(trial_t(P, ht[0], eo[0], eo[0], true, tre), trial_t(P, ht[4], eo[4], eo[4], true, tre),
+                               trial_t(P, ht[8], eo[8], eo[8], true, tre));
+          R de = R(0), dt = R(0);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+              const int i = 3 * k + l, j = 3 * l + k;
+              const R to = scaled_t(trial_t(P, ht[i], eo[i], eo[j], k == l, tre), k == l, vol, fto);
+              const R d1 = e[i] - eo[i], d2 = t[i] - to;
+              de += d1 * d1;
+              dt += d2 * d2;
+            }
+          }
+          de = sqrt(de);
+          dt = sqrt(dt);
+          dmax[0] = max(dmax[0], de); dmax[1] = max(dmax[1], dt);
+          dsum[0] += de; dsum[1] += dt;
+        }
+        // tau - tau_c = (t - <t>_prev) - A0 (e - E): the constants tau_c =
+        // <t>_prev - A0 E only change the k = 0 term, which the Green operator
+        // drops; the transforms then round relative to a field of fluctuations
+        R de9[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) de9[q] = (MODE == kIter) ? val[q] : e[q] - c.E[q];
+        const R tre = de9[0] + de9[4] + de9[8];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
 #pragma unroll
           for (int l = 0; l < 3; ++l) {
             const int i = 3 * k + l, j = 3 * l + k;
-            const R to = scaled_t(trial_t(P, hv[i], pr[i], pr[j], k == l, tre), k == l, vol, fto);
-            const R mo = trial_m(P, hv[9 + i], pr[9 + i], pr[9 + j], k == l, trg) * fmo;
-            const R d1 = e[i] - pr[i], d2 = t[i] - to, d3 = gm[i] - pr[9 + i], d4 = m[i] - mo;
-            de += d1 * d1; dt += d2 * d2; dg += d3 * d3; dm += d4 * d4;
+            R ae = a0 * de9[i] + b0 * de9[j];
+            if (k == l) ae += c.ref.lam * tre;
+            zr[2 * i] = (t[i] - tms[i]) - ae;
           }
         }
-        de = sqrt(de); dt = sqrt(dt); dg = sqrt(dg); dm = sqrt(dm);
-        dmax[0] = max(dmax[0], de); dmax[1] = max(dmax[1], dt);
-        dmax[2] = max(dmax[2], dg); dmax[3] = max(dmax[3], dm);
-        dsum[0] += de; dsum[1] += dt; dsum[2] += dg; dsum[3] += dm;
-      }
-      {
-        R out[20];
+        if constexpr (sizeof(R) == 4) {
+          pv4[0] = make_float4(e[0], e[1], e[2], e[3]);
+          pv4[1] = make_float4(e[4], e[5], e[6], e[7]);
+        } else {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-          out[q] = e[q];
-          out[9 + q] = gm[q];
+          for (int q = 0; q < 8; ++q) pv[q] = e[q];
         }
-        out[18] = ft;
-        out[19] = fm;
-        store_rec(pv, out);
+        e8 = e[8];
       }
-      // polarizations (eq. micropolar_polarizatons): tau = t - A0 e, mu = m - B0 gamma,
-      // transformed less the constants tau_c = <t>_prev - A0 E, mu_c = <m>_prev - B0 Gamma
-      // (a constant only changes the k = 0 term, which the Green operator drops):
-      // tau - tau_c = (t - <t>_prev) - A0 (e - E) is made of fluctuations, so the
-      // transforms' rounding, relative to the size of their input, is smaller
+      // ---- micro level
+      {
+        R g[9], go[9], hm[9], m[9];
+        if constexpr (sizeof(R) == 4) {
+          const float4 q2 = pv4[2], q3 = pv4[3], q4 = pv4[4];
+          const float4 h2 = hv4[2], h3 = hv4[3], h4 = hv4[4];
+          go[0] = q2.y; go[1] = q2.z; go[2] = q2.w; go[3] = q3.x; go[4] = q3.y;
+          go[5] = q3.z; go[6] = q3.w; go[7] = q4.x; go[8] = q4.y;
+          hm[0] = h2.y; hm[1] = h2.z; hm[2] = h2.w; hm[3] = h3.x; hm[4] = h3.y;
+          hm[5] = h3.z; hm[6] = h3.w; hm[7] = h4.x; hm[8] = h4.y;
+        } else {
 #pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        zr[2 * q] = (t[q] - tms[q]) - zr[2 * q];
-        zr[2 * (9 + q)] = (m[q] - tms[9 + q]) - zr[2 * (9 + q)];
+          for (int q = 0; q < 9; ++q) {
+            go[q] = pv[9 + q];
+            hm[q] = hv[9 + q];
+          }
+        }
+#pragma unroll
+        R val[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) val[q] = (MODE == kIter) ? zv[2 * (9 + q)] : R(0);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) g[q] = (MODE == kIter) ? c.G[q] + val[q] : go[q];
+        double qn = pq.y;
+        return_micro<R>(P, g, hm, qn, m, qn, fm);
+        if (MODE == kIter) {
+          const R trg = (go[0] + go[4]) + go[8];
+          R dg = R(0), dm = R(0);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+              const int i = 3 * k + l, j = 3 * l + k;
+              const R mo = trial_m(P, hm[i], go[i], go[j], k == l, trg) * fmo;
+              const R d3 = g[i] - go[i], d4 = m[i] - mo;
+              dg += d3 * d3;
+              dm += d4 * d4;
+            }
+          }
+          dg = sqrt(dg);
+          dm = sqrt(dm);
+          dmax[2] = max(dmax[2], dg); dmax[3] = max(dmax[3], dm);
+          dsum[2] += dg; dsum[3] += dm;
+        }
+        R dg9[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dg9[q] = (MODE == kIter) ? val[q] : g[q] - c.G[q];
+        const R trg = dg9[0] + dg9[4] + dg9[8];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+          for (int l = 0; l < 3; ++l) {
+            const int i = 3 * k + l, j = 3 * l + k;
+            R bg = c.ref.beta * dg9[i] + c.ref.gamma * dg9[j];
+            if (k == l) bg += c.ref.alpha * trg;
+            zr[2 * (9 + i)] = (m[i] - tms[9 + i]) - bg;
+          }
+        }
+        if constexpr (sizeof(R) == 4) {
+          pv4[2] = make_float4(e8, g[0], g[1], g[2]);
+          pv4[3] = make_float4(g[3], g[4], g[5], g[6]);
+          pv4[4] = make_float4(g[7], g[8], ft, fm);
+        } else {
+          pv[8] = e8;
+#pragma unroll
+          for (int q = 0; q < 9; ++q) pv[9 + q] = g[q];
+          pv[18] = ft;
+          pv[19] = fm;
+        }
       }
     }
     if (MODE == kXInv) {

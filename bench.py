@@ -229,6 +229,21 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- GPU leg
 
+def combine_ranks(ms, voxel_iters, world):
+    """Whole-job figures of the replicas: the slowest rank's time and the
+    voxel-iterations of all ranks (every rank calls this; process group
+    already initialised when world > 1)."""
+    if world <= 1:
+        return float(ms), float(voxel_iters)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tot = torch.tensor([float(voxel_iters)], dtype=torch.float64)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(tot[0])
+
+
 def _config(args):
     return {"workload": f"voronoi{args.cells}-{args.n}^3", "n": args.n, "cells": args.cells,
             "increments": 20, "load": "E11 to 1%", "tol": 1e-6, "err": "local",
@@ -295,15 +310,7 @@ def run_ours(args, rank, world, local_rank):
     rve.profile(False)
     rve.close()
 
-    local = torch.tensor([ms, float(iters) * nvox], dtype=torch.float64)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot = torch.tensor([float(iters) * nvox], dtype=torch.float64)
-        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.SUM)
-        ms_max, vox_it = float(t[0]), float(tot[0])
-    else:
-        ms_max, vox_it = float(local[0]), float(local[1])
+    ms_max, vox_it = combine_ranks(ms, float(iters) * nvox, world)
     value = vox_it / (ms_max / 1e3)
 
     # ---------------- roofline of the dominant kernel (events on the run's stream)

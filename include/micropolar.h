@@ -208,8 +208,9 @@ mp_status mp_rve_profile_read(const mp_rve* rve, double* ms, int64_t* launches, 
  * iterating, in launches shared by all of them, and each cell leaves its
  * loop, commits and starts its next increment on its own error (eq. err).
  * A cell's results are identical (bit for bit) whichever cells it shares the
- * batch with; they equal mp_solve's up to the summation order of the
- * error and homogenized-average reductions.  results[i] receives problem i's
+ * batch with; they agree with mp_solve's to rounding (mp_solve runs
+ * separately compiled single-cell forms of the kernels and sums its error
+ * and homogenized-average reductions in another order).  results[i] receives problem i's
  * outputs as mp_solve would write them (results may be NULL for none);
  * per_item[i] (may be NULL) its status.  Returns MP_OK when every problem
  * succeeded, else the status of the first that failed (message from

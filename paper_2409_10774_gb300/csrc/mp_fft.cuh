@@ -175,6 +175,38 @@ __device__ void stage_aos(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ ou
   }
 }
 
+// The same stage with the radix, Ns, the line length M and the twiddle stride
+// known at compile time (index arithmetic folds to shifts and constants, and
+// only the one butterfly is instantiated).
+template <class R, int DIR, int RADIX, int NS, int M, int TSTRIDE>
+__device__ __forceinline__ void stage_fixed(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out, int rows,
+                                            const cpx<R>* __restrict__ tw) {
+  constexpr int nb = M / RADIX;
+  constexpr int tstep = M / (NS * RADIX);
+  constexpr int rs = M * 18;
+  const int total = rows * nb * 18;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int c = idx % 18;
+    const int q = idx / 18;
+    const int rr = q / nb, j = q % nb;
+    const int kk = j % NS, jq = j / NS;
+    const cpx<R>* src = in + rr * rs + c;
+    cpx<R> v[RADIX];
+    v[0] = src[j * 18];
+#pragma unroll
+    for (int r = 1; r < RADIX; ++r) {
+      const cpx<R> x = src[(j + r * nb) * 18];
+      v[r] = (NS == 1) ? x : cmul(x, twiddle<R, DIR>(tw, r * kk * tstep * TSTRIDE));
+    }
+    if constexpr (RADIX == 2) dft2<R, DIR>(v);
+    else if constexpr (RADIX == 4) dft4<R, DIR>(v);
+    else dft8<R, DIR>(v);
+    cpx<R>* dst = out + rr * rs + c + (jq * NS * RADIX + kk) * 18;
+#pragma unroll
+    for (int r = 0; r < RADIX; ++r) dst[r * NS * 18] = v[r];
+  }
+}
+
 // Transform every line of an AoS tile; data starts in b0, the result pointer
 // (b0 or b1) is returned.  Ends with a barrier.  `tw`, when given, is a copy
 // of the plan's twiddle table (e.g. in shared memory).
@@ -194,6 +226,45 @@ __device__ cpx<R>* tile_fft(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R>&
     out = t;
   }
   return in;
+}
+
+// The x-axis transform inside pass A (twiddle stride 2: the table holds the
+// N1 = 2 M roots).  Lengths whose plan (radix 8 first, 4 last; see the host's
+// radix plan) is known are unrolled at compile time; others take tile_fft.
+template <class R, int DIR>
+__device__ cpx<R>* tile_fft_x(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R>& p, const cpx<R>* tw) {
+  auto sync_swap = [&]() {
+    __syncthreads();
+    cpx<R>* t = b0;
+    b0 = b1;
+    b1 = t;
+  };
+  switch (p.m) {
+    case 256:
+      stage_fixed<R, DIR, 8, 1, 256, 2>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, DIR, 8, 8, 256, 2>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, DIR, 4, 64, 256, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    case 128:
+      stage_fixed<R, DIR, 8, 1, 128, 2>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, DIR, 4, 8, 128, 2>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, DIR, 4, 32, 128, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    case 64:
+      stage_fixed<R, DIR, 8, 1, 64, 2>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, DIR, 8, 8, 64, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    case 32:
+      stage_fixed<R, DIR, 8, 1, 32, 2>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, DIR, 4, 8, 32, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    case 16:
+      stage_fixed<R, DIR, 4, 1, 16, 2>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, DIR, 4, 4, 16, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    default:
+      return tile_fft<R, DIR, 8>(b0, b1, rows, p, tw);
+  }
 }
 
 }  // namespace mp

@@ -423,7 +423,7 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
     if (packed) {
       x_inverse_pre<R>(b0, b1, nr, M, msh, tws);
       __syncthreads();
-      zbuf = tile_fft<R, +1, 8>(b1, b0, nr, c.px, tws);
+      zbuf = tile_fft_x<R, +1>(b1, b0, nr, c.px, tws);
     }
   }
   if (use_vox) {
@@ -639,7 +639,7 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
   cpx<R>* X;
   if (packed) {
     cpx<R>* other = (zbuf == b0) ? b1 : b0;
-    cpx<R>* Z = tile_fft<R, -1, 8>(zbuf, other, nr, c.px, tws);
+    cpx<R>* Z = tile_fft_x<R, -1>(zbuf, other, nr, c.px, tws);
     cpx<R>* dst = (Z == b0) ? b1 : b0;
     x_forward_post<R>(Z, dst, nr, M, msh, tws);
     X = dst;

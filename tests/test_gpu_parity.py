@@ -107,7 +107,9 @@ def _oracle_green(n, h, ref, tau, mu):
 
 
 @pytest.mark.parametrize("n", [(16, 16, 16), (24, 12, 8), (48, 6, 2), (1, 8, 6), (8, 1, 4),
-                               (6, 4, 1), (2, 2, 2), (1, 1, 1), (32, 18, 36)])
+                               (6, 4, 1), (2, 2, 2), (1, 1, 1), (32, 18, 36),
+                               # x lengths whose transform stages are unrolled at compile time
+                               (64, 6, 4), (128, 4, 2), (256, 2, 4)])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_green_apply_matches_oracle(ctx, n, precision):
     import paper_2409_10774_gb300 as M

@@ -200,7 +200,8 @@ __device__ __forceinline__ void stage_fixed(const cpx<R>* __restrict__ in, cpx<R
     }
     if constexpr (RADIX == 2) dft2<R, DIR>(v);
     else if constexpr (RADIX == 4) dft4<R, DIR>(v);
-    else dft8<R, DIR>(v);
+    else if constexpr (RADIX == 8) dft8<R, DIR>(v);
+    else dft16<R, DIR>(v);
     cpx<R>* dst = out + rr * rs + c + (jq * NS * RADIX + kk) * 18;
 #pragma unroll
     for (int r = 0; r < RADIX; ++r) dst[r * NS * 18] = v[r];
@@ -264,6 +265,31 @@ __device__ cpx<R>* tile_fft_x(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R
       return b0;
     default:
       return tile_fft<R, DIR, 8>(b0, b1, rows, p, tw);
+  }
+}
+
+// The y / z column transforms (one line per component, twiddle stride 1):
+// power-of-two lengths with the host's radix-16 plan unrolled at compile
+// time, others through tile_fft.
+template <class R, int DIR>
+__device__ cpx<R>* tile_fft_yz(cpx<R>* b0, cpx<R>* b1, const AxisPlan<R>& p, const cpx<R>* tw) {
+  auto sync_swap = [&]() {
+    __syncthreads();
+    cpx<R>* t = b0;
+    b0 = b1;
+    b1 = t;
+  };
+  switch (p.m) {
+    case 256:
+      stage_fixed<R, DIR, 16, 1, 256, 1>(b0, b1, 1, tw); sync_swap();
+      stage_fixed<R, DIR, 16, 16, 256, 1>(b0, b1, 1, tw); sync_swap();
+      return b0;
+    case 128:
+      stage_fixed<R, DIR, 16, 1, 128, 1>(b0, b1, 1, tw); sync_swap();
+      stage_fixed<R, DIR, 8, 16, 128, 1>(b0, b1, 1, tw); sync_swap();
+      return b0;
+    default:
+      return tile_fft<R, DIR, 16>(b0, b1, 1, p, tw);
   }
 }
 

@@ -140,13 +140,13 @@ __device__ __forceinline__ void fft_y_tile(const CellDev<R>& c, long long tile, 
   for (int k = threadIdx.x; k < N; k += blockDim.x) tws[k] = c.py.tw[k];
   copy_column<R, true>(b0, g, N, stride);
   __syncthreads();
-  cpx<R>* r = tile_fft<R, DIR, 16>(b0, b1, 1, c.py, tws);
+  cpx<R>* r = tile_fft_yz<R, DIR>(b0, b1, c.py, tws);
   copy_column<R, false>(r, g, N, stride);
   __syncthreads();
 }
 
 template <class R, int DIR, bool MULTI>
-__global__ void __launch_bounds__(kThreadsYZ) k_fft_y(CellDev<R> c0, Work<R> w) {
+__global__ void __launch_bounds__(kThreadsYZ, 3) k_fft_y(CellDev<R> c0, Work<R> w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ CellDev<R> cs;
   for_items<R, MULTI>(c0, (long long)c0.n3 * c0.kx, w, cs,
@@ -178,7 +178,7 @@ __device__ __forceinline__ void green_z_tile(const CellDev<R>& c, long long tile
   for (int k = threadIdx.x; k < N; k += blockDim.x) tws[k] = c.pz.tw[k];
   copy_column<R, true>(b0, g, N, stride);
   __syncthreads();
-  cpx<R>* r = tile_fft<R, -1, 16>(b0, b1, 1, c.pz, tws);
+  cpx<R>* r = tile_fft_yz<R, -1>(b0, b1, c.pz, tws);
   const R x1 = c.n1 == 1 ? R(0) : c.two_pi_over_L[0] * (R)kx;
   const R x2 = signed_freq_scale<R>(ky, c.n2, c.two_pi_over_L[1]);
   for (int kz = threadIdx.x; kz < N; kz += blockDim.x) {
@@ -195,7 +195,7 @@ __device__ __forceinline__ void green_z_tile(const CellDev<R>& c, long long tile
   }
   __syncthreads();
   cpx<R>* other = (r == b0) ? b1 : b0;
-  cpx<R>* o = tile_fft<R, +1, 16>(r, other, 1, c.pz, tws);
+  cpx<R>* o = tile_fft_yz<R, +1>(r, other, c.pz, tws);
   copy_column<R, false>(o, g, N, stride);
   __syncthreads();
 }

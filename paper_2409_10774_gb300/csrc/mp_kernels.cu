@@ -200,6 +200,9 @@ __device__ __forceinline__ void green_z_tile(const CellDev<R>& c, long long tile
   __syncthreads();
 }
 
+// Two 288-thread blocks per SM: the register file is split over the SM's
+// four sub-partitions, so 18 warps allow 96 registers per thread (a few
+// spills in FP32 cost less than dropping to one block per SM).
 template <class R, bool MULTI>
 __global__ void __launch_bounds__(kThreadsYZ, 2) k_green_z(CellDev<R> c0, Work<R> w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -199,6 +199,7 @@ __device__ __forceinline__ void stage_fixed(const cpx<R>* __restrict__ in, cpx<R
       v[r] = (NS == 1) ? x : cmul(x, twiddle<R, DIR>(tw, r * kk * tstep * TSTRIDE));
     }
     if constexpr (RADIX == 2) dft2<R, DIR>(v);
+    else if constexpr (RADIX == 3) dft3<R, DIR>(v);
     else if constexpr (RADIX == 4) dft4<R, DIR>(v);
     else if constexpr (RADIX == 8) dft8<R, DIR>(v);
     else dft16<R, DIR>(v);
@@ -230,8 +231,9 @@ __device__ cpx<R>* tile_fft(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R>&
 }
 
 // The x-axis transform inside pass A (twiddle stride 2: the table holds the
-// N1 = 2 M roots).  Lengths whose plan (radix 8 first, 4 last; see the host's
-// radix plan) is known are unrolled at compile time; others take tile_fft.
+// N1 = 2 M roots).  Common lengths, whose plan (radix <= 8, radix 3 last; see
+// the host's radix plan) is known, are unrolled at compile time; others take
+// tile_fft.
 template <class R, int DIR>
 __device__ cpx<R>* tile_fft_x(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R>& p, const cpx<R>* tw) {
   auto sync_swap = [&]() {
@@ -263,33 +265,75 @@ __device__ cpx<R>* tile_fft_x(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R
       stage_fixed<R, DIR, 4, 1, 16, 2>(b0, b1, rows, tw); sync_swap();
       stage_fixed<R, DIR, 4, 4, 16, 2>(b0, b1, rows, tw); sync_swap();
       return b0;
+    case 24:
+      stage_fixed<R, DIR, 8, 1, 24, 2>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, DIR, 3, 8, 24, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    case 12:
+      stage_fixed<R, DIR, 4, 1, 12, 2>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, DIR, 3, 4, 12, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    case 8:
+      stage_fixed<R, DIR, 8, 1, 8, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
     default:
       return tile_fft<R, DIR, 8>(b0, b1, rows, p, tw);
   }
 }
 
 // The y / z column transforms (one line per component, twiddle stride 1):
-// power-of-two lengths with the host's radix-16 plan unrolled at compile
-// time, others through tile_fft.
-template <class R, int DIR>
-__device__ cpx<R>* tile_fft_yz(cpx<R>* b0, cpx<R>* b1, const AxisPlan<R>& p, const cpx<R>* tw) {
+// the common lengths with the host's plan (radix 16 where it saves a stage,
+// radix 3 last) unrolled at compile time, others through tile_fft.
+template <class R, int DIR, int N>
+__device__ __forceinline__ cpx<R>* fft_yz_fixed(cpx<R>* b0, cpx<R>* b1, const cpx<R>* tw) {
   auto sync_swap = [&]() {
     __syncthreads();
     cpx<R>* t = b0;
     b0 = b1;
     b1 = t;
   };
-  switch (p.m) {
-    case 256:
-      stage_fixed<R, DIR, 16, 1, 256, 1>(b0, b1, 1, tw); sync_swap();
-      stage_fixed<R, DIR, 16, 16, 256, 1>(b0, b1, 1, tw); sync_swap();
-      return b0;
-    case 128:
-      stage_fixed<R, DIR, 16, 1, 128, 1>(b0, b1, 1, tw); sync_swap();
-      stage_fixed<R, DIR, 8, 16, 128, 1>(b0, b1, 1, tw); sync_swap();
-      return b0;
-    default:
-      return tile_fft<R, DIR, 16>(b0, b1, 1, p, tw);
+  if constexpr (N == 256) {
+    stage_fixed<R, DIR, 16, 1, 256, 1>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 16, 16, 256, 1>(b0, b1, 1, tw); sync_swap();
+  } else if constexpr (N == 128) {
+    stage_fixed<R, DIR, 16, 1, 128, 1>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 8, 16, 128, 1>(b0, b1, 1, tw); sync_swap();
+  } else if constexpr (N == 64) {
+    stage_fixed<R, DIR, 8, 1, 64, 1>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 8, 8, 64, 1>(b0, b1, 1, tw); sync_swap();
+  } else if constexpr (N == 48) {
+    stage_fixed<R, DIR, 16, 1, 48, 1>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 3, 16, 48, 1>(b0, b1, 1, tw); sync_swap();
+  } else if constexpr (N == 32) {
+    stage_fixed<R, DIR, 8, 1, 32, 1>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 4, 8, 32, 1>(b0, b1, 1, tw); sync_swap();
+  } else if constexpr (N == 24) {
+    stage_fixed<R, DIR, 8, 1, 24, 1>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 3, 8, 24, 1>(b0, b1, 1, tw); sync_swap();
+  } else {
+    static_assert(N == 16, "no compile-time plan for this length");
+    stage_fixed<R, DIR, 16, 1, 16, 1>(b0, b1, 1, tw); sync_swap();
+  }
+  return b0;
+}
+
+// A kernel compiled for one length (NF > 0) runs only that plan; the NF = 0
+// form dispatches on the plan's length at run time.
+template <class R, int DIR, int NF>
+__device__ cpx<R>* tile_fft_yz(cpx<R>* b0, cpx<R>* b1, const AxisPlan<R>& p, const cpx<R>* tw) {
+  if constexpr (NF > 0) {
+    return fft_yz_fixed<R, DIR, NF>(b0, b1, tw);
+  } else {
+    switch (p.m) {
+      case 256: return fft_yz_fixed<R, DIR, 256>(b0, b1, tw);
+      case 128: return fft_yz_fixed<R, DIR, 128>(b0, b1, tw);
+      case 64: return fft_yz_fixed<R, DIR, 64>(b0, b1, tw);
+      case 48: return fft_yz_fixed<R, DIR, 48>(b0, b1, tw);
+      case 32: return fft_yz_fixed<R, DIR, 32>(b0, b1, tw);
+      case 24: return fft_yz_fixed<R, DIR, 24>(b0, b1, tw);
+      case 16: return fft_yz_fixed<R, DIR, 16>(b0, b1, tw);
+      default: return tile_fft<R, DIR, 16>(b0, b1, 1, p, tw);
+    }
   }
 }
 

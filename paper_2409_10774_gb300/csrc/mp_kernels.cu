@@ -127,7 +127,7 @@ __device__ __forceinline__ void for_items(const CellDev<R>& c0, long long n0, co
 
 // ------------------------------------------------------------------ y pass
 // One tile = one (kz, kx) column: 18 lines of length N2.
-template <class R, int DIR>
+template <class R, int DIR, int NF>
 __device__ __forceinline__ void fft_y_tile(const CellDev<R>& c, long long tile, unsigned char* smem) {
   cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem);
   const int N = c.n2;
@@ -140,22 +140,24 @@ __device__ __forceinline__ void fft_y_tile(const CellDev<R>& c, long long tile, 
   for (int k = threadIdx.x; k < N; k += blockDim.x) tws[k] = c.py.tw[k];
   copy_column<R, true>(b0, g, N, stride);
   __syncthreads();
-  cpx<R>* r = tile_fft_yz<R, DIR>(b0, b1, c.py, tws);
+  cpx<R>* r = tile_fft_yz<R, DIR, NF>(b0, b1, c.py, tws);
   copy_column<R, false>(r, g, N, stride);
   __syncthreads();
 }
 
-template <class R, int DIR, bool MULTI>
+// NF > 0: compiled for one column length (its transform plan unrolled);
+// NF = 0: any length, dispatched at run time (multi-cell launches).
+template <class R, int DIR, bool MULTI, int NF>
 __global__ void __launch_bounds__(kThreadsYZ, 3) k_fft_y(CellDev<R> c0, Work<R> w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ CellDev<R> cs;
   for_items<R, MULTI>(c0, (long long)c0.n3 * c0.kx, w, cs,
-                      [&](const CellDev<R>& c, long long t) { fft_y_tile<R, DIR>(c, t, smem_raw); });
+                      [&](const CellDev<R>& c, long long t) { fft_y_tile<R, DIR, NF>(c, t, smem_raw); });
 }
 
 // ------------------------------------------------------------------ z pass + Green
 // One tile = one (ky, kx) column: 18 lines of length N3.
-template <class R>
+template <class R, int NF>
 __device__ __forceinline__ void green_z_tile(const CellDev<R>& c, long long tile, unsigned char* smem) {
   cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem);
   const int N = c.n3;
@@ -178,7 +180,7 @@ __device__ __forceinline__ void green_z_tile(const CellDev<R>& c, long long tile
   for (int k = threadIdx.x; k < N; k += blockDim.x) tws[k] = c.pz.tw[k];
   copy_column<R, true>(b0, g, N, stride);
   __syncthreads();
-  cpx<R>* r = tile_fft_yz<R, -1>(b0, b1, c.pz, tws);
+  cpx<R>* r = tile_fft_yz<R, -1, NF>(b0, b1, c.pz, tws);
   const R x1 = c.n1 == 1 ? R(0) : c.two_pi_over_L[0] * (R)kx;
   const R x2 = signed_freq_scale<R>(ky, c.n2, c.two_pi_over_L[1]);
   for (int kz = threadIdx.x; kz < N; kz += blockDim.x) {
@@ -195,7 +197,7 @@ __device__ __forceinline__ void green_z_tile(const CellDev<R>& c, long long tile
   }
   __syncthreads();
   cpx<R>* other = (r == b0) ? b1 : b0;
-  cpx<R>* o = tile_fft_yz<R, +1>(r, other, c.pz, tws);
+  cpx<R>* o = tile_fft_yz<R, +1, NF>(r, other, c.pz, tws);
   copy_column<R, false>(o, g, N, stride);
   __syncthreads();
 }
@@ -203,12 +205,12 @@ __device__ __forceinline__ void green_z_tile(const CellDev<R>& c, long long tile
 // Two 288-thread blocks per SM: the register file is split over the SM's
 // four sub-partitions, so 18 warps allow 96 registers per thread (a few
 // spills in FP32 cost less than dropping to one block per SM).
-template <class R, bool MULTI>
+template <class R, bool MULTI, int NF>
 __global__ void __launch_bounds__(kThreadsYZ, 2) k_green_z(CellDev<R> c0, Work<R> w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ CellDev<R> cs;
   for_items<R, MULTI>(c0, (long long)c0.n2 * c0.kx, w, cs,
-                      [&](const CellDev<R>& c, long long t) { green_z_tile<R>(c, t, smem_raw); });
+                      [&](const CellDev<R>& c, long long t) { green_z_tile<R, NF>(c, t, smem_raw); });
 }
 
 // ------------------------------------------------------------------ x pass (pass A)
@@ -1168,12 +1170,18 @@ static cudaError_t set_smem_attrs() {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kSmemOptin - fa.sharedSizeBytes));
   };
-  raise((const void*)k_fft_y<R, -1, false>);
-  raise((const void*)k_fft_y<R, +1, false>);
-  raise((const void*)k_fft_y<R, -1, true>);
-  raise((const void*)k_fft_y<R, +1, true>);
-  raise((const void*)k_green_z<R, false>);
-  raise((const void*)k_green_z<R, true>);
+  raise((const void*)k_fft_y<R, -1, false, 0>);
+  raise((const void*)k_fft_y<R, +1, false, 0>);
+  raise((const void*)k_fft_y<R, -1, false, 128>);
+  raise((const void*)k_fft_y<R, +1, false, 128>);
+  raise((const void*)k_fft_y<R, -1, false, 256>);
+  raise((const void*)k_fft_y<R, +1, false, 256>);
+  raise((const void*)k_fft_y<R, -1, true, 0>);
+  raise((const void*)k_fft_y<R, +1, true, 0>);
+  raise((const void*)k_green_z<R, false, 0>);
+  raise((const void*)k_green_z<R, false, 128>);
+  raise((const void*)k_green_z<R, false, 256>);
+  raise((const void*)k_green_z<R, true, 0>);
   raise((const void*)k_pass_a<R, kIter, false>);
   raise((const void*)k_pass_a<R, kStart, false>);
   raise((const void*)k_pass_a<R, kXFwd, false>);
@@ -1201,8 +1209,16 @@ cudaError_t launch_fft_y(const LaunchCfg& L, const CellDev<R>& c, int dir, cudaS
   cudaError_t e = set_smem_attrs<R>();
   if (e != cudaSuccess) return e;
   if (c.n2 > 1) {
-    if (dir < 0) k_fft_y<R, -1, false><<<L.grid_y, kThreadsYZ, smem_line_pass<R>(c.n2), st>>>(c, Work<R>{});
-    else k_fft_y<R, +1, false><<<L.grid_y, kThreadsYZ, smem_line_pass<R>(c.n2), st>>>(c, Work<R>{});
+    const size_t sm = smem_line_pass<R>(c.n2);
+    if (dir < 0) {
+      if (c.n2 == 256) k_fft_y<R, -1, false, 256><<<L.grid_y, kThreadsYZ, sm, st>>>(c, Work<R>{});
+      else if (c.n2 == 128) k_fft_y<R, -1, false, 128><<<L.grid_y, kThreadsYZ, sm, st>>>(c, Work<R>{});
+      else k_fft_y<R, -1, false, 0><<<L.grid_y, kThreadsYZ, sm, st>>>(c, Work<R>{});
+    } else {
+      if (c.n2 == 256) k_fft_y<R, +1, false, 256><<<L.grid_y, kThreadsYZ, sm, st>>>(c, Work<R>{});
+      else if (c.n2 == 128) k_fft_y<R, +1, false, 128><<<L.grid_y, kThreadsYZ, sm, st>>>(c, Work<R>{});
+      else k_fft_y<R, +1, false, 0><<<L.grid_y, kThreadsYZ, sm, st>>>(c, Work<R>{});
+    }
   }
   return cudaGetLastError();
 }
@@ -1211,7 +1227,10 @@ template <class R>
 cudaError_t launch_green_z(const LaunchCfg& L, const CellDev<R>& c, cudaStream_t st) {
   cudaError_t e = set_smem_attrs<R>();
   if (e != cudaSuccess) return e;
-  k_green_z<R, false><<<L.grid_z, kThreadsYZ, smem_line_pass<R>(c.n3), st>>>(c, Work<R>{});
+  const size_t sm = smem_line_pass<R>(c.n3);
+  if (c.n3 == 256) k_green_z<R, false, 256><<<L.grid_z, kThreadsYZ, sm, st>>>(c, Work<R>{});
+  else if (c.n3 == 128) k_green_z<R, false, 128><<<L.grid_z, kThreadsYZ, sm, st>>>(c, Work<R>{});
+  else k_green_z<R, false, 0><<<L.grid_z, kThreadsYZ, sm, st>>>(c, Work<R>{});
   return cudaGetLastError();
 }
 
@@ -1267,11 +1286,11 @@ cudaError_t launch_multi_iteration(const MultiCfg<R>& m, cudaStream_t st) {
   cudaError_t e = set_smem_attrs<R>();
   if (e != cudaSuccess) return e;
   if (m.items_y > 0)
-    k_fft_y<R, -1, true><<<m.grid_y, kThreadsYZ, m.smem_y, st>>>(CellDev<R>{}, m.wy);
+    k_fft_y<R, -1, true, 0><<<m.grid_y, kThreadsYZ, m.smem_y, st>>>(CellDev<R>{}, m.wy);
   if (m.items_z > 0)
-    k_green_z<R, true><<<m.grid_z, kThreadsYZ, m.smem_z, st>>>(CellDev<R>{}, m.wz);
+    k_green_z<R, true, 0><<<m.grid_z, kThreadsYZ, m.smem_z, st>>>(CellDev<R>{}, m.wz);
   if (m.items_y > 0)
-    k_fft_y<R, +1, true><<<m.grid_y, kThreadsYZ, m.smem_y, st>>>(CellDev<R>{}, m.wy);
+    k_fft_y<R, +1, true, 0><<<m.grid_y, kThreadsYZ, m.smem_y, st>>>(CellDev<R>{}, m.wy);
   if (m.items_a > 0)
     k_pass_a<R, kIter, true><<<m.grid_a, kThreads, m.smem_a, st>>>(CellDev<R>{}, m.wa, nullptr, nullptr,
                                                                     nullptr, nullptr, nullptr);
@@ -1300,8 +1319,8 @@ cudaError_t launch_multi_commit(const MultiCfg<R>& m, cudaStream_t st) {
 template <class R>
 void multi_grids(MultiCfg<R>& m, int nsm) {
   set_smem_attrs<R>();
-  m.grid_y = grid_for<R>((const void*)k_fft_y<R, -1, true>, kThreadsYZ, m.smem_y, m.items_y, nsm);
-  m.grid_z = grid_for<R>((const void*)k_green_z<R, true>, kThreadsYZ, m.smem_z, m.items_z, nsm);
+  m.grid_y = grid_for<R>((const void*)k_fft_y<R, -1, true, 0>, kThreadsYZ, m.smem_y, m.items_y, nsm);
+  m.grid_z = grid_for<R>((const void*)k_green_z<R, true, 0>, kThreadsYZ, m.smem_z, m.items_z, nsm);
   m.grid_a = grid_for<R>((const void*)k_pass_a<R, kIter, true>, kThreads, m.smem_a, m.items_a, nsm);
   m.grid_s = grid_for<R>((const void*)k_pass_a<R, kStart, true>, kThreads, m.smem_a, m.items_s, nsm);
   long long g = m.items_v < 8ll * nsm ? m.items_v : 8ll * nsm;
@@ -1326,9 +1345,9 @@ cudaError_t launch_green_apply(const LaunchCfg& L, const CellDev<R>& c, const R*
   if (e != cudaSuccess) return e;
   const size_t sa = smem_pass_a<R>(c.n1, c.rows_a);
   k_pass_a<R, kXFwd, false><<<L.grid_a, kThreads, sa, st>>>(c, Work<R>{}, nullptr, tau, mu, nullptr, nullptr);
-  if (c.n2 > 1) k_fft_y<R, -1, false><<<L.grid_y, kThreadsYZ, smem_line_pass<R>(c.n2), st>>>(c, Work<R>{});
-  k_green_z<R, false><<<L.grid_z, kThreadsYZ, smem_line_pass<R>(c.n3), st>>>(c, Work<R>{});
-  if (c.n2 > 1) k_fft_y<R, +1, false><<<L.grid_y, kThreadsYZ, smem_line_pass<R>(c.n2), st>>>(c, Work<R>{});
+  if (c.n2 > 1) k_fft_y<R, -1, false, 0><<<L.grid_y, kThreadsYZ, smem_line_pass<R>(c.n2), st>>>(c, Work<R>{});
+  k_green_z<R, false, 0><<<L.grid_z, kThreadsYZ, smem_line_pass<R>(c.n3), st>>>(c, Work<R>{});
+  if (c.n2 > 1) k_fft_y<R, +1, false, 0><<<L.grid_y, kThreadsYZ, smem_line_pass<R>(c.n2), st>>>(c, Work<R>{});
   k_pass_a<R, kXInv, false><<<L.grid_a, kThreads, sa, st>>>(c, Work<R>{}, nullptr, nullptr, nullptr, e_out, g_out);
   return cudaGetLastError();
 }
@@ -1380,9 +1399,15 @@ LaunchCfg make_launch_cfg(const CellDev<R>& c, int nsm) {
   L.items_a = items;
   L.grid_a = grid_for<R>((const void*)k_pass_a<R, kIter, false>, kThreads, smem_pass_a<R>(c.n1, rows), items,
                          nsm);
-  L.grid_y = grid_for<R>((const void*)k_fft_y<R, -1, false>, kThreadsYZ, smem_line_pass<R>(c.n2),
+  const void* fy = c.n2 == 256   ? (const void*)k_fft_y<R, -1, false, 256>
+                   : c.n2 == 128 ? (const void*)k_fft_y<R, -1, false, 128>
+                                 : (const void*)k_fft_y<R, -1, false, 0>;
+  const void* fz = c.n3 == 256   ? (const void*)k_green_z<R, false, 256>
+                   : c.n3 == 128 ? (const void*)k_green_z<R, false, 128>
+                                 : (const void*)k_green_z<R, false, 0>;
+  L.grid_y = grid_for<R>(fy, kThreadsYZ, smem_line_pass<R>(c.n2),
                          (long long)c.n3 * c.kx, nsm);
-  L.grid_z = grid_for<R>((const void*)k_green_z<R, false>, kThreadsYZ, smem_line_pass<R>(c.n3),
+  L.grid_z = grid_for<R>(fz, kThreadsYZ, smem_line_pass<R>(c.n3),
                          (long long)c.n2 * c.kx, nsm);
   long long vb = (c.nvox + 255) / 256;
   L.grid_v = (int)(vb < 4ll * nsm ? vb : 4ll * nsm);

@@ -44,11 +44,12 @@ struct PhaseDev {
   R lam, mu, kap, alpha, beta, gamma;   // eq. stiffnesses_iso
   R a1, a2, b1, b2;                     // eq. equiv_stress / equiv_couple_stress (b2 = 0 if gamma == beta)
   double tY, tH, mY, mH;                // eq. radius_1 / radius_2 (elastic: +inf yield)
-  float tYf, tHf, mYf, mHf;             // the same rounded to single precision (elastic-branch screen)
+  float tYf, tHf, mYf, mHf;             // the same rounded to single precision (FP32 fields)
   double ct, cm;                        // 2 a1 mu and b1 (gamma + beta) (eq. trial_stresses2)
   double inv_t, inv_m;                  // 1 / (tH + ct), 1 / (mH + cm)
   double ct_inv, tH_inv;                // ct / (tH + ct), tH / (tH + ct)
   double cm_inv, mH_inv;                // cm / (mH + cm), mH / (mH + cm)
+  float inv_tf, inv_mf, ct_invf, tH_invf, cm_invf, mH_invf;  // the last six in single precision
   int elastic;
   int skew_m;                           // 1 when gamma > beta (b2 finite, skew part of m live)
 };

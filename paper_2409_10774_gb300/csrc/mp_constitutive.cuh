@@ -20,9 +20,8 @@ namespace mp {
 
 // 1 / sqrt(x) in FP64 for x > 0 by Newton's method on f(y) = 1/y^2 - x,
 // y <- y (3 - x y^2) / 2, from the single-precision hardware estimate
-// (relative error ~1e-7).  One step leaves ~1e-14, below single precision
-// (enough when the result scales FP32 fields); two steps reach FP64 rounding.
-// Arguments outside the single-precision normal range take the FP64 library path.
+// (relative error ~1e-7).  Two steps reach FP64 rounding.  Arguments outside
+// the single-precision normal range take the FP64 library path.
 // xf is x rounded to single precision (callers often have it at hand).
 template <int STEPS>
 __device__ __forceinline__ double rsqrt_newton(double x, float xf) {
@@ -34,25 +33,32 @@ __device__ __forceinline__ double rsqrt_newton(double x, float xf) {
   return y;
 }
 
-// A single-precision lower bound of x >= 0 from the top word of its FP64 bit
-// pattern (mantissa truncated to 20 bits; 0 below the float normal range,
-// FLT_MAX above it), with integer operations only.
-__device__ __forceinline__ float float_below(double x) {
+// x >= 0 rounded toward zero to single precision (0 below the float normal
+// range, FLT_MAX above it), with integer operations only.
+__device__ __forceinline__ float float_rz(double x) {
   const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
   const int ex = (hi >> 20) & 0x7ff;
   if (hi <= 0 || ex < 1023 - 126) return 0.0f;
   if (ex > 1023 + 127) return 3.402823466e38f;
-  return __int_as_float(((ex - 1023 + 127) << 23) | ((hi & 0xfffff) << 3));
+  return __int_as_float(((ex - 1023 + 127) << 23) | ((hi & 0xfffff) << 3) | (int)(lo >> 29));
 }
 
-// True when the single-precision trial value q2 = (t_eq^trial)^2 is certainly
-// below (Y + H p)^2 - i.e. the FP64 test of the elastic branch is certain to
-// pass - so that the FP64 test can be skipped.  Yf, Hf are Y, H rounded to
-// single precision and p is bounded from below, so the single-precision
-// radius is within a few ulps of the FP64 one; the 1e-5 margin covers that.
-__device__ __forceinline__ bool surely_inside(float q2, float Yf, float Hf, double p) {
-  const float r = fmaf(Hf, float_below(p), Yf);
-  return q2 < r * r * 0.99999f;
+// Closed-form return of one level in single precision (FP32 fields): the
+// trial value q2 = (eq. stress)^2 is itself a single-precision quantity, so
+// the radius Y + H p_n, the multiplier increment and the scale factor are
+// formed in single precision too; only the accumulated multiplier p stays in
+// FP64, so that small increments are not lost against it.  Returns false on
+// the elastic branch.
+__device__ __forceinline__ bool return_level_f32(float q2, float Yf, float Hf, float inv, float c_inv, float H_inv,
+                                                 double pn, double& p, float& f) {
+  const float Rn = fmaf(Hf, float_rz(pn), Yf);
+  if (q2 < Rn * Rn) return false;
+  const float rinv = rsqrtf(q2);
+  const float eq = q2 * rinv;
+  p = pn + (double)((eq - Rn) * inv);
+  f = fmaf(c_inv * Rn, rinv, H_inv);
+  return true;
 }
 
 // t_kl = lam tr(e) d_kl + (mu + kappa) e_kl + (mu - kappa) e_lk  (eq. elast_constitutive_iso)
@@ -132,25 +138,24 @@ __device__ __forceinline__ void return_macro(const PhaseDev<R>& P, const R* e, c
   ft = R(1);
   const R vol = vol_of(t[0], t[4], t[8]);
   if (!P.elastic) {
-    constexpr int kNewton = sizeof(R) == 4 ? 1 : 2;
     // eq. equiv_stress on the trial deviator
     R s[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) s[i] = t[i];
     s[0] -= vol; s[4] -= vol; s[8] -= vol;
     const R teq2r = eq_sq(s, P.a1, P.a2, true);
-    // FP32 fields: a trial value far inside the yield surface needs no FP64 test
-    const bool in_t = sizeof(R) == 4 && surely_inside((float)teq2r, P.tYf, P.tHf, pn);
-    const double R1n = fma(P.tH, pn, P.tY);
-    if (!in_t) {
-      const double teq2 = (double)teq2r;
-      if (!(teq2 < R1n * R1n)) {          // plastic: t_eq^trial >= t_Y + t_H p_n
+    if constexpr (sizeof(R) == 4) {
+      float f;
+      if (return_level_f32(teq2r, P.tYf, P.tHf, P.inv_tf, P.ct_invf, P.tH_invf, pn, p, f)) ft = f;
+    } else {
+      const double R1n = fma(P.tH, pn, P.tY);
+      if (!(teq2r < R1n * R1n)) {  // plastic: t_eq^trial >= t_Y + t_H p_n
         // eq. trial_stresses2: p - p_n = (t_eq^trial - R1(p_n)) / (t_H + 2 a1 mu).
         // Since R1(p) + 2 a1 mu (p - p_n) = t_eq^trial, the return factor
         // R1 / (R1 + 2 a1 mu (p - p_n)) = R1(p) / t_eq^trial
         //   = [2 a1 mu R1(p_n) + t_H t_eq^trial] / [(t_H + 2 a1 mu) t_eq^trial].
-        const double rinv = rsqrt_newton<kNewton>(teq2, (float)teq2r);
-        const double teq = teq2 * rinv;
+        const double rinv = rsqrt_newton<2>(teq2r, (float)teq2r);
+        const double teq = teq2r * rinv;
         p = pn + (teq - R1n) * P.inv_t;
         ft = (R)fma(P.ct_inv * R1n, rinv, P.tH_inv);
       }
@@ -172,16 +177,16 @@ __device__ __forceinline__ void return_micro(const PhaseDev<R>& P, const R* g, c
   q = qn;
   fm = R(1);
   if (!P.elastic) {
-    constexpr int kNewton = sizeof(R) == 4 ? 1 : 2;
     // eq. equiv_couple_stress on the trial couple stress
     const R meq2r = eq_sq(m, P.b1, P.b2, P.skew_m != 0);
-    const bool in_m = sizeof(R) == 4 && surely_inside((float)meq2r, P.mYf, P.mHf, qn);
-    const double R2n = fma(P.mH, qn, P.mY);
-    if (!in_m) {
-      const double meq2 = (double)meq2r;
-      if (!(meq2 < R2n * R2n)) {
-        const double rinv = rsqrt_newton<kNewton>(meq2, (float)meq2r);
-        const double meq = meq2 * rinv;
+    if constexpr (sizeof(R) == 4) {
+      float f;
+      if (return_level_f32(meq2r, P.mYf, P.mHf, P.inv_mf, P.cm_invf, P.mH_invf, qn, q, f)) fm = f;
+    } else {
+      const double R2n = fma(P.mH, qn, P.mY);
+      if (!(meq2r < R2n * R2n)) {
+        const double rinv = rsqrt_newton<2>(meq2r, (float)meq2r);
+        const double meq = meq2r * rinv;
         q = qn + (meq - R2n) * P.inv_m;
         fm = (R)fma(P.cm_inv * R2n, rinv, P.mH_inv);
       }

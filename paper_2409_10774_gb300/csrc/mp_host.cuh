@@ -87,6 +87,12 @@ PhaseDev<R> phase_dev(const mp_phase& ph) {
   d.tH_inv = ph.tH / (ph.tH + d.ct);
   d.cm_inv = d.cm / (ph.mH + d.cm);
   d.mH_inv = ph.mH / (ph.mH + d.cm);
+  d.inv_tf = (float)d.inv_t;
+  d.inv_mf = (float)d.inv_m;
+  d.ct_invf = (float)d.ct_inv;
+  d.tH_invf = (float)d.tH_inv;
+  d.cm_invf = (float)d.cm_inv;
+  d.mH_invf = (float)d.mH_inv;
   return d;
 }
 

@@ -500,7 +500,6 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
             ht[q] = hv[q];
           }
         }
-#pragma unroll
         R val[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) val[q] = (MODE == kIter) ? zv[2 * q] : R(0);
@@ -574,7 +573,6 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
             hm[q] = hv[9 + q];
           }
         }
-#pragma unroll
         R val[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) val[q] = (MODE == kIter) ? zv[2 * (9 + q)] : R(0);

@@ -29,10 +29,22 @@ __device__ __forceinline__ double shfl_max(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
-__device__ __forceinline__ double shfl_sum(double v) {
+template <class T>
+__device__ __forceinline__ T shfl_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Compensated (Kahan) accumulation s += x; c carries the rounding lost so far
+// (the sum is s - c).  Keeps per-thread running sums in the field type accurate
+// to a few units in the last place however many terms they take.
+template <class T>
+__device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
+  const T y = x - c;
+  const T t = s + y;
+  c = (t - s) - y;
+  s = t;
 }
 
 template <class R>
@@ -368,7 +380,7 @@ __device__ __forceinline__ void flag_timeout(int* status) {
 template <class R, int MODE, bool MULTI>
 __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item, unsigned char* smem_raw,
                                             uint32_t& parity, double* itm, R* tms, R (&tmax)[4],
-                                            double (&tsum)[4], const R* fin_tau, const R* fin_mu, R* fout_e,
+                                            R (&tsum)[4], R (&tcmp)[4], R (&rcar)[2], const R* fin_tau, const R* fin_mu, R* fout_e,
                                             R* fout_g) {
   const int rows = c.rows_a;
   const int N1 = c.n1;
@@ -656,50 +668,56 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
     bulk_commit();
   }
   // ---------------------------------------------------------- error partials of the item
+  // Reduced in the field type (on this part FP64 runs at a small fraction of
+  // the FP32 rate) and widened to FP64 once per item (multi-cell records) or
+  // once per kernel (single cell: per-thread compensated carries).
   if (MODE == kIter) {
     // the sums only enter the average measure (eq. err_average)
     const bool want_sum = c.err_kind != 0;
+    R* redr = reinterpret_cast<R*>(red);  // [warps][8] in the field type
     if constexpr (MULTI) {
-      // per-item record: maxima reduced in the field type (exact), sums in FP64
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const R mx = shfl_max(dmax[a]);
-        const double sm = want_sum ? shfl_sum((double)dsum[a]) : 0.0;
+        const R sm = want_sum ? shfl_sum(dsum[a]) : R(0);
         if (lane == 0) {
-          red[warp * 8 + a] = (double)mx;
-          red[warp * 8 + 4 + a] = sm;
+          redr[warp * 8 + a] = mx;
+          redr[warp * 8 + 4 + a] = sm;
         }
       }
     } else {
-      // single cell: each thread carries its maxima and FP64 sums across the
-      // block's items; the block combines them once, at the end of the kernel
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         tmax[a] = max(tmax[a], dmax[a]);
-        if (want_sum) tsum[a] += (double)dsum[a];
+        if (want_sum) kahan_add(tsum[a], tcmp[a], dsum[a]);
       }
     }
-    __syncthreads();
-    const int nwarp = blockDim.x >> 5;
-    if (MULTI && threadIdx.x < 8) {
-      double a = red[threadIdx.x];
-      for (int w = 1; w < nwarp; ++w) {
-        const double vv = red[w * 8 + threadIdx.x];
-        a = (threadIdx.x < 4) ? fmax(a, vv) : a + vv;
-      }
-      itm[threadIdx.x] = a;
-    } else if (threadIdx.x >= 32 && threadIdx.x < 32 + 36) {
-      // Row sums.  With the unnormalised inverse along x, sum_x e~ = N1 X_in[0],
-      // so sum_x e = N1 (E + X_in[0]); the forward DC is sum_x tau.
-      const int q = threadIdx.x - 32;
-      double a = 0.0;
+    // Row sums.  With the unnormalised inverse along x, sum_x e~ = N1 X_in[0],
+    // so sum_x e = N1 (E + X_in[0]); the forward DC is sum_x tau.
+    R rsum = R(0);
+    const int q = threadIdx.x - 32;
+    if (q >= 0 && q < 36) {
       if (q < 18) {
-        const double mean = (q < 9) ? (double)c.E[q] : (double)c.G[q - 9];
-        for (int rr = 0; rr < nr; ++rr) a += (double)N1 * (mean + (double)dcin[q * rows + rr]);
+        const R mean = (q < 9) ? c.E[q] : c.G[q - 9];
+        for (int rr = 0; rr < nr; ++rr) rsum += R(N1) * (mean + dcin[q * rows + rr]);
       } else {
-        for (int rr = 0; rr < nr; ++rr) a += (double)X[rr * M * 18 + (q - 18)].x;
+        for (int rr = 0; rr < nr; ++rr) rsum += X[rr * M * 18 + (q - 18)].x;
       }
-      itm[8 + q] = a;
+      if constexpr (!MULTI) kahan_add(rcar[0], rcar[1], rsum);
+    }
+    if constexpr (MULTI) {
+      __syncthreads();
+      const int nwarp = blockDim.x >> 5;
+      if (threadIdx.x < 8) {
+        R a = redr[threadIdx.x];
+        for (int w = 1; w < nwarp; ++w) {
+          const R vv = redr[w * 8 + threadIdx.x];
+          a = (threadIdx.x < 4) ? max(a, vv) : a + vv;
+        }
+        itm[threadIdx.x] = (double)a;
+      } else if (q >= 0 && q < 36) {
+        itm[8 + q] = (double)rsum;
+      }
     }
   }
   __syncthreads();
@@ -730,13 +748,14 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
   bool failed = false;
   int* status = c0.status;
   R tmax[4] = {R(0), R(0), R(0), R(0)};
-  double tsum[4] = {0.0, 0.0, 0.0, 0.0};
+  R tsum[4] = {R(0), R(0), R(0), R(0)}, tcmp[4] = {R(0), R(0), R(0), R(0)};
+  R rcar[2] = {R(0), R(0)};  // threads 32..67: the block's row sum (and its compensation) of entry q
   for_items<R, MULTI>(c0, c0.items_a, w, cs, [&](const CellDev<R>& c, long long item) {
     if (failed) {
       flag_timeout(c.status);  // every cell with a skipped item reports the failure
       return;
     }
-    if (!pass_a_item<R, MODE, MULTI>(c, item, smem_raw, parity, itm, tms, tmax, tsum, fin_tau, fin_mu, fout_e,
+    if (!pass_a_item<R, MODE, MULTI>(c, item, smem_raw, parity, itm, tms, tmax, tsum, tcmp, rcar, fin_tau, fin_mu, fout_e,
                                      fout_g)) {
       failed = true;
       status = c.status;
@@ -746,10 +765,8 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
       if constexpr (MULTI) {
         for (int i = threadIdx.x; i < kErrPartials; i += blockDim.x)
           c.ipart[item * kErrPartials + i] = itm[i];
-      } else if (threadIdx.x >= 8 && threadIdx.x < kErrPartials) {
-        acc[threadIdx.x] += itm[threadIdx.x];  // row sums; the error terms are carried per thread
+        __syncthreads();
       }
-      __syncthreads();
     }
   });
   if (MODE == kIter && !MULTI && !failed) {
@@ -759,7 +776,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const R mx = shfl_max(tmax[a]);
-      const double sm = shfl_sum(tsum[a]);
+      const double sm = shfl_sum((double)tsum[a] - (double)tcmp[a]);
       if (lane == 0) {
         red[warp * 8 + a] = (double)mx;
         red[warp * 8 + 4 + a] = sm;
@@ -774,6 +791,8 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
       }
       acc[threadIdx.x] = a;
     }
+    const int q = threadIdx.x - 32;
+    if (q >= 0 && q < 36) acc[8 + q] = (double)rcar[0] - (double)rcar[1];
     __syncthreads();
   }
   if (threadIdx.x == 0) bulk_wait_all();

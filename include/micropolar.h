@@ -216,13 +216,21 @@ mp_status mp_rve_profile_read(const mp_rve* rve, double* ms, int64_t* launches, 
  * succeeded, else the status of the first that failed (message from
  * mp_last_error(ctx)).  Device memory for each cell is taken from the
  * context's allocator when the cell is admitted and released when it ends;
- * cells that do not fit wait until earlier ones finish. */
+ * cells that do not fit wait until earlier ones finish.
+ * An FP32 cell whose error has not fallen by 1% in 64 iterations while above
+ * its tolerance (the floor set by the rounding of its FP32 transforms) continues
+ * the increment in the increment form e^{i+1} = e^i - Gamma0 * (tau^i -
+ * tau^{i-1}), whose transforms round relative to the change of the
+ * polarization; if that sets no new low for 1024 iterations, it finishes the
+ * increment in FP64 (iters_fp64).  A prescribed iteration schedule disables
+ * both. */
 typedef struct mp_batch_stats {
   int64_t rounds;              /* rounds of the FP32 and of the FP64 engine                 */
   int64_t rounds_fp64;
   int64_t voxel_iters;         /* voxels x fixed-point iterations, all cells               */
   int64_t voxel_iters_fp64;    /* ... of them run in FP64                                  */
   int64_t escalations;         /* FP32 increments finished in FP64                         */
+  int64_t delta_switches;      /* FP32 increments continued in the increment form          */
 } mp_batch_stats;
 /* stats (may be NULL) receives the work counters of the call. */
 mp_status mp_batch_solve(mp_ctx* ctx, const mp_problem* const* problems, int32_t count,

@@ -82,7 +82,7 @@ class mp_alloc(C.Structure):
 
 class mp_batch_stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("rounds", "rounds_fp64", "voxel_iters", "voxel_iters_fp64",
-                                         "escalations")]
+                                         "escalations", "delta_switches")]
 
 
 class mp_server_opts(C.Structure):

@@ -201,16 +201,26 @@ struct Progress {
   std::vector<int> iters_steps, iters64_steps;
   int it64 = 0;             // iterations of the current increment run in FP64
   double ref_err = 0.0;     // stagnation watch (FP32): error level and iteration
-  int it_ref = 0;           //   at which it last halved
+  int it_ref = 0;           //   of its last significant new low
+  int delta = 0;            // increment form: 0 off, 1 switching on this round, 2 on
   bool escalate = false;    // FP32 iteration stagnated: finish the increment in FP64
   bool demote = false;      // FP64-finished increment committed: next one in FP32
 };
 
-// An FP32-mixed cell whose error has not halved in this many iterations while
-// still above the tolerance finishes the increment in FP64 (the FP32 fields
-// have reached their rounding floor, which for strongly heterogeneous
-// plastic cells can sit above the tolerance of the local error measure).
+// An FP32-mixed cell whose error has set no new low (a drop by kStagnationDrop)
+// in kStagnationIters iterations while still above the tolerance has met the
+// rounding floor of its FP32 transforms, which for strongly heterogeneous
+// plastic cells can sit above the tolerance of the local error measure (a
+// slowly but steadily converging cell keeps setting new lows and stays as it
+// is).  It continues in the increment form, whose transforms round relative to
+// the shrinking change of the polarization.
+// That form has no such floor above the tolerance (an increment below the
+// rounding of e leaves e unchanged and the measured change at zero), so a stall
+// there is slow convergence, which FP64 would not speed up: only a cell that
+// sets no new low for kStagnationItersDelta iterations finishes in FP64.
 constexpr int kStagnationIters = 64;
+constexpr int kStagnationItersDelta = 1024;
+constexpr double kStagnationDrop = 0.01;
 
 template <class R>
 struct Slot {
@@ -247,6 +257,7 @@ class Engine {
   int active() const { return (int)slots_.size(); }
   int64_t voxel_iters() const { return voxel_iters_; }
   int64_t rounds() const { return rounds_; }
+  int64_t delta_switches() const { return delta_switches_; }
 
   // Arena bytes the request needs.
   size_t footprint(const Request& q) const {
@@ -328,11 +339,16 @@ class Engine {
         g.state = Progress::kIter;
         g.it = 0;
         g.it64 = 0;
+        g.delta = 0;
         g.err = 2.0 * q.tol;
         g.ref_err = 0.0;
         g.it_ref = 0;
       }
-      if (g.state == Progress::kIter) l_iter.push_back(i);
+      if (g.state == Progress::kIter) {
+        c.delta_in = g.delta == 2 ? 1 : 0;
+        c.delta_out = g.delta >= 1 ? 1 : 0;
+        l_iter.push_back(i);
+      }
     }
     mp_status st = upload_and_launch(l_commit, l_init, l_start, l_iter);
     if (st != MP_OK) return fail_all(finished, st);
@@ -345,6 +361,7 @@ class Engine {
       g.err = e[0];
       g.it += 1;
       if (kFp64) g.it64 += 1;
+      if (g.delta == 1) g.delta = 2;  // this round wrote the first increment
       voxel_iters_ += q.nvox;
       const int target = q.lockstep.empty() ? -1 : q.lockstep[g.s - 1];
       mp_status out = MP_OK;
@@ -366,11 +383,18 @@ class Engine {
       if (!leave) {
         // FP32 stagnation watch (not under a prescribed iteration schedule)
         if (!kFp64 && target < 0) {
-          if (g.it_ref == 0 || g.err < 0.5 * g.ref_err) {
+          if (g.it_ref == 0 || g.err < (1.0 - kStagnationDrop) * g.ref_err) {
             g.ref_err = g.err;
             g.it_ref = g.it;
-          } else if (g.it - g.it_ref >= kStagnationIters) {
-            g.escalate = true;
+          } else if (g.it - g.it_ref >= (g.delta ? kStagnationItersDelta : kStagnationIters)) {
+            if (g.delta == 0) {
+              g.delta = 1;
+              g.ref_err = g.err;
+              g.it_ref = g.it;
+              ++delta_switches_;
+            } else {
+              g.escalate = true;
+            }
           }
         }
         continue;
@@ -571,8 +595,8 @@ class Engine {
       w.n_act = k;
       *items[f] = pre[k];
     };
-    fill(kFY, l_iter, [](const Slot<R>& s) { return s.c.n2 > 1 ? (long long)s.c.n3 * s.c.kx : 0ll; });
-    fill(kFZ, l_iter, [](const Slot<R>& s) { return (long long)s.c.n2 * s.c.kx; });
+    fill(kFY, l_iter, [](const Slot<R>& s) { return s.c.n2 > 1 ? tiles_y(s.c) : 0ll; });
+    fill(kFZ, l_iter, [](const Slot<R>& s) { return tiles_z(s.c); });
     fill(kFA, l_iter, [](const Slot<R>& s) { return s.c.items_a; });
     fill(kFS, l_start, [](const Slot<R>& s) { return s.c.items_a; });
     fill(kFV, l_commit, [](const Slot<R>& s) { return (s.c.nvox + 255) / 256; });
@@ -678,7 +702,7 @@ class Engine {
   cudaStream_t st_;
   std::vector<Slot<R>> slots_;
   size_t resident_ = 0;
-  int64_t voxel_iters_ = 0, rounds_ = 0;
+  int64_t voxel_iters_ = 0, rounds_ = 0, delta_switches_ = 0;
   void* d_meta_ = nullptr;
   void* h_meta_ = nullptr;
   double* h_err_ = nullptr;
@@ -885,6 +909,7 @@ mp_status mp_batch_solve(mp_ctx* ctx, const mp_problem* const* problems, int32_t
       stats->voxel_iters = ef.voxel_iters() + ed.voxel_iters();
       stats->voxel_iters_fp64 = ed.voxel_iters();
       stats->escalations = escalations;
+      stats->delta_switches = ef.delta_switches();
     }
     for (Request* q : pending) {
       q->status = MP_E_CUDA;

@@ -102,10 +102,36 @@ struct CellDev {
   double* avg_out;        // row of this increment's homogenized averages
   double* err_out;        // [8] error of the last iteration (err, per field, status)
   int err_kind;           // eq. err metric: 0 = local (max), 1 = average
+  // Increment form of the fixed-point iteration (pass A, iteration mode):
+  // delta_in: the transformed field is e^{i+1} - e^i (else e^{i+1} - E);
+  // delta_out: the polarization written is tau(e^i) - tau(e^{i-1}) (else tau - tau_c).
+  int delta_in, delta_out;
   double* tmean;          // [18] <t>, <m> of the last iteration (constants subtracted before transforms)
   int predict;            // commit: write the next increment's predictor
   double ratio;           // commit: (t_{n+1} - t_n) / (t_n - t_{n-1})
 };
+
+// Columns per tile of the y / z passes for a transform length n: short
+// columns are grouped so that a tile holds about 256 points (the 288 threads
+// of a block then have a butterfly or a Green-operator point each); lengths
+// without a compile-time plan take one column per tile.
+__host__ __device__ constexpr int cols_per_tile(int n) {
+  return n == 16 ? 16 : n == 24 ? 10 : n == 32 ? 8 : n == 48 ? 5 : n == 64 ? 4 : n == 128 ? 2 : 1;
+}
+// Tiles of the y pass (columns (kz, kx), length N2) and of the z pass
+// (columns (ky, kx), length N3) of a cell.
+template <class R>
+__host__ __device__ inline long long tiles_y(const CellDev<R>& c) {
+  const long long cols = (long long)c.n3 * c.kx;
+  const int cpt = cols_per_tile(c.n2);
+  return (cols + cpt - 1) / cpt;
+}
+template <class R>
+__host__ __device__ inline long long tiles_z(const CellDev<R>& c) {
+  const long long cols = (long long)c.n2 * c.kx;
+  const int cpt = cols_per_tile(c.n3);
+  return (cols + cpt - 1) / cpt;
+}
 
 // The work of one multi-cell launch: entries e = 0..n_act-1 name cells
 // (slots of `cells`); entry e owns global work items pre[e] .. pre[e+1]-1.

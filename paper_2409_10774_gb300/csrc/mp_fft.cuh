@@ -177,25 +177,26 @@ __device__ void stage_aos(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ ou
 
 // The same stage with the radix, Ns, the line length M and the twiddle stride
 // known at compile time (index arithmetic folds to shifts and constants, and
-// only the one butterfly is instantiated).
-template <class R, int DIR, int RADIX, int NS, int M, int TSTRIDE>
+// only the one butterfly is instantiated).  LN lines are interleaved point by
+// point (18 components of one column, or of several columns side by side).
+template <class R, int DIR, int RADIX, int NS, int M, int TSTRIDE, int LN = 18>
 __device__ __forceinline__ void stage_fixed(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ out, int rows,
                                             const cpx<R>* __restrict__ tw) {
   constexpr int nb = M / RADIX;
   constexpr int tstep = M / (NS * RADIX);
-  constexpr int rs = M * 18;
-  const int total = rows * nb * 18;
+  constexpr int rs = M * LN;
+  const int total = rows * nb * LN;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int c = idx % 18;
-    const int q = idx / 18;
+    const int c = idx % LN;
+    const int q = idx / LN;
     const int rr = q / nb, j = q % nb;
     const int kk = j % NS, jq = j / NS;
     const cpx<R>* src = in + rr * rs + c;
     cpx<R> v[RADIX];
-    v[0] = src[j * 18];
+    v[0] = src[j * LN];
 #pragma unroll
     for (int r = 1; r < RADIX; ++r) {
-      const cpx<R> x = src[(j + r * nb) * 18];
+      const cpx<R> x = src[(j + r * nb) * LN];
       v[r] = (NS == 1) ? x : cmul(x, twiddle<R, DIR>(tw, r * kk * tstep * TSTRIDE));
     }
     if constexpr (RADIX == 2) dft2<R, DIR>(v);
@@ -203,9 +204,9 @@ __device__ __forceinline__ void stage_fixed(const cpx<R>* __restrict__ in, cpx<R
     else if constexpr (RADIX == 4) dft4<R, DIR>(v);
     else if constexpr (RADIX == 8) dft8<R, DIR>(v);
     else dft16<R, DIR>(v);
-    cpx<R>* dst = out + rr * rs + c + (jq * NS * RADIX + kk) * 18;
+    cpx<R>* dst = out + rr * rs + c + (jq * NS * RADIX + kk) * LN;
 #pragma unroll
-    for (int r = 0; r < RADIX; ++r) dst[r * NS * 18] = v[r];
+    for (int r = 0; r < RADIX; ++r) dst[r * NS * LN] = v[r];
   }
 }
 
@@ -281,11 +282,14 @@ __device__ cpx<R>* tile_fft_x(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R
   }
 }
 
-// The y / z column transforms (one line per component, twiddle stride 1):
-// the common lengths with the host's plan (radix 16 where it saves a stage,
-// radix 3 last) unrolled at compile time, others through tile_fft.
+// The y / z column transforms (twiddle stride 1) of a tile of
+// cols_per_tile(N) columns, 18 lines each, interleaved point by point: the
+// common lengths with the host's plan (radix 16 where it saves a stage, radix
+// 3 last) unrolled at compile time, others (one column per tile) through
+// tile_fft.
 template <class R, int DIR, int N>
 __device__ __forceinline__ cpx<R>* fft_yz_fixed(cpx<R>* b0, cpx<R>* b1, const cpx<R>* tw) {
+  constexpr int L = 18 * cols_per_tile(N);
   auto sync_swap = [&]() {
     __syncthreads();
     cpx<R>* t = b0;
@@ -293,48 +297,36 @@ __device__ __forceinline__ cpx<R>* fft_yz_fixed(cpx<R>* b0, cpx<R>* b1, const cp
     b1 = t;
   };
   if constexpr (N == 256) {
-    stage_fixed<R, DIR, 16, 1, 256, 1>(b0, b1, 1, tw); sync_swap();
-    stage_fixed<R, DIR, 16, 16, 256, 1>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 16, 1, 256, 1, L>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 16, 16, 256, 1, L>(b0, b1, 1, tw); sync_swap();
   } else if constexpr (N == 128) {
-    stage_fixed<R, DIR, 16, 1, 128, 1>(b0, b1, 1, tw); sync_swap();
-    stage_fixed<R, DIR, 8, 16, 128, 1>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 16, 1, 128, 1, L>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 8, 16, 128, 1, L>(b0, b1, 1, tw); sync_swap();
   } else if constexpr (N == 64) {
-    stage_fixed<R, DIR, 8, 1, 64, 1>(b0, b1, 1, tw); sync_swap();
-    stage_fixed<R, DIR, 8, 8, 64, 1>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 8, 1, 64, 1, L>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 8, 8, 64, 1, L>(b0, b1, 1, tw); sync_swap();
   } else if constexpr (N == 48) {
-    stage_fixed<R, DIR, 16, 1, 48, 1>(b0, b1, 1, tw); sync_swap();
-    stage_fixed<R, DIR, 3, 16, 48, 1>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 16, 1, 48, 1, L>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 3, 16, 48, 1, L>(b0, b1, 1, tw); sync_swap();
   } else if constexpr (N == 32) {
-    stage_fixed<R, DIR, 8, 1, 32, 1>(b0, b1, 1, tw); sync_swap();
-    stage_fixed<R, DIR, 4, 8, 32, 1>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 8, 1, 32, 1, L>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 4, 8, 32, 1, L>(b0, b1, 1, tw); sync_swap();
   } else if constexpr (N == 24) {
-    stage_fixed<R, DIR, 8, 1, 24, 1>(b0, b1, 1, tw); sync_swap();
-    stage_fixed<R, DIR, 3, 8, 24, 1>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 8, 1, 24, 1, L>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 3, 8, 24, 1, L>(b0, b1, 1, tw); sync_swap();
   } else {
     static_assert(N == 16, "no compile-time plan for this length");
-    stage_fixed<R, DIR, 16, 1, 16, 1>(b0, b1, 1, tw); sync_swap();
+    stage_fixed<R, DIR, 16, 1, 16, 1, L>(b0, b1, 1, tw); sync_swap();
   }
   return b0;
 }
 
-// A kernel compiled for one length (NF > 0) runs only that plan; the NF = 0
-// form dispatches on the plan's length at run time.
+// NF > 0: the compile-time plan of length NF (cols_per_tile(NF) columns per
+// tile); otherwise the run-time plan p (one column per tile).
 template <class R, int DIR, int NF>
 __device__ cpx<R>* tile_fft_yz(cpx<R>* b0, cpx<R>* b1, const AxisPlan<R>& p, const cpx<R>* tw) {
-  if constexpr (NF > 0) {
-    return fft_yz_fixed<R, DIR, NF>(b0, b1, tw);
-  } else {
-    switch (p.m) {
-      case 256: return fft_yz_fixed<R, DIR, 256>(b0, b1, tw);
-      case 128: return fft_yz_fixed<R, DIR, 128>(b0, b1, tw);
-      case 64: return fft_yz_fixed<R, DIR, 64>(b0, b1, tw);
-      case 48: return fft_yz_fixed<R, DIR, 48>(b0, b1, tw);
-      case 32: return fft_yz_fixed<R, DIR, 32>(b0, b1, tw);
-      case 24: return fft_yz_fixed<R, DIR, 24>(b0, b1, tw);
-      case 16: return fft_yz_fixed<R, DIR, 16>(b0, b1, tw);
-      default: return tile_fft<R, DIR, 16>(b0, b1, 1, p, tw);
-    }
-  }
+  if constexpr (NF > 0) return fft_yz_fixed<R, DIR, NF>(b0, b1, tw);
+  else return tile_fft<R, DIR, 16>(b0, b1, 1, p, tw);
 }
 
 }  // namespace mp

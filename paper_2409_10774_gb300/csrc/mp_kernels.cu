@@ -67,17 +67,24 @@ constexpr size_t kSmemOptin = 227 * 1024;
 constexpr size_t kSmemStaticReserve = 2048;
 constexpr size_t kSmemBudget = kSmemOptin - kSmemStaticReserve;
 
-// Cooperative copy of one tile column: `n` chunks of 18 complex values, chunk
-// i at g + i * stride (complex units), into / out of a contiguous AoS tile.
-// Loads are asynchronous 16-byte copies (cp.async), so every thread keeps all
-// of its loads in flight; the caller's barrier follows cp_async_wait_all.
-template <class R, bool TO_SMEM>
-__device__ __forceinline__ void copy_column(cpx<R>* tile, cpx<R>* g, int n, long long stride) {
+// Cooperative copy of a y / z tile of CPT columns (those below ncols; col0 is
+// the first), n points each, 18 complex values per (point, column): the values
+// of point p of tile column j sit at g + cofs[j] + p * stride (complex units)
+// and in the tile at ((p CPT + j) 18).  Loads are asynchronous 16-byte copies
+// (cp.async), so every thread keeps all of its loads in flight; the caller's
+// barrier follows cp_async_wait_all.
+template <class R, bool TO_SMEM, int CPT>
+__device__ __forceinline__ void copy_tile(cpx<R>* tile, cpx<R>* g, int n, long long col0, long long ncols,
+                                          long long stride, const long long* cofs) {
   constexpr int W = 18 * (int)sizeof(cpx<R>) / 16;  // float4 per chunk
   float4* t4 = reinterpret_cast<float4*>(tile);
-  for (int i = threadIdx.x; i < n * W; i += blockDim.x) {
+  const int total = n * CPT * W;
+  const int nj = (int)(ncols - col0 < CPT ? ncols - col0 : CPT);
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
     const int row = i / W, w = i - row * W;
-    float4* g4 = reinterpret_cast<float4*>(g + row * stride) + w;
+    const int p = row / CPT, j = row - p * CPT;
+    if (j >= nj) continue;
+    float4* g4 = reinterpret_cast<float4*>(g + cofs[j] + p * stride) + w;
     if (TO_SMEM) cp_async16(t4 + i, g4);
     else *g4 = t4[i];
   }
@@ -138,71 +145,112 @@ __device__ __forceinline__ void for_items(const CellDev<R>& c0, long long n0, co
 }
 
 // ------------------------------------------------------------------ y pass
-// One tile = one (kz, kx) column: 18 lines of length N2.
+// Shared memory of a y / z tile: two tiles of 18 cols_per_tile(n) lines of n
+// points, the axis' twiddle table (n entries) and the tile's column offsets.
+template <class R>
+size_t smem_line_pass(int n) {
+  return (2ull * 18 * cols_per_tile(n) + 1) * (size_t)n * sizeof(cpx<R>) + 16 * sizeof(long long);
+}
+
+// One tile = CPT consecutive columns (kz, kx), column index kz KX + kx, each
+// 18 lines of length N2.  NF > 0: N2 = NF with its compile-time plan and
+// CPT = cols_per_tile(NF); NF < 0: any length through the run-time plan, one
+// column per tile.
 template <class R, int DIR, int NF>
 __device__ __forceinline__ void fft_y_tile(const CellDev<R>& c, long long tile, unsigned char* smem) {
+  constexpr int CPT = NF > 0 ? cols_per_tile(NF) : 1;
   cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem);
   const int N = c.n2;
-  cpx<R>* b1 = b0 + 18 * N;
-  const long long stride = (long long)c.kx * 18;
-  const int kz = (int)(tile / c.kx);
-  const int kx = (int)(tile - (long long)kz * c.kx);
-  cpx<R>* g = c.spec + ((long long)kz * N * c.kx + kx) * 18;
-  cpx<R>* tws = b1 + 18 * N;  // the axis' twiddle table, read from shared memory
+  cpx<R>* b1 = b0 + 18 * CPT * N;
+  cpx<R>* tws = b1 + 18 * CPT * N;  // the axis' twiddle table, read from shared memory
+  long long* cofs = reinterpret_cast<long long*>(tws + N);
+  const int KX = c.kx;
+  const long long stride = (long long)KX * 18;
+  const long long ncols = (long long)c.n3 * KX, col0 = tile * CPT;
+  if (threadIdx.x < CPT) {
+    const long long col = col0 + threadIdx.x, kz = col / KX;
+    cofs[threadIdx.x] = (kz * N * KX + (col - kz * KX)) * 18;
+  }
   for (int k = threadIdx.x; k < N; k += blockDim.x) tws[k] = c.py.tw[k];
-  copy_column<R, true>(b0, g, N, stride);
+  __syncthreads();
+  copy_tile<R, true, CPT>(b0, c.spec, N, col0, ncols, stride, cofs);
   __syncthreads();
   cpx<R>* r = tile_fft_yz<R, DIR, NF>(b0, b1, c.py, tws);
-  copy_column<R, false>(r, g, N, stride);
+  copy_tile<R, false, CPT>(r, c.spec, N, col0, ncols, stride, cofs);
   __syncthreads();
 }
 
+// Per-tile dispatch of the run-time-length kernels on the compile-time plans.
+template <class R, int DIR>
+__device__ __forceinline__ void fft_y_tile_any(const CellDev<R>& c, long long tile, unsigned char* smem) {
+  switch (c.n2) {
+    case 256: fft_y_tile<R, DIR, 256>(c, tile, smem); break;
+    case 128: fft_y_tile<R, DIR, 128>(c, tile, smem); break;
+    case 64: fft_y_tile<R, DIR, 64>(c, tile, smem); break;
+    case 48: fft_y_tile<R, DIR, 48>(c, tile, smem); break;
+    case 32: fft_y_tile<R, DIR, 32>(c, tile, smem); break;
+    case 24: fft_y_tile<R, DIR, 24>(c, tile, smem); break;
+    case 16: fft_y_tile<R, DIR, 16>(c, tile, smem); break;
+    default: fft_y_tile<R, DIR, -1>(c, tile, smem); break;
+  }
+}
+
 // NF > 0: compiled for one column length (its transform plan unrolled);
-// NF = 0: any length, dispatched at run time (multi-cell launches).
+// NF = 0: any length, dispatched per tile (multi-cell launches).
 template <class R, int DIR, bool MULTI, int NF>
 __global__ void __launch_bounds__(kThreadsYZ, 3) k_fft_y(CellDev<R> c0, Work<R> w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ CellDev<R> cs;
-  for_items<R, MULTI>(c0, (long long)c0.n3 * c0.kx, w, cs,
-                      [&](const CellDev<R>& c, long long t) { fft_y_tile<R, DIR, NF>(c, t, smem_raw); });
+  for_items<R, MULTI>(c0, tiles_y(c0), w, cs, [&](const CellDev<R>& c, long long t) {
+    if constexpr (NF > 0) fft_y_tile<R, DIR, NF>(c, t, smem_raw);
+    else fft_y_tile_any<R, DIR>(c, t, smem_raw);
+  });
 }
 
 // ------------------------------------------------------------------ z pass + Green
-// One tile = one (ky, kx) column: 18 lines of length N3.
+// One tile = CPT consecutive columns (ky, kx), column index ky KX + kx, each
+// 18 lines of length N3 (NF as for the y pass).
 template <class R, int NF>
 __device__ __forceinline__ void green_z_tile(const CellDev<R>& c, long long tile, unsigned char* smem) {
+  constexpr int CPT = NF > 0 ? cols_per_tile(NF) : 1;
   cpx<R>* b0 = reinterpret_cast<cpx<R>*>(smem);
   const int N = c.n3;
-  cpx<R>* b1 = b0 + 18 * N;
-  const long long stride = (long long)c.n2 * c.kx * 18;
+  cpx<R>* b1 = b0 + 18 * CPT * N;
+  cpx<R>* tws = b1 + 18 * CPT * N;  // the axis' twiddle table, read from shared memory
+  long long* cofs = reinterpret_cast<long long*>(tws + N);
+  const int KX = c.kx;
+  const long long stride = (long long)c.n2 * KX * 18;
+  const long long ncols = (long long)c.n2 * KX, col0 = tile * CPT;
   const R scale = (R)c.inv_nvox;
-  const int ky = (int)(tile / c.kx);
-  const int kx = (int)(tile - (long long)ky * c.kx);
-  cpx<R>* g = c.spec + ((long long)ky * c.kx + kx) * 18;
-  const bool ny_nyq = (c.n2 % 2 == 0) && (ky == c.n2 / 2);
-  if (ny_nyq) {  // the whole column is on the Nyquist plane of y: zero fluctuation
-    constexpr int W = 18 * (int)sizeof(cpx<R>) / 16;
-    for (int i = threadIdx.x; i < N * W; i += blockDim.x) {
-      const int row = i / W, w = i - row * W;
-      reinterpret_cast<float4*>(g + row * stride)[w] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    return;  // uniform across the block
-  }
-  cpx<R>* tws = b1 + 18 * N;  // the axis' twiddle table, read from shared memory
+  if (threadIdx.x < CPT) cofs[threadIdx.x] = (col0 + threadIdx.x) * 18;
   for (int k = threadIdx.x; k < N; k += blockDim.x) tws[k] = c.pz.tw[k];
-  copy_column<R, true>(b0, g, N, stride);
+  __syncthreads();
+  copy_tile<R, true, CPT>(b0, c.spec, N, col0, ncols, stride, cofs);
   __syncthreads();
   cpx<R>* r = tile_fft_yz<R, -1, NF>(b0, b1, c.pz, tws);
-  const R x1 = c.n1 == 1 ? R(0) : c.two_pi_over_L[0] * (R)kx;
-  const R x2 = signed_freq_scale<R>(ky, c.n2, c.two_pi_over_L[1]);
-  for (int kz = threadIdx.x; kz < N; kz += blockDim.x) {
-    cpx<R>* pt = r + kz * 18;  // the point's 18 values, updated in shared memory
-    const bool nz_nyq = (N % 2 == 0) && (kz == N / 2);
+  const bool even_y = (c.n2 % 2 == 0);
+  const int ky0 = (int)(col0 / KX), kx0 = (int)(col0 - (long long)ky0 * KX);
+  const int nj = (int)(ncols - col0 < CPT ? ncols - col0 : CPT);
+  for (int i = threadIdx.x; i < N * CPT; i += blockDim.x) {
+    const int kz = i / CPT, j = i - kz * CPT;
+    if (j >= nj) continue;
+    // column col0 + j = (ky, kx)
+    int kx = kx0 + j, ky = ky0;
+    if (CPT > 1) {
+      const int dy = kx / KX;
+      ky += dy;
+      kx -= dy * KX;
+    }
+    cpx<R>* pt = r + i * 18;  // the point's 18 values, updated in shared memory
+    // zero fluctuation on the Nyquist planes of y and z and at k = 0
+    const bool nyq = (even_y && ky == c.n2 / 2) || ((N % 2 == 0) && (kz == N / 2));
     const bool zero = (kx == 0 && ky == 0 && kz == 0);
-    if (nz_nyq || zero) {
+    if (nyq || zero) {
 #pragma unroll
       for (int q = 0; q < 18; ++q) pt[q] = cmake<R>(R(0), R(0));
     } else {
+      const R x1 = c.n1 == 1 ? R(0) : c.two_pi_over_L[0] * (R)kx;
+      const R x2 = signed_freq_scale<R>(ky, c.n2, c.two_pi_over_L[1]);
       const R x3 = signed_freq_scale<R>(kz, N, c.two_pi_over_L[2]);
       green_point<R>(c.ref, x1, x2, x3, pt, scale);
     }
@@ -210,19 +258,37 @@ __device__ __forceinline__ void green_z_tile(const CellDev<R>& c, long long tile
   __syncthreads();
   cpx<R>* other = (r == b0) ? b1 : b0;
   cpx<R>* o = tile_fft_yz<R, +1, NF>(r, other, c.pz, tws);
-  copy_column<R, false>(o, g, N, stride);
+  copy_tile<R, false, CPT>(o, c.spec, N, col0, ncols, stride, cofs);
   __syncthreads();
 }
 
-// Two 288-thread blocks per SM: the register file is split over the SM's
-// four sub-partitions, so 18 warps allow 96 registers per thread (a few
-// spills in FP32 cost less than dropping to one block per SM).
+template <class R>
+__device__ __forceinline__ void green_z_tile_any(const CellDev<R>& c, long long tile, unsigned char* smem) {
+  switch (c.n3) {
+    case 256: green_z_tile<R, 256>(c, tile, smem); break;
+    case 128: green_z_tile<R, 128>(c, tile, smem); break;
+    case 64: green_z_tile<R, 64>(c, tile, smem); break;
+    case 48: green_z_tile<R, 48>(c, tile, smem); break;
+    case 32: green_z_tile<R, 32>(c, tile, smem); break;
+    case 24: green_z_tile<R, 24>(c, tile, smem); break;
+    case 16: green_z_tile<R, 16>(c, tile, smem); break;
+    default: green_z_tile<R, -1>(c, tile, smem); break;
+  }
+}
+
+// The register file is split over the SM's four sub-partitions: 27 warps
+// (three 288-thread blocks) allow 72 registers per thread, which the FP32
+// single-length forms fit without spills; the others run two blocks per SM
+// (18 warps, 96 registers: a few spills cost less than one block per SM).
 template <class R, bool MULTI, int NF>
-__global__ void __launch_bounds__(kThreadsYZ, 2) k_green_z(CellDev<R> c0, Work<R> w) {
+__global__ void __launch_bounds__(kThreadsYZ, (sizeof(R) == 4 && NF > 0) ? 3 : 2)
+    k_green_z(CellDev<R> c0, Work<R> w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ CellDev<R> cs;
-  for_items<R, MULTI>(c0, (long long)c0.n2 * c0.kx, w, cs,
-                      [&](const CellDev<R>& c, long long t) { green_z_tile<R, NF>(c, t, smem_raw); });
+  for_items<R, MULTI>(c0, tiles_z(c0), w, cs, [&](const CellDev<R>& c, long long t) {
+    if constexpr (NF > 0) green_z_tile<R, NF>(c, t, smem_raw);
+    else green_z_tile_any<R>(c, t, smem_raw);
+  });
 }
 
 // ------------------------------------------------------------------ x pass (pass A)
@@ -494,6 +560,7 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
       const double2 pq = pq_s[lv];
       const R fto = pv[18], fmo = pv[19];
       const R a0 = c.ref.mu + c.ref.kap, b0 = c.ref.mu - c.ref.kap;
+      const bool din = MODE == kIter && c.delta_in != 0, dout = MODE == kIter && c.delta_out != 0;
       R ft, fm, e8;
       // ---- macro level
       {
@@ -512,14 +579,21 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
             ht[q] = hv[q];
           }
         }
-        R val[9];
+        // de9: the strain change that enters the polarization, e - E (full
+        // form) or e^i - e^{i-1} (increment form)
+        R de9[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) val[q] = (MODE == kIter) ? zv[2 * q] : R(0);
+        for (int q = 0; q < 9; ++q) de9[q] = (MODE == kIter) ? zv[2 * q] : R(0);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) e[q] = (MODE == kIter) ? c.E[q] + val[q] : eo[q];
+        for (int q = 0; q < 9; ++q) e[q] = (MODE == kIter) ? (din ? eo[q] : c.E[q]) + de9[q] : eo[q];
         double pn = pq.x;
         return_macro<R>(P, e, ht, pn, t, pn, ft);
         if (MODE == kIter) {
+          if (dout) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) de9[q] = e[q] - eo[q];
+          }
+          const R trd = de9[0] + de9[4] + de9[8];
           // previous stresses rebuilt from the stored strains and scale factor
           // (t = tr/3 d + f_t dev(t_trial)), in the same operation order
           const R tre = (eo[0] + eo[4]) + eo[8];
@@ -535,28 +609,33 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
               const R d1 = e[i] - eo[i], d2 = t[i] - to;
               de += d1 * d1;
               dt += d2 * d2;
+              // full form: tau - tau_c = (t - <t>_prev) - A0 (e - E); the
+              // constants tau_c = <t>_prev - A0 E only change the k = 0 term,
+              // which the Green operator drops, and the transforms then round
+              // relative to a field of fluctuations.  Increment form:
+              // tau(e^i) - tau(e^{i-1}) = (t - t_prev) - A0 (e^i - e^{i-1}).
+              R ae = a0 * de9[i] + b0 * de9[j];
+              if (k == l) ae += c.ref.lam * trd;
+              zr[2 * i] = (t[i] - (dout ? to : tms[i])) - ae;
             }
           }
           de = sqrt(de);
           dt = sqrt(dt);
           dmax[0] = max(dmax[0], de); dmax[1] = max(dmax[1], dt);
           dsum[0] += de; dsum[1] += dt;
-        }
-        // tau - tau_c = (t - <t>_prev) - A0 (e - E): the constants tau_c =
-        // <t>_prev - A0 E only change the k = 0 term, which the Green operator
-        // drops; the transforms then round relative to a field of fluctuations
-        R de9[9];
+        } else {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) de9[q] = (MODE == kIter) ? val[q] : e[q] - c.E[q];
-        const R tre = de9[0] + de9[4] + de9[8];
+          for (int q = 0; q < 9; ++q) de9[q] = e[q] - c.E[q];
+          const R trd = de9[0] + de9[4] + de9[8];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
+          for (int k = 0; k < 3; ++k) {
 #pragma unroll
-          for (int l = 0; l < 3; ++l) {
-            const int i = 3 * k + l, j = 3 * l + k;
-            R ae = a0 * de9[i] + b0 * de9[j];
-            if (k == l) ae += c.ref.lam * tre;
-            zr[2 * i] = (t[i] - tms[i]) - ae;
+            for (int l = 0; l < 3; ++l) {
+              const int i = 3 * k + l, j = 3 * l + k;
+              R ae = a0 * de9[i] + b0 * de9[j];
+              if (k == l) ae += c.ref.lam * trd;
+              zr[2 * i] = (t[i] - tms[i]) - ae;
+            }
           }
         }
         if constexpr (sizeof(R) == 4) {
@@ -585,14 +664,19 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
             hm[q] = hv[9 + q];
           }
         }
-        R val[9];
+        R dg9[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) val[q] = (MODE == kIter) ? zv[2 * (9 + q)] : R(0);
+        for (int q = 0; q < 9; ++q) dg9[q] = (MODE == kIter) ? zv[2 * (9 + q)] : R(0);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) g[q] = (MODE == kIter) ? c.G[q] + val[q] : go[q];
+        for (int q = 0; q < 9; ++q) g[q] = (MODE == kIter) ? (din ? go[q] : c.G[q]) + dg9[q] : go[q];
         double qn = pq.y;
         return_micro<R>(P, g, hm, qn, m, qn, fm);
         if (MODE == kIter) {
+          if (dout) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) dg9[q] = g[q] - go[q];
+          }
+          const R trd = dg9[0] + dg9[4] + dg9[8];
           const R trg = (go[0] + go[4]) + go[8];
           R dg = R(0), dm = R(0);
 #pragma unroll
@@ -604,25 +688,28 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
               const R d3 = g[i] - go[i], d4 = m[i] - mo;
               dg += d3 * d3;
               dm += d4 * d4;
+              R bg = c.ref.beta * dg9[i] + c.ref.gamma * dg9[j];
+              if (k == l) bg += c.ref.alpha * trd;
+              zr[2 * (9 + i)] = (m[i] - (dout ? mo : tms[9 + i])) - bg;
             }
           }
           dg = sqrt(dg);
           dm = sqrt(dm);
           dmax[2] = max(dmax[2], dg); dmax[3] = max(dmax[3], dm);
           dsum[2] += dg; dsum[3] += dm;
-        }
-        R dg9[9];
+        } else {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) dg9[q] = (MODE == kIter) ? val[q] : g[q] - c.G[q];
-        const R trg = dg9[0] + dg9[4] + dg9[8];
+          for (int q = 0; q < 9; ++q) dg9[q] = g[q] - c.G[q];
+          const R trd = dg9[0] + dg9[4] + dg9[8];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
+          for (int k = 0; k < 3; ++k) {
 #pragma unroll
-          for (int l = 0; l < 3; ++l) {
-            const int i = 3 * k + l, j = 3 * l + k;
-            R bg = c.ref.beta * dg9[i] + c.ref.gamma * dg9[j];
-            if (k == l) bg += c.ref.alpha * trg;
-            zr[2 * (9 + i)] = (m[i] - tms[9 + i]) - bg;
+            for (int l = 0; l < 3; ++l) {
+              const int i = 3 * k + l, j = 3 * l + k;
+              R bg = c.ref.beta * dg9[i] + c.ref.gamma * dg9[j];
+              if (k == l) bg += c.ref.alpha * trd;
+              zr[2 * (9 + i)] = (m[i] - tms[9 + i]) - bg;
+            }
           }
         }
         if constexpr (sizeof(R) == 4) {
@@ -829,6 +916,9 @@ __device__ void finish_err(const CellDev<R>& c, const double* s, int err_kind, d
     // The transformed polarization was tau - tau_c = (t - T_c) - A0 (e - E) (T_c =
     // c.tmean as read by pass A), so <t> = <tau - tau_c> + T_c + A0 (<e> - E) and
     // likewise <m>; <t>, <m> then become the constants of the next iteration.
+    // In the increment form it was (t - t_prev) - A0 (e - e_prev), so the same
+    // formula holds with T_c = <t_prev> (the unrounded last mean) and
+    // <e_prev> = E.
     const double lam = c.ref.lam, mu = c.ref.mu, kap = c.ref.kap;
     const double al = c.ref.alpha, be = c.ref.beta, ga = c.ref.gamma;
     double xe[9], xg[9];
@@ -840,9 +930,10 @@ __device__ void finish_err(const CellDev<R>& c, const double* s, int err_kind, d
     for (int k = 0; k < 3; ++k)
       for (int l = 0; l < 3; ++l) {
         const int i = 3 * k + l, j = 3 * l + k;
-        mt[i] = s[26 + i] * iv + (double)(R)c.tmean[i] + (mu + kap) * xe[i] + (mu - kap) * xe[j] +
-                (k == l ? lam * tre : 0.0);
-        mm[i] = s[35 + i] * iv + (double)(R)c.tmean[9 + i] + be * xg[i] + ga * xg[j] + (k == l ? al * trg : 0.0);
+        const double tc = c.delta_out ? c.tmean[i] : (double)(R)c.tmean[i];
+        const double mc = c.delta_out ? c.tmean[9 + i] : (double)(R)c.tmean[9 + i];
+        mt[i] = s[26 + i] * iv + tc + (mu + kap) * xe[i] + (mu - kap) * xe[j] + (k == l ? lam * tre : 0.0);
+        mm[i] = s[35 + i] * iv + mc + be * xg[i] + ga * xg[j] + (k == l ? al * trg : 0.0);
       }
     for (int q = 0; q < 9; ++q) {
       c.tmean[q] = mt[q];
@@ -1158,8 +1249,6 @@ __global__ void __launch_bounds__(256) k_radial_return_points(
 }
 
 // ------------------------------------------------------------------ launchers
-template <class R>
-size_t smem_line_pass(int n) { return (2ull * 18 + 1) * (size_t)n * sizeof(cpx<R>); }  // 2 tiles + twiddles
 
 template <class R>
 size_t smem_pass_a(int n1, int rows) { return PassASmem<R>(n1, rows).total; }
@@ -1422,10 +1511,8 @@ LaunchCfg make_launch_cfg(const CellDev<R>& c, int nsm) {
   const void* fz = c.n3 == 256   ? (const void*)k_green_z<R, false, 256>
                    : c.n3 == 128 ? (const void*)k_green_z<R, false, 128>
                                  : (const void*)k_green_z<R, false, 0>;
-  L.grid_y = grid_for<R>(fy, kThreadsYZ, smem_line_pass<R>(c.n2),
-                         (long long)c.n3 * c.kx, nsm);
-  L.grid_z = grid_for<R>(fz, kThreadsYZ, smem_line_pass<R>(c.n3),
-                         (long long)c.n2 * c.kx, nsm);
+  L.grid_y = grid_for<R>(fy, kThreadsYZ, smem_line_pass<R>(c.n2), tiles_y(c), nsm);
+  L.grid_z = grid_for<R>(fz, kThreadsYZ, smem_line_pass<R>(c.n3), tiles_z(c), nsm);
   long long vb = (c.nvox + 255) / 256;
   L.grid_v = (int)(vb < 4ll * nsm ? vb : 4ll * nsm);
   return L;

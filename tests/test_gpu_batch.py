@@ -231,15 +231,18 @@ def _truncate(problem, n_steps):
 
 def test_batch_fp32_escalates_stagnating_cells(ctx):
     """A strongly plastic cell whose FP32 iteration stalls above the tolerance
-    of the local error measure finishes those increments in FP64 and
-    converges; it agrees with the plain FP64 solve to the tolerance's level and
-    is the same alone and beside another cell."""
+    of the local error measure continues those increments in the increment
+    form (and, should that stall too, in FP64) and converges; it agrees with
+    the plain FP64 solve to the tolerance's level and is the same alone and
+    beside another cell."""
     import paper_2409_10774_gb300 as M
     p = _truncate(W.workload_serving_request(0), 3)
-    r32 = M.mp_batch_solve(ctx, [p], precision=1)[0]
+    st = {}
+    r32 = M.mp_batch_solve(ctx, [p], precision=1, stats=st)[0]
     r64 = M.mp_batch_solve(ctx, [p], precision=0)[0]
     assert r32["status"] == "ok" and r64["status"] == "ok"
-    assert r32["iters_fp64"].sum() > 0
+    assert st["delta_switches"] > 0
+    assert st["escalations"] == int((r32["iters_fp64"] > 0).sum())
     assert np.all(r32["iters_fp64"] <= r32["iters"])
     assert list(r64["iters_fp64"]) == list(r64["iters"])
     assert np.all(r32["err"] <= p["tol"])

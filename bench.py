@@ -537,7 +537,7 @@ def run_serve_leg(args):
                     "statuses": {s_: status.count(s_) for s_ in set(status)}, "clocks": clocks})
     # baseline: plain FP64 single-instance solves, one by one
     service = []
-    for r in reqs[: args.fp64_sample]:
+    for r in reqs[: args.serve_fp64_sample]:
         torch.cuda.synchronize(dev)
         t1 = time.perf_counter()
         M.mp_solve(ctx, r, precision=0)
@@ -586,8 +586,9 @@ def main():
                          "serving measurements")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--fp64-sample", type=int, default=16)
-    ap.add_argument("--rates", default="1,3,10")
-    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--rates", default="0.5,2")
+    ap.add_argument("--requests", type=int, default=12)
+    ap.add_argument("--serve-fp64-sample", type=int, default=4)
     ap.add_argument("--budget-gb", type=int, default=64)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -1,0 +1,126 @@
+"""GPU parity of the length-specialised transform paths and of the 256^3 cell.
+
+* The y / z transforms of the lengths with compile-time plans (16, 24, 32,
+  48, 64, 128, 256; several columns per tile for the short ones) and the x
+  transforms of the short packed rows, through the Green-operator entry point,
+  against the FP64 oracle (tolerances as in test_gpu_parity.py).
+* Whole solves in lockstep with the oracle on thin cells whose y, z or x
+  length is 128 or 256, so that mp_solve launches the kernels compiled for
+  those lengths: the ones the 256^3 measurement times.
+* The 256^3 Voronoi cell of the measurement, in the same launch
+  configuration (FP32 fields, the paper's mean reference medium), loaded to
+  0.5 % in one increment: the mean strain equals the prescribed one, and on
+  sampled voxels the returned stresses are Algorithm 1 of the returned
+  strains, evaluated one by one by the oracle.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from parity_helpers import compare_solves as _compare_solves
+from oracle import constitutive as OC
+from oracle import fft as OF
+from oracle import solver as OS
+from oracle.green import GreenOperator, wavevectors
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2409_10774_gb300 as M
+    return M.Context(0)
+
+
+def _oracle_green(n, h, ref, tau, mu):
+    lam, mu0, kap, al, be, ga = ref
+    A0 = OC.stiffness_A(lam, mu0, kap)
+    B0 = OC.stiffness_B(al, be, ga)
+    xi, active = wavevectors(n, h)
+    e_hat, g_hat = GreenOperator(xi, active, A0, B0)(OF.fftn(tau), OF.fftn(mu))
+    return OF.ifftn(e_hat).real, OF.ifftn(g_hat).real
+
+
+@pytest.mark.parametrize("n", [(4, 24, 48), (2, 32, 64), (2, 48, 32), (2, 64, 24), (2, 128, 16),
+                               (2, 16, 128), (2, 256, 4), (2, 4, 256),
+                               # short packed x rows with compile-time plans
+                               (48, 4, 2), (24, 2, 4), (16, 2, 2), (12, 2, 2)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_green_apply_compile_time_lengths(ctx, n, precision):
+    import paper_2409_10774_gb300 as M
+    rng = np.random.default_rng(sum(n) * 131 + precision)
+    shape = (n[2], n[1], n[0], 3, 3)
+    tau = rng.standard_normal(shape)
+    mu = rng.standard_normal(shape)
+    h = 0.61
+    ref = (20.0, 12.0, 3.0, 0.7, 1.1, 1.9)
+    e_ref, g_ref = _oracle_green(n, h, ref, tau, mu)
+    dt = torch.float64 if precision == 0 else torch.float32
+    e, g = M.mp_green_apply(ctx, precision, n, h, ref, torch.as_tensor(tau, dtype=dt, device="cuda"),
+                            torch.as_tensor(mu, dtype=dt, device="cuda"))
+    e = e.cpu().numpy().astype(np.float64)
+    g = g.cpu().numpy().astype(np.float64)
+    tol = 1e-12 if precision == 0 else 2e-6
+    assert np.abs(e - e_ref).max() <= 10 * tol * np.abs(e_ref).max()
+    assert np.abs(g - g_ref).max() <= 10 * tol * np.abs(g_ref).max()
+
+
+def _thin_problem(n, seed):
+    rng = np.random.default_rng(seed)
+    phase = (rng.uniform(size=(n[2], n[1], n[0])) < 0.35).astype(np.uint16)
+    rows = [dict(W.generators._matrix_row()), dict(W.generators._matrix_row(2.0))]
+    rows[1]["elastic"] = 1
+    phases = W.phase_record(rows)
+    Ef = np.array([[0.004, 0.001, 0.0], [0.0, -0.001, 0.0], [0.0, 0.0, 0.001]])
+    Gf = np.array([[0.0, 0.001, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.002]])
+    time, E, G = W.ramp_path(1, Ef, Gf)  # one plastic increment
+    return W.generators._problem(n, phase, phases, time, E, G, 1e-9, h=1.0, ref_kind="midrange")
+
+
+@pytest.mark.parametrize("n", [(4, 4, 256), (4, 256, 4), (4, 128, 8), (2, 8, 128), (256, 4, 4)])
+def test_lockstep_solves_on_length_specialised_kernels(ctx, n):
+    import paper_2409_10774_gb300 as M
+    prob = _thin_problem(n, seed=sum(n))
+    ref = OS.solve(prob)
+    assert ref["status"] == "ok"
+    r64 = M.mp_solve(ctx, prob, precision=0, fields=True, lockstep_iters=ref["iters"])
+    assert r64["status"] == "ok"
+    _compare_solves(r64, ref, 1e-11, 1e-11, h=prob["h"])
+    r32 = M.mp_solve(ctx, prob, precision=1, fields=True, lockstep_iters=ref["iters"])
+    assert r32["status"] == "ok"
+    _compare_solves(r32, ref, 1e-6, 1e-5, h=prob["h"])
+
+
+def test_voronoi_256_sampled_return_and_mean(ctx):
+    import paper_2409_10774_gb300 as M
+    p = W.workload_voronoi(n=256, n_cells=200)
+    p = dict(p)
+    # one increment straight to the final strain of the load path: plastic
+    # at once, with a zero history
+    p["time"] = np.array([0.0, 1.0])
+    p["E"] = np.array([np.zeros((3, 3)), p["E"][-1]])
+    p["G"] = np.array([np.zeros((3, 3)), p["G"][-1]])
+    res = M.mp_solve(ctx, p, precision=1, fields=True, lockstep_iters=[6])
+    assert res["status"] == "ok"
+    assert np.isfinite(res["err"]).all()
+    E = p["E"][1]
+    np.testing.assert_allclose(res["Eavg"][0], E, rtol=0, atol=1e-6 * np.abs(E).max())
+    f = res["final"]
+    rng = np.random.default_rng(256)
+    nv = 256 ** 3
+    idx = rng.choice(nv, 4096, replace=False)
+    z, y, x = np.unravel_index(idx, (256, 256, 256))
+    e = f["e"][z, y, x]
+    g = f["g"][z, y, x]
+    pid = p["phase"][z, y, x]
+    z9 = np.zeros_like(e)
+    zs = np.zeros(len(idx))
+    t, m, pp, qq = OC.radial_return_field(e, g, z9, z9, z9, z9, zs, zs, pid, p["phases"])
+    assert pp.max() > 0.0, "the sampled voxels must include plastic ones"
+    assert np.abs(f["t"][z, y, x] - t).max() <= 2e-6 * np.abs(t).max()
+    assert np.abs(f["m"][z, y, x] - m).max() <= 2e-6 * max(np.abs(m).max(), 1e-300) + 1e-12
+    assert np.abs(f["p"][z, y, x] - pp).max() <= 2e-5 * pp.max()

@@ -320,6 +320,93 @@ __device__ __forceinline__ void x_inverse_pre(const cpx<R>* X, cpx<R>* Z, int ro
   }
 }
 
+// The inverse pre-step fused into the first (Ns = 1) Stockham stage: each
+// butterfly forms its RADIX inputs Z[j + r M / RADIX] from X (as
+// x_inverse_pre does) instead of reading them from a separate pass, which
+// saves one shared-memory pass and one barrier per item.
+template <class R, int RADIX, int M>
+__device__ __forceinline__ void stage_first_inv_packed(const cpx<R>* __restrict__ X, cpx<R>* __restrict__ out,
+                                                       int rows, const cpx<R>* __restrict__ tw) {
+  constexpr int nb = M / RADIX;
+  constexpr int rs = M * 18;
+  const int total = rows * nb * 18;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int c = idx % 18;
+    const int q = idx / 18;
+    const int rr = q / nb, j = q % nb;
+    const cpx<R>* x = X + rr * rs + c;
+    cpx<R> v[RADIX];
+#pragma unroll
+    for (int r = 0; r < RADIX; ++r) {
+      const int k = j + r * nb;
+      cpx<R> a = x[k * 18];
+      if (k == 0) a.y = R(0);
+      const cpx<R> b = (k == 0) ? cmake<R>(R(0), R(0)) : cconj(x[(M - k) * 18]);
+      cpx<R> w = tw[k];
+      w.y = -w.y;  // W_N^-k
+      v[r] = cadd(cadd(a, b), cmuli(cmul(w, csub(a, b))));
+    }
+    if constexpr (RADIX == 3) dft3<R, +1>(v);
+    else if constexpr (RADIX == 4) dft4<R, +1>(v);
+    else dft8<R, +1>(v);
+    cpx<R>* dst = out + rr * rs + c + (j * RADIX) * 18;
+#pragma unroll
+    for (int r = 0; r < RADIX; ++r) dst[r * 18] = v[r];
+  }
+}
+
+// Inverse x transform of packed rows: the spectral rows X in b0 -> the
+// packed real rows (returned: b0 or b1).  Ends with a barrier.
+template <class R>
+__device__ cpx<R>* tile_fft_x_inv_packed(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R>& p, int msh,
+                                         const cpx<R>* tw) {
+  auto sync_swap = [&]() {
+    __syncthreads();
+    cpx<R>* t = b0;
+    b0 = b1;
+    b1 = t;
+  };
+  switch (p.m) {
+    case 256:
+      stage_first_inv_packed<R, 8, 256>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, +1, 8, 8, 256, 2>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, +1, 4, 64, 256, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    case 128:
+      stage_first_inv_packed<R, 8, 128>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, +1, 4, 8, 128, 2>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, +1, 4, 32, 128, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    case 64:
+      stage_first_inv_packed<R, 8, 64>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, +1, 8, 8, 64, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    case 32:
+      stage_first_inv_packed<R, 8, 32>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, +1, 4, 8, 32, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    case 16:
+      stage_first_inv_packed<R, 4, 16>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, +1, 4, 4, 16, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    case 24:
+      stage_first_inv_packed<R, 8, 24>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, +1, 3, 8, 24, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    case 12:
+      stage_first_inv_packed<R, 4, 12>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, +1, 3, 4, 12, 2>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    case 8:
+      stage_first_inv_packed<R, 8, 8>(b0, b1, rows, tw); sync_swap();
+      return b0;
+    default:
+      x_inverse_pre<R>(b0, b1, rows, p.m, msh, tw);
+      __syncthreads();
+      return tile_fft<R, +1, 8>(b1, b0, rows, p, tw);
+  }
+}
+
 template <class R>
 __device__ __forceinline__ void x_forward_post(const cpx<R>* Z, cpx<R>* X, int rows, int M, int msh,
                                                const cpx<R>* tw) {
@@ -504,9 +591,7 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
         dcin[cc * rows + rr] = b0[rr * M * 18 + cc].x;
       }
     if (packed) {
-      x_inverse_pre<R>(b0, b1, nr, M, msh, tws);
-      __syncthreads();
-      zbuf = tile_fft_x<R, +1>(b1, b0, nr, c.px, tws);
+      zbuf = tile_fft_x_inv_packed<R>(b0, b1, nr, c.px, msh, tws);
     }
   }
   if (use_vox) {

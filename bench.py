@@ -247,7 +247,7 @@ def combine_ranks(ms, voxel_iters, world):
 def _config(args):
     return {"workload": f"voronoi{args.cells}-{args.n}^3", "n": args.n, "cells": args.cells,
             "increments": 20, "load": "E11 to 1%", "tol": 1e-6, "err": "local",
-            "ref_medium": "mean", "fields": "fp32", "scalars": "fp64",
+            "ref_medium": "mean", "fields": "fp32", "scalars": "fp64 p, q, totals",
             "l2": "no flush: the cell's device state (~5.3 GB) exceeds L2",
             "parallelism": f"replicas x{args.gpus}"}
 

@@ -19,9 +19,11 @@
  *     follow the paper's index order (eq. strains, eq. elast_constitutive_aniso).
  *   - Field arrays are voxel-major: value (v, kl) at [9 v + 3 k + l].
  *   - precision 0 = plain FP64 (fields, FFTs, Green operator, radial return);
- *     precision 1 = FP32 fields / FFTs / Green operator with the scalar part
- *     of the radial return (equivalent stresses' square roots, p, q, scale
- *     factors), the error norm reductions and the homogenized averages in FP64.
+ *     precision 1 = FP32 fields / FFTs / Green operator / radial return (the
+ *     trial equivalent stress is an FP32 quantity, so its radius, square root
+ *     and scale factor are formed in FP32 as well), with the accumulated
+ *     plastic multipliers p, q, the error norm totals and the homogenized
+ *     averages in FP64.
  *   - Status codes only; nothing throws or aborts across this boundary.  The
  *     message of the last failure is available from mp_last_error().
  *   - Host pointers are read during the call and not retained.  Output host
@@ -92,7 +94,7 @@ typedef struct mp_problem {
   int32_t max_iter;             /* per step; <= 0 means 10000                             */
   int32_t ref_kind;             /* MP_REF_*                                               */
   const double* ref_moduli;     /* 6 values when ref_kind == MP_REF_EXPLICIT             */
-  int32_t precision;            /* 0 = FP64, 1 = FP32 fields with FP64 scalars            */
+  int32_t precision;            /* 0 = FP64, 1 = FP32 fields with FP64 p, q and totals    */
   const int32_t* lockstep_iters;/* optional host n_steps: run exactly these iterations    */
   double div_limit;             /* err above this => MP_E_DIVERGED; <= 0 means 1e6        */
 } mp_problem;

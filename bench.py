@@ -204,7 +204,7 @@ def _oracle_subprocess(args):
 
 def cpu_baseline_block():
     value, iters, secs = _oracle_subprocess({"budget_s": 15.0})
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": f"FP64 numpy oracle, {iters} fixed-point iterations ({secs:.1f} s) of the first "
                       f"load increment of the {ORACLE_N}^3 regeneration of the Voronoi cell "
                       f"(same seeds scaled by 1/4), after 1 untimed iteration"}
@@ -218,7 +218,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(iters, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config(args),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+                             "kind": "oracle",
                              "sample": f"each step = one FP64 oracle fixed-point iteration of the first "
                                        f"load increment of the {ORACLE_N}^3 regeneration of the Voronoi "
                                        f"cell; {args.warmup} untimed, {iters} timed"},
@@ -276,20 +277,25 @@ def run_ours(args, rank, world, local_rank):
     rve = M.Rve(ctx, prob, precision=1, stream=stream)
 
     def advance(k):
-        done = 0
+        """Run k load increments (wrapping around the 20-increment path) and
+        return the fixed-point iterations they took, counted per increment:
+        a reset zeroes the cell's own running total."""
+        done, iters = 0, 0
         while done < k:
             if rve.steps_done >= n_steps:
                 rve.reset(stream=stream)  # wrap around the 20-increment path
+            before = rve.iterations
             st = rve.run(1, stream=stream)
             if st != 0:
                 raise RuntimeError(f"increment failed: {M.binding.last_error(ctx.ptr)}")
+            iters += rve.iterations - before
             done += 1
+        return iters
 
     advance(args.warmup)
     torch.cuda.synchronize(dev)
     rve.profile(True)
     rve.profile_read(reset=True)
-    it0 = rve.iterations
     sampler = ClockSampler(local_rank)
     sampler.start()
     if world > 1:
@@ -298,15 +304,17 @@ def run_ours(args, rank, world, local_rank):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    advance(args.steps)
+    iters = advance(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
-    iters = rve.iterations - it0
     prof = rve.profile_read(reset=True)
+    if iters <= 0 or prof["pass_a"][1] != iters:
+        raise RuntimeError(f"timed iteration count {iters} disagrees with the pass-A launches "
+                           f"{prof['pass_a'][1]}")
     rve.profile(False)
     rve.close()
 
@@ -342,6 +350,7 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         v64 = (r64.iterations - i0) * nvox / (e0.elapsed_time(e1) / 1e3)
+        res64 = r64.results(fields=False, stream=stream)
         r64.close()
         fp64 = {"value": v64, "unit": UNIT, "increments": k64,
                 "note": f"plain FP64 GPU solver, increments {args.warmup + 1}..{args.warmup + k64}"}
@@ -359,6 +368,7 @@ def run_ours(args, rank, world, local_rank):
         k_e2e = min(args.steps, n_steps)
         r.run(k_e2e, stream=stream)
         res = r.results(fields=False, stream=stream)                  # D2H: homogenized results
+        res32 = res
         iters_e2e = r.iterations
         r.close()
         torch.cuda.synchronize(dev)
@@ -369,6 +379,24 @@ def run_ours(args, rank, world, local_rank):
                "d2h_bytes_per_step": d2h // k_e2e,
                "note": f"Rve create (uploads) + {k_e2e} increments from the zero state + results + destroy; "
                        f"T11 after increment {k_e2e}: {res['T'][-1][0, 0]:.6e}"}
+
+    # ---------------- FP32-mixed error against the plain FP64 GPU solver, per result
+    fp32_err = None
+    if fp64 is not None and e2e is not None:
+        k = min(res64["steps_done"], res32["steps_done"])
+
+        def rel(key, partner=None):
+            a, b = np.asarray(res32[key][:k]), np.asarray(res64[key][:k])
+            d = np.abs(a - b).reshape(k, -1).max(axis=1)
+            sc = np.abs(b).reshape(k, -1).max(axis=1)
+            return [float(x) for x in d / np.maximum(sc, 1e-300)]
+
+        fp32_err = {"increments": list(range(1, k + 1)),
+                    "note": "relative difference of the FP32-mixed results (same cell, same load path, "
+                            "from the zero state) to the plain FP64 GPU solver's, per increment; "
+                            "the FP32 fields against the FP64 oracle are checked by the -m gpu tests",
+                    **{f"{key}_rel": rel(key) for key in ("T", "Eavg", "P", "Teq")}}
+        fp32_err["max_T_rel"] = max(fp32_err["T_rel"])
 
     if rank != 0:
         return 0
@@ -386,11 +414,57 @@ def run_ours(args, rank, world, local_rank):
         "kernels": kernels,
         "fp64_gpu": fp64,
         "speedup_vs_fp64_gpu": (value / world / fp64["value"]) if fp64 else None,
+        "fp32_vs_fp64_gpu": fp32_err,
         "clocks": clocks,
         "cpu_baseline": cpu_block,
     }
+    if not args.no_cufft:
+        line["cufft"] = cufft_comparison(n)
+        line["cufft"]["ours_y_ms"] = kernels["fft_y_fwd"]["ms_per_launch"]
+        line["cufft"]["ours_green_z_ms"] = kernels["green_z"]["ms_per_launch"]
+    if world == 1 and not args.no_batch:
+        line["batch"] = batch_measure(args)
+    if world == 1 and not args.no_serve:
+        line["serve"] = serve_measure(args)
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------- library FFT comparison
+
+def cufft_comparison(n, reps=10):
+    """Timed comparison only (never on the product path): cuFFT (through
+    torch.fft) on a spectrum of the solver's shape, complex64
+    [N3][N2][N1/2][18], transformed along y (one direction) and along z
+    (forward then inverse, the z pass's two transforms without the Green
+    operator).  Each transform reads and writes the whole spectrum once."""
+    import torch
+    kx = max(n[0] // 2, 1)
+    x = torch.randn((n[2], n[1], kx, 18), dtype=torch.complex64, device="cuda")
+    nbytes = 2 * x.numel() * x.element_size()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    y_ms = timed(lambda: torch.fft.fft(x, dim=1))
+    z_ms = timed(lambda: torch.fft.ifft(torch.fft.fft(x, dim=0), dim=0))
+    out = {"library": "cuFFT via torch.fft " + torch.__version__, "layout": "complex64 [N3][N2][N1/2][18]",
+           "y_one_direction_ms": y_ms, "y_gbs": nbytes / (y_ms / 1e3) / 1e9,
+           "z_forward_inverse_ms": z_ms, "z_gbs": 2 * nbytes / (z_ms / 1e3) / 1e9,
+           "note": "out-of-place library transforms with their own allocations; timed on the bench stream "
+                   "after one untimed call"}
+    del x
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------- batched and served solves
@@ -400,7 +474,7 @@ def _percentile(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
 
 
-def run_batch_leg(args):
+def batch_measure(args):
     """Batched dataset generation: `--batch-count` RVEs (default 512) of
     uneven size solved in one mp_batch_solve call (FP32 fields, tolerance
     1e-6), timed end to end (problem upload, all rounds, results download),
@@ -453,7 +527,7 @@ def run_batch_leg(args):
         # the batch's own time for the same RVEs is not separable; compare rates
         fp64 = {"solves_per_s": k / s64, "voxel_iters_per_s": vi64 / s64, "sample": k,
                 "seconds": s64, "statuses": st64}
-    line = {
+    return {
         "leg": "batch", "metric": "batched RVE solves/s", "value": len(probs) / secs, "unit": "solves/s",
         "higher_is_better": True, "seconds": secs, "voxel_iters_per_s": vox_it / secs,
         "dtype": "f32", "data": "synthetic",
@@ -468,11 +542,14 @@ def run_batch_leg(args):
         "speedup_vs_fp64_single": (len(probs) / secs) / fp64["solves_per_s"] if fp64 else None,
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+
+
+def run_batch_leg(args):
+    print(json.dumps(batch_measure(args)), flush=True)
     return 0
 
 
-def run_serve_leg(args):
+def serve_measure(args):
     """Serving: requests (RSA spheres, N in {32,64,96,128}, 5-20 increments,
     FP32, tolerance 1e-6) arrive as a Poisson process at each rate of
     `--rates`; each is submitted to one mp_server at its arrival time and
@@ -556,7 +633,7 @@ def run_serve_leg(args):
                 lat.append(free_at - a)
             base.append({"rate_per_s": rate, "p50_s": _percentile(lat, 50), "p99_s": _percentile(lat, 99),
                          "solves_per_s": m / (free_at - arrivals[0]), "requests": m})
-    line = {
+    return {
         "leg": "serve", "metric": "serving p50/p99 latency and solves/s", "unit": "s",
         "higher_is_better": False, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "requests RSA spheres r=6 vf0.3, N in {32,64,96,128}, 5-20 increments",
@@ -565,7 +642,10 @@ def run_serve_leg(args):
         "rates": out,
         "fp64_one_by_one": {"service_s": service, "queue": base},
     }
-    print(json.dumps(line), flush=True)
+
+
+def run_serve_leg(args):
+    print(json.dumps(serve_measure(args)), flush=True)
     return 0
 
 
@@ -586,9 +666,12 @@ def main():
                          "serving measurements")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--fp64-sample", type=int, default=16)
-    ap.add_argument("--rates", default="0.5,2")
-    ap.add_argument("--requests", type=int, default=12)
-    ap.add_argument("--serve-fp64-sample", type=int, default=4)
+    ap.add_argument("--rates", default="0.25")
+    ap.add_argument("--requests", type=int, default=6)
+    ap.add_argument("--serve-fp64-sample", type=int, default=2)
+    ap.add_argument("--no-cufft", action="store_true", help="leave the cuFFT timing out of the line")
+    ap.add_argument("--no-batch", action="store_true", help="leave the batch sub-object out of the line")
+    ap.add_argument("--no-serve", action="store_true", help="leave the serving sub-object out of the line")
     ap.add_argument("--budget-gb", type=int, default=64)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -329,7 +329,9 @@ mp_status mp_green_apply(mp_ctx* ctx, int32_t precision, const int32_t n[3], dou
  * device (with the context's device current); make that first call before
  * any stream capture.  Calls share the array: calls whose GPU work overlaps
  * (other streams or host threads) race on it and must be serialised by the
- * caller.  Arguments as for mp_green_apply. */
+ * caller.  Arguments as for mp_green_apply; ctx must not be NULL
+ * (MP_E_INVALID_ARG), its device is made current for the call and the
+ * caller's current device is restored before returning. */
 #define MP_STATIC_SCRATCH_BYTES (8u * 1024u * 1024u)
 mp_status mp_green_apply_static(mp_ctx* ctx, int32_t precision, const int32_t n[3], double h,
                                 const double ref_moduli[6], const void* tau, const void* mu,

@@ -443,11 +443,25 @@ def _real(precision):
     return torch.float64 if precision == 0 else torch.float32
 
 
-def _check_dev(t, dtype, shape_last=None):
+def _check_dev(specs):
+    """Device pointers of the tensors in `specs` = [(tensor, dtype, numel,
+    name), ...] after checking everything the kernels rely on: each is a
+    contiguous CUDA tensor of its dtype holding exactly `numel` elements (the
+    kernels read and write that many, so a shorter tensor would be accessed
+    out of bounds).  Sizes and dtypes of all arguments are checked before
+    their placement."""
     import torch
-    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
-        raise ValueError(f"expected a contiguous CUDA tensor of {dtype}")
-    return C.c_void_p(t.data_ptr())
+    for t, dtype, numel, name in specs:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name}: expected a torch tensor")
+        if t.numel() != numel:
+            raise ValueError(f"{name}: expected {numel} elements, got {t.numel()} (shape {tuple(t.shape)})")
+        if dtype is not None and t.dtype != dtype:
+            raise ValueError(f"{name}: expected dtype {dtype}, got {t.dtype}")
+    for t, _, _, name in specs:
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous CUDA tensor")
+    return [C.c_void_p(t.data_ptr()) for t, _, _, _ in specs]
 
 
 def mp_radial_return(ctx, precision, phase, phases, e, g, e_n, g_n, t_n, m_n, p_n, q_n, stream=None):
@@ -456,16 +470,21 @@ def mp_radial_return(ctx, precision, phase, phases, e, g, e_n, g_n, t_n, m_n, p_
     when given as torch.int16; p_n, q_n float64.  Returns (t, m, p, q)."""
     import torch
     R = _real(precision)
-    count = e.shape[0]
+    count = int(e.shape[0])
+    if not isinstance(phase, torch.Tensor) or phase.is_floating_point() or phase.element_size() != 2:
+        raise ValueError("phase: expected a 16-bit integer tensor")
+    ptrs = _check_dev([(phase, None, count, "phase")]
+                      + [(x, R, 9 * count, nm) for x, nm in ((e, "e"), (g, "g"), (e_n, "e_n"), (g_n, "g_n"),
+                                                             (t_n, "t_n"), (m_n, "m_n"))]
+                      + [(x, torch.float64, count, nm) for x, nm in ((p_n, "p_n"), (q_n, "q_n"))])
+    ph_ptr, args, pq = ptrs[0], ptrs[1:7], ptrs[7:9]
+    ph = phase_table(phases)
     t = torch.empty_like(e)
     m = torch.empty_like(g)
     p = torch.empty(count, dtype=torch.float64, device=e.device)
     q = torch.empty(count, dtype=torch.float64, device=e.device)
-    ph = phase_table(phases)
-    args = [_check_dev(x, R) for x in (e, g, e_n, g_n, t_n, m_n)]
-    st = LIB.mp_radial_return(ctx.ptr, int(precision), int(count), C.c_void_p(phase.data_ptr()),
-                              len(phases), ph, *args, _check_dev(p_n, torch.float64),
-                              _check_dev(q_n, torch.float64), C.c_void_p(t.data_ptr()),
+    st = LIB.mp_radial_return(ctx.ptr, int(precision), int(count), ph_ptr,
+                              len(phases), ph, *args, *pq, C.c_void_p(t.data_ptr()),
                               C.c_void_p(m.data_ptr()), C.c_void_p(p.data_ptr()),
                               C.c_void_p(q.data_ptr()), _stream_handle(stream))
     if st != MP_OK:
@@ -476,15 +495,16 @@ def mp_radial_return(ctx, precision, phase, phases, e, g, e_n, g_n, t_n, m_n, p_
 def mp_green_apply(ctx, precision, n, h, ref_moduli, tau, mu, stream=None):
     """Fluctuations (e~, gamma~) of the polarization fields tau, mu: device
     tensors (N3, N2, N1, 3, 3) of the precision's real type."""
-    import torch
     R = _real(precision)
+    nel = 9 * int(n[0]) * int(n[1]) * int(n[2])
+    ptau, pmu = _check_dev([(tau, R, nel, "tau"), (mu, R, nel, "mu")])
+    import torch
     e = torch.empty_like(tau)
     g = torch.empty_like(mu)
     nn = (C.c_int32 * 3)(*[int(v) for v in n])
     ref = (C.c_double * 6)(*[float(v) for v in ref_moduli])
-    st = LIB.mp_green_apply(ctx.ptr, int(precision), nn, float(h), ref, _check_dev(tau, R),
-                            _check_dev(mu, R), C.c_void_p(e.data_ptr()), C.c_void_p(g.data_ptr()),
-                            _stream_handle(stream))
+    st = LIB.mp_green_apply(ctx.ptr, int(precision), nn, float(h), ref, ptau, pmu,
+                            C.c_void_p(e.data_ptr()), C.c_void_p(g.data_ptr()), _stream_handle(stream))
     if st != MP_OK:
         raise MicropolarError(st, ctx.error())
     return e, g
@@ -496,16 +516,18 @@ def mp_green_apply_static(ctx, precision, n, h, ref_moduli, tau, mu, e_out=None,
     inside the library (its scratch is a static device array of
     MP_STATIC_SCRATCH_BYTES).  The caller passes the output tensors; when they
     are omitted this wrapper allocates them with torch before the call."""
-    import torch
     R = _real(precision)
+    nel = 9 * int(n[0]) * int(n[1]) * int(n[2])
+    import torch
     if e_out is None:
         e_out = torch.empty_like(tau)
     if g_out is None:
         g_out = torch.empty_like(mu)
+    ptau, pmu, pe, pg = _check_dev([(tau, R, nel, "tau"), (mu, R, nel, "mu"), (e_out, R, nel, "e_out"),
+                                    (g_out, R, nel, "g_out")])
     nn = (C.c_int32 * 3)(*[int(v) for v in n])
     ref = (C.c_double * 6)(*[float(v) for v in ref_moduli])
-    st = LIB.mp_green_apply_static(ctx.ptr, int(precision), nn, float(h), ref, _check_dev(tau, R),
-                                   _check_dev(mu, R), _check_dev(e_out, R), _check_dev(g_out, R),
+    st = LIB.mp_green_apply_static(ctx.ptr, int(precision), nn, float(h), ref, ptau, pmu, pe, pg,
                                    _stream_handle(stream))
     if st != MP_OK:
         raise MicropolarError(st, ctx.error())

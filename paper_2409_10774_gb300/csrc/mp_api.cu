@@ -13,9 +13,6 @@
 
 using namespace mp;
 
-// Context accessor for the static-scratch entry point (mp_static.cu); not exported.
-MP_HIDDEN int mp_ctx_device(const mp_ctx* ctx) { return ctx ? ctx->device : 0; }
-
 namespace mp {
 
 namespace {
@@ -36,8 +33,6 @@ mp_status set_error(mp_ctx* ctx, mp_status st, const char* fmt, ...) {
 const char* last_error_global() { return g_last_error.c_str(); }
 
 }  // namespace mp
-
-MP_HIDDEN void mp_ctx_set_error(mp_ctx* ctx, const char* msg) { set_error(ctx, MP_E_INVALID_ARG, "%s", msg); }
 
 namespace mp {
 
@@ -238,29 +233,6 @@ mp_status validate_problem(const mp_problem* p, std::vector<long long>* counts_o
 }
 
 // ------------------------------------------------------------------ plans and tables
-void radix_plan(int m, int* radix, int& nst, bool allow16) {
-  nst = 0;
-  int k2 = 0;
-  while (m % 2 == 0) {
-    m /= 2;
-    ++k2;
-  }
-  int k3 = 0;
-  while (m % 3 == 0) {
-    m /= 3;
-    ++k3;
-  }
-  // powers of two: as few stages as possible, radix 16 only where it saves one
-  // (the x axis, transformed inside pass A, is limited to radix 8)
-  static const int kPlan2[10][4] = {{0}, {2}, {4}, {8}, {16}, {8, 4}, {8, 8}, {16, 8}, {16, 16}, {8, 8, 8}};
-  static const int kPlan2x[10][4] = {{0}, {2}, {4}, {8}, {4, 4}, {8, 4}, {8, 8}, {8, 4, 4}, {8, 8, 4}, {8, 8, 8}};
-  static const int kLen2[10] = {0, 1, 1, 1, 1, 2, 2, 2, 2, 3};
-  static const int kLen2x[10] = {0, 1, 1, 1, 2, 2, 2, 3, 3, 3};
-  const int len = allow16 ? kLen2[k2] : kLen2x[k2];
-  for (int i = 0; i < len; ++i) radix[nst++] = allow16 ? kPlan2[k2][i] : kPlan2x[k2][i];
-  for (int i = 0; i < k3; ++i) radix[nst++] = 3;
-}
-
 template <class R>
 mp_status make_axis(mp_ctx* ctx, int n, bool packed, AxisPlan<R>& p, DevBuf& tw, cudaStream_t st,
                     std::vector<cpx<R>>& host_tw) {
@@ -272,10 +244,6 @@ mp_status make_axis(mp_ctx* ctx, int n, bool packed, AxisPlan<R>& p, DevBuf& tw,
   return MP_OK;
 }
 
-mp_status use_device(mp_ctx* ctx) {
-  MP_CK(ctx, cudaSetDevice(ctx->device));
-  return MP_OK;
-}
 
 }  // namespace mp
 
@@ -603,7 +571,7 @@ mp_status mp_rve_create(mp_ctx* ctx, const mp_problem* p, mp_rve** out, void* st
   std::vector<long long> counts;
   mp_status st = validate_problem(p, &counts, ref, msg);
   if (st != MP_OK) return set_error(ctx, st, "%s", msg.c_str());
-  if ((st = use_device(ctx)) != MP_OK) return st;
+  MP_DEVICE_SCOPE(ctx);
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   mp_rve* r = new mp_rve();
   r->ctx = ctx;
@@ -641,8 +609,8 @@ mp_status mp_rve_create(mp_ctx* ctx, const mp_problem* p, mp_rve** out, void* st
 
 mp_status mp_rve_reset(mp_rve* r, void* stream) {
   if (!r) return set_error(nullptr, MP_E_INVALID_ARG, "rve is NULL");
-  mp_status st = use_device(r->ctx);
-  if (st != MP_OK) return st;
+  MP_DEVICE_SCOPE(r->ctx);
+  mp_status st = MP_OK;
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   // the transform constants start from zero as in a fresh cell
   MP_CK(r->ctx, cudaMemsetAsync(r->tmean.ptr, 0, r->tmean.bytes, cs));
@@ -685,8 +653,8 @@ mp_status mp_checkpoint(mp_rve* r, void* host_buf, size_t* bytes, void* stream) 
     *bytes = need;
     return set_error(r->ctx, MP_E_INVALID_ARG, "checkpoint buffer too small (%zu bytes needed)", need);
   }
-  mp_status st = use_device(r->ctx);
-  if (st != MP_OK) return st;
+  MP_DEVICE_SCOPE(r->ctx);
+  mp_status st = MP_OK;
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   unsigned char* out = static_cast<unsigned char*>(host_buf);
   std::memcpy(out, &h, sizeof(h));
@@ -728,8 +696,8 @@ mp_status mp_resume(mp_rve* r, const void* host_buf, size_t bytes, void* stream)
   const size_t need = sizeof(h) + h.bytes_prev + h.bytes_hist + h.bytes_pq + h.bytes_elast + h.bytes_tmean +
                       h.bytes_rows + nst * (sizeof(double) + sizeof(int32_t));
   if (bytes < need) return set_error(r->ctx, MP_E_INVALID_ARG, "checkpoint truncated");
-  mp_status st = use_device(r->ctx);
-  if (st != MP_OK) return st;
+  MP_DEVICE_SCOPE(r->ctx);
+  mp_status st = MP_OK;
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   const unsigned char* in = static_cast<const unsigned char*>(host_buf);
   size_t o = sizeof(h);
@@ -761,8 +729,8 @@ mp_status mp_resume(mp_rve* r, const void* host_buf, size_t bytes, void* stream)
 
 mp_status mp_rve_run(mp_rve* r, int32_t n_steps, void* stream) {
   if (!r) return set_error(nullptr, MP_E_INVALID_ARG, "rve is NULL");
-  mp_status st = use_device(r->ctx);
-  if (st != MP_OK) return st;
+  MP_DEVICE_SCOPE(r->ctx);
+  mp_status st = MP_OK;
   if (r->failed_step) return set_error(r->ctx, MP_E_INVALID_ARG, "cell failed at step %d; reset first", r->failed_step);
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   for (int k = 0; k < n_steps && r->steps_done < r->n_steps; ++k) {
@@ -777,8 +745,8 @@ int32_t mp_rve_steps_done(const mp_rve* r) { return r ? r->steps_done : 0; }
 
 mp_status mp_rve_profile(mp_rve* r, int32_t enable) {
   if (!r) return set_error(nullptr, MP_E_INVALID_ARG, "rve is NULL");
-  mp_status st = use_device(r->ctx);
-  if (st != MP_OK) return st;
+  MP_DEVICE_SCOPE(r->ctx);
+  mp_status st = MP_OK;
   if (enable && !r->ev[0]) {
     for (auto& e : r->ev) MP_CK(r->ctx, cudaEventCreate(&e));
   }
@@ -824,8 +792,8 @@ int64_t mp_rve_iterations(const mp_rve* r) { return r ? r->total_iters : 0; }
 mp_status mp_rve_results(mp_rve* r, mp_result* res, void* stream) {
   if (!r || !res) return set_error(r ? r->ctx : nullptr, MP_E_INVALID_ARG, "NULL argument");
   mp_ctx* ctx = r->ctx;
-  mp_status st = use_device(ctx);
-  if (st != MP_OK) return st;
+  MP_DEVICE_SCOPE(ctx);
+  mp_status st = MP_OK;
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   const int ns = r->steps_done;
   std::vector<double> rows((size_t)kAvgPartials * (ns > 0 ? ns : 1));
@@ -887,8 +855,12 @@ mp_status mp_rve_results(mp_rve* r, mp_result* res, void* stream) {
 
 void mp_rve_destroy(mp_rve* r) {
   if (!r) return;
-  if (r->ctx) cudaSetDevice(r->ctx->device);
-  rve_free(r);
+  if (r->ctx) {
+    DeviceScope dev(r->ctx->device);
+    rve_free(r);
+  } else {
+    rve_free(r);
+  }
   delete r;
 }
 
@@ -923,8 +895,8 @@ mp_status mp_radial_return(mp_ctx* ctx, int32_t precision, int64_t count, const 
     mp_status s = check_phase(phases[k], k, msg);
     if (s != MP_OK) return set_error(ctx, s, "%s", msg.c_str());
   }
-  mp_status st = use_device(ctx);
-  if (st != MP_OK) return st;
+  MP_DEVICE_SCOPE(ctx);
+  mp_status st = MP_OK;
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   DevBuf tab;
   if (precision == 0) {
@@ -1020,8 +992,8 @@ mp_status mp_green_apply(mp_ctx* ctx, int32_t precision, const int32_t n[3], dou
   const double* r = ref_moduli;
   if (!(r[0] + 2 * r[1] > 0) || !(r[1] > 0) || !(r[2] > 0) || !(r[5] >= 0) || !(r[3] + r[4] + r[5] >= 0))
     return set_error(ctx, MP_E_INADMISSIBLE, "reference medium not admissible for the Green operator");
-  mp_status st = use_device(ctx);
-  if (st != MP_OK) return st;
+  MP_DEVICE_SCOPE(ctx);
+  mp_status st = MP_OK;
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   return precision == 0 ? green_apply_impl<double>(ctx, n, h, ref_moduli, tau, mu, e_out, g_out, cs)
                         : green_apply_impl<float>(ctx, n, h, ref_moduli, tau, mu, e_out, g_out, cs);

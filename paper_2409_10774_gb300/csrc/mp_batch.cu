@@ -867,8 +867,8 @@ mp_status mp_batch_solve(mp_ctx* ctx, const mp_problem* const* problems, int32_t
   if (!ctx) return set_error(nullptr, MP_E_INVALID_ARG, "ctx is NULL");
   if (count < 0 || (count > 0 && !problems)) return set_error(ctx, MP_E_INVALID_ARG, "invalid problem list");
   if (count == 0) return MP_OK;
-  mp_status st = use_device(ctx);
-  if (st != MP_OK) return st;
+  MP_DEVICE_SCOPE(ctx);
+  mp_status st = MP_OK;
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
   std::vector<Request> reqs((size_t)count);
   std::deque<Request*> pending;
@@ -930,8 +930,8 @@ mp_status mp_batch_solve(mp_ctx* ctx, const mp_problem* const* problems, int32_t
 mp_status mp_server_create(mp_ctx* ctx, const mp_server_opts* opts, mp_server** out) {
   if (!ctx || !out) return set_error(nullptr, MP_E_INVALID_ARG, "NULL argument");
   *out = nullptr;
-  mp_status st = use_device(ctx);
-  if (st != MP_OK) return st;
+  MP_DEVICE_SCOPE(ctx);
+  mp_status st = MP_OK;
   size_t budget = opts ? opts->hbm_budget_bytes : 0;
   if (budget == 0) {
     size_t free_b = 0, total_b = 0;

@@ -10,6 +10,7 @@
 
 #include "../../include/micropolar.h"
 #include "mp_common.cuh"
+#include "mp_plan.cuh"
 
 #define MP_HIDDEN __attribute__((visibility("hidden")))
 
@@ -34,16 +35,40 @@ MP_HIDDEN const char* last_error_global();
 // Device memory through the context's allocator callbacks, else cudaMalloc.
 MP_HIDDEN mp_status dalloc(mp_ctx* ctx, DevBuf& b, size_t bytes);
 MP_HIDDEN void dfree(mp_ctx* ctx, DevBuf& b);
-MP_HIDDEN mp_status use_device(mp_ctx* ctx);
 // eq. energetic_bounds and the yield parameters of one phase.
 MP_HIDDEN mp_status check_phase(const mp_phase& ph, int idx, std::string& msg);
 // Full problem validation; fills the phase counts and the reference medium.
 MP_HIDDEN mp_status validate_problem(const mp_problem* p, std::vector<long long>* counts_out, double ref[6],
                                      std::string& msg);
-// Radix sequence of a complex transform of length m (allow16: radix-16 stages).
-MP_HIDDEN void radix_plan(int m, int* radix, int& nst, bool allow16);
+
+// Selects a device for the duration of an entry point and gives the caller's
+// current device back when the scope ends.
+struct DeviceScope {
+  int prev = -1;
+  bool changed = false;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) {
+      err = cudaSetDevice(dev);
+      changed = (err == cudaSuccess) && prev >= 0;
+    }
+  }
+  ~DeviceScope() {
+    if (changed) cudaSetDevice(prev);
+  }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+};
 
 }  // namespace mp
+
+// Opens a DeviceScope on the context's device (returns MP_E_CUDA on failure).
+#define MP_DEVICE_SCOPE(ctx)                                                                      \
+  ::mp::DeviceScope _mp_dev_scope((ctx)->device);                                                 \
+  if (_mp_dev_scope.err != cudaSuccess)                                                           \
+  return ::mp::set_error((ctx), MP_E_CUDA, "cudaSetDevice(%d) failed: %s", (ctx)->device,         \
+                         cudaGetErrorString(_mp_dev_scope.err))
 
 #define MP_CK(ctx, call)                                                                          \
   do {                                                                                            \
@@ -106,24 +131,6 @@ RefDev<R> ref_dev(const double ref[6]) {
   r.beta = (R)ref[4];
   r.gamma = (R)ref[5];
   return r;
-}
-
-// FFT plan of one axis and its twiddle table W_N^k = exp(-2 pi i k / N),
-// k < N, computed in FP64 (p.tw is left for the caller to point at the
-// device copy of host_tw).
-template <class R>
-void axis_tables(int n, bool packed, AxisPlan<R>& p, std::vector<cpx<R>>& host_tw) {
-  p.n = n;
-  p.m = packed ? (n > 1 ? n / 2 : 1) : n;
-  p.tstride = packed ? 2 : 1;
-  radix_plan(p.m, p.radix, p.nstages, !packed);
-  host_tw.resize(n);
-  for (int k = 0; k < n; ++k) {
-    const double a = 2.0 * M_PI * (double)k / (double)n;
-    host_tw[k].x = (R)std::cos(a);
-    host_tw[k].y = (R)(-std::sin(a));
-  }
-  p.tw = nullptr;
 }
 
 }  // namespace mp

@@ -15,7 +15,9 @@
 // The array's name is only a host-side stand-in in host code; its device
 // address is looked up with cudaGetSymbolAddress once per device, with that
 // device current, on the first call made on the device (make that first
-// call before any stream capture).  All calls share the array and it keeps
+// call before any stream capture).  A context is required (as for
+// mp_green_apply): its device is made current for the call and the caller's
+// current device is restored on return.  All calls share the array and it keeps
 // the last call's contents: the status word is cleared on every call, and
 // the spectrum is fully overwritten by the forward transform before it is
 // read.  Calls whose work overlaps on the GPU (other streams, other host
@@ -24,13 +26,10 @@
 #include <mutex>
 
 #include "../../include/micropolar.h"
+#include "mp_host.cuh"
 #include "mp_kernels.cuh"
 
 using namespace mp;
-
-// Context accessors (defined with mp_ctx in mp_api.cu; not exported).
-__attribute__((visibility("hidden"))) int mp_ctx_device(const mp_ctx* ctx);
-__attribute__((visibility("hidden"))) void mp_ctx_set_error(mp_ctx* ctx, const char* msg);
 
 namespace {
 
@@ -43,23 +42,20 @@ static __device__ __align__(256) unsigned char g_static_scratch[MP_STATIC_SCRATC
 std::mutex g_setup_mutex;
 void* g_scratch_ptr[64] = {nullptr};
 
-mp_status fail(mp_ctx* ctx, mp_status st, const char* msg) {
-  mp_ctx_set_error(ctx, msg);
-  return st;
-}
+mp_status fail(mp_ctx* ctx, mp_status st, const char* msg) { return set_error(ctx, st, "%s", msg); }
 
-// Device address of the scratch array for the current device (set-up on the
-// first call made on that device).
-mp_status scratch_for_current_device(void** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
-    return fail(nullptr, MP_E_NO_DEVICE, "mp_green_apply_static: no current CUDA device");
+// Device address of the scratch array for the context's device, which the
+// caller has made current (set-up on the first call made on that device).
+mp_status scratch_for_device(mp_ctx* ctx, void** out) {
+  const int dev = ctx->device;
+  if (dev < 0 || dev >= 64) return fail(ctx, MP_E_NO_DEVICE, "mp_green_apply_static: device index out of range");
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess || !p)
-      return fail(nullptr, MP_E_CUDA, "mp_green_apply_static: cudaGetSymbolAddress failed");
+      return set_error(ctx, MP_E_CUDA, "mp_green_apply_static: cudaGetSymbolAddress failed: %s",
+                       cudaGetErrorString(e));
     g_scratch_ptr[dev] = p;
   }
   *out = g_scratch_ptr[dev];
@@ -74,27 +70,11 @@ bool axis_ok(int n) {
   return n == 1;
 }
 
-void radices(int m, int* radix, int& nst, bool allow16) {
-  nst = 0;
-  int k2 = 0, k3 = 0;
-  while (m % 2 == 0) { m /= 2; ++k2; }
-  while (m % 3 == 0) { m /= 3; ++k3; }
-  // powers of two: as few stages as possible, radix 16 only where it saves one
-  // (the x axis, transformed inside pass A, is limited to radix 8)
-  static const int kPlan2[10][4] = {{0}, {2}, {4}, {8}, {16}, {8, 4}, {8, 8}, {16, 8}, {16, 16}, {8, 8, 8}};
-  static const int kPlan2x[10][4] = {{0}, {2}, {4}, {8}, {4, 4}, {8, 4}, {8, 8}, {8, 4, 4}, {8, 8, 4}, {8, 8, 8}};
-  static const int kLen2[10] = {0, 1, 1, 1, 1, 2, 2, 2, 2, 3};
-  static const int kLen2x[10] = {0, 1, 1, 1, 2, 2, 2, 3, 3, 3};
-  const int len = allow16 ? kLen2[k2] : kLen2x[k2];
-  for (int i = 0; i < len; ++i) radix[nst++] = allow16 ? kPlan2[k2][i] : kPlan2x[k2][i];
-  for (int i = 0; i < k3; ++i) radix[nst++] = 3;
-}
-
 template <class R>
 mp_status run(mp_ctx* ctx, const int32_t n[3], double h, const double ref[6], const void* tau,
               const void* mu, void* e_out, void* g_out, cudaStream_t st) {
   void* base = nullptr;
-  mp_status s = scratch_for_current_device(&base);
+  mp_status s = scratch_for_device(ctx, &base);
   if (s != MP_OK) return s;
   unsigned char* b = static_cast<unsigned char*>(base);
   int* status = reinterpret_cast<int*>(b);
@@ -127,32 +107,17 @@ mp_status run(mp_ctx* ctx, const int32_t n[3], double h, const double ref[6], co
   // twiddle tables W_N^k = exp(-2 pi i k / N), built on the host stack and copied in
   static thread_local cpx<R> host_tw[3][kMaxAxis];
   for (int a = 0; a < 3; ++a) {
-    AxisPlan<R>& p = *plans[a];
-    const bool packed = (a == 0);
-    p.n = n[a];
-    p.m = packed ? (n[a] > 1 ? n[a] / 2 : 1) : n[a];
-    p.tstride = packed ? 2 : 1;
-    radices(p.m, p.radix, p.nstages, !packed);
-    for (int k = 0; k < n[a]; ++k) {
-      const double ang = 2.0 * M_PI * (double)k / (double)n[a];
-      host_tw[a][k].x = (R)std::cos(ang);
-      host_tw[a][k].y = (R)(-std::sin(ang));
-    }
-    p.tw = tw[a];
+    axis_plan<R>(n[a], a == 0, *plans[a], host_tw[a]);  // the plans every entry point uses
+    plans[a]->tw = tw[a];
   }
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
   for (int a = 0; a < 3 && e == cudaSuccess; ++a)
     e = cudaMemcpyAsync(tw[a], host_tw[a], sizeof(cpx<R>) * n[a], cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
-    int dev = 0, nsm = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) {
-      LaunchCfg L = make_launch_cfg<R>(c, nsm > 0 ? nsm : 1);
-      c.rows_a = L.rows;
-      c.items_a = L.items_a;
-      e = launch_green_apply<R>(L, c, (const R*)tau, (const R*)mu, (R*)e_out, (R*)g_out, st);
-    }
+    LaunchCfg L = make_launch_cfg<R>(c, ctx->nsm > 0 ? ctx->nsm : 1);
+    c.rows_a = L.rows;
+    c.items_a = L.items_a;
+    e = launch_green_apply<R>(L, c, (const R*)tau, (const R*)mu, (R*)e_out, (R*)g_out, st);
   }
   int flag = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, status, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -169,6 +134,7 @@ extern "C" {
 mp_status mp_green_apply_static(mp_ctx* ctx, int32_t precision, const int32_t n[3], double h,
                                 const double ref_moduli[6], const void* tau, const void* mu,
                                 void* e_out, void* g_out, void* stream) {
+  if (!ctx) return set_error(nullptr, MP_E_INVALID_ARG, "mp_green_apply_static: ctx is NULL");
   if (!n || !ref_moduli || !tau || !mu || !e_out || !g_out || (precision != 0 && precision != 1))
     return fail(ctx, MP_E_INVALID_ARG, "mp_green_apply_static: invalid arguments");
   for (int j = 0; j < 3; ++j)
@@ -180,8 +146,7 @@ mp_status mp_green_apply_static(mp_ctx* ctx, int32_t precision, const int32_t n[
     return fail(ctx, MP_E_INADMISSIBLE, "mp_green_apply_static: reference medium not admissible");
   if (!(precision == 0 ? sizes_fit<double>(n[0], n[1], n[2]) : sizes_fit<float>(n[0], n[1], n[2])))
     return fail(ctx, MP_E_UNSUPPORTED_SIZE, "mp_green_apply_static: grid too large for the tiles");
-  if (ctx && cudaSetDevice(mp_ctx_device(ctx)) != cudaSuccess)
-    return fail(ctx, MP_E_NO_DEVICE, "mp_green_apply_static: cannot select the context's device");
+  MP_DEVICE_SCOPE(ctx);  // the context's device, the caller's given back on return
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   return precision == 0 ? run<double>(ctx, n, h, ref_moduli, tau, mu, e_out, g_out, st)
                         : run<float>(ctx, n, h, ref_moduli, tau, mu, e_out, g_out, st);

@@ -66,9 +66,27 @@ def test_static_matches_allocating_entry_point_twice(ctx, precision, n):
 
 def test_static_rejects_grids_beyond_the_array(ctx):
     from paper_2409_10774_gb300 import binding as B
-    n = (64, 64, 64)  # FP32 half spectrum of 64^3 needs 37.7 MB of scratch
+    n = (64, 64, 64)  # FP32 half spectrum of 64^3: 32*64*64 points x 18 x 8 bytes = 18.9 MB
     tau = torch.zeros((64, 64, 64, 3, 3), dtype=torch.float32, device="cuda")
     with pytest.raises(B.MicropolarError) as ei:
         B.mp_green_apply_static(ctx, 1, n, 1.0, REF, tau, tau.clone())
     assert ei.value.status == 3
     assert "static scratch" in str(ei.value)
+
+
+def test_static_requires_a_context_and_keeps_the_callers_device(ctx):
+    """A NULL context is refused like mp_green_apply's; a valid call leaves
+    the caller's current device as it found it."""
+    import ctypes as C
+    from paper_2409_10774_gb300 import binding as B
+    n = (8, 8, 8)
+    tau = torch.zeros((8, 8, 8, 3, 3), dtype=torch.float32, device="cuda")
+    out = torch.empty_like(tau)
+    nn = (C.c_int32 * 3)(*n)
+    ref = (C.c_double * 6)(*REF)
+    p = lambda t: C.c_void_p(t.data_ptr())
+    st = B.LIB.mp_green_apply_static(None, 1, nn, 1.0, ref, p(tau), p(tau), p(out), p(out), None)
+    assert st == 1
+    before = torch.cuda.current_device()
+    B.mp_green_apply_static(ctx, 1, n, 1.0, REF, tau, tau.clone())
+    assert torch.cuda.current_device() == before

@@ -35,7 +35,7 @@ if ROOT not in sys.path:
 METRIC = "voxel-iters/s at 256^3 and batched RVE solves/s vs plain FP64; serving p50/p99"
 UNIT = "voxel-iters/s"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_CLASSES = ("fft_y_fwd", "green_z", "fft_y_inv", "pass_a", "reduce", "start", "commit")
+KERNEL_CLASSES = ("fft_y_fwd", "green_z", "fft_y_inv", "pass_a", "reduce", "start", "commit", "spectral")
 
 
 # ---------------------------------------------------------------- algorithmic bytes
@@ -54,6 +54,7 @@ def algorithmic_bytes(n, precision=1):
         "fft_y_fwd": 2 * spec,
         "green_z": 2 * spec,
         "fft_y_inv": 2 * spec,
+        "spectral": 2 * spec,
         "pass_a": 2 * spec + nvox * (2 * 20 * r + 20 * r + 16),
     }
 

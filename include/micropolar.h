@@ -18,12 +18,19 @@
  *     k, l = 0..2 standing for the paper's 1..3.  e_kl, gamma_kl, t_kl, m_kl
  *     follow the paper's index order (eq. strains, eq. elast_constitutive_aniso).
  *   - Field arrays are voxel-major: value (v, kl) at [9 v + 3 k + l].
- *   - precision 0 = plain FP64 (fields, FFTs, Green operator, radial return);
- *     precision 1 = FP32 fields / FFTs / Green operator / radial return (the
- *     trial equivalent stress is an FP32 quantity, so its radius, square root
- *     and scale factor are formed in FP32 as well), with the accumulated
- *     plastic multipliers p, q, the error norm totals and the homogenized
- *     averages in FP64.
+ *   - precision (MP_PRECISION_*):
+ *     0 = plain FP64: fields, FFTs, Green operator, radial return;
+ *     1 = FP32 fields, FFTs, Green operator and trial stresses, with the scalar
+ *         solve of the radial return (radius, equivalent stress, plastic
+ *         multiplier of eq. trial_stresses2, scale factor) in FP64, the
+ *         accumulated plastic strains p, q in FP64, the error measure's sums,
+ *         means and ratios (eq. err) in FP64 (the per-voxel norms of FP32
+ *         field differences are FP32 quantities and their maxima are exact),
+ *         and the homogenized averages summed in FP64;
+ *     2 = as 1, but the level return's radius, square root, multiplier
+ *         increment and scale factor are formed in FP32 (the trial
+ *         equivalent stress is itself an FP32 quantity); p, q and every sum
+ *         stay FP64.
  *   - Status codes only; nothing throws or aborts across this boundary.  The
  *     message of the last failure is available from mp_last_error().
  *   - Host pointers are read during the call and not retained.  Output host
@@ -41,7 +48,7 @@
 extern "C" {
 #endif
 
-#define MP_ABI_VERSION 1
+#define MP_ABI_VERSION 2
 
 typedef enum mp_status {
   MP_OK = 0,
@@ -77,6 +84,10 @@ typedef struct mp_phase {
 #define MP_REF_MEAN 0
 #define MP_REF_MIDRANGE 1
 #define MP_REF_EXPLICIT 2
+/* Arithmetic of a solve (see the conventions above). */
+#define MP_PRECISION_FP64 0
+#define MP_PRECISION_MIXED 1
+#define MP_PRECISION_FP32_RETURN 2
 
 /* The cell problem (Algorithm 2 inputs). */
 typedef struct mp_problem {
@@ -94,7 +105,7 @@ typedef struct mp_problem {
   int32_t max_iter;             /* per step; <= 0 means 10000                             */
   int32_t ref_kind;             /* MP_REF_*                                               */
   const double* ref_moduli;     /* 6 values when ref_kind == MP_REF_EXPLICIT             */
-  int32_t precision;            /* 0 = FP64, 1 = FP32 fields with FP64 p, q and totals    */
+  int32_t precision;            /* MP_PRECISION_*: 0 FP64, 1 FP32 fields + FP64 scalars, 2 */
   const int32_t* lockstep_iters;/* optional host n_steps: run exactly these iterations    */
   double div_limit;             /* err above this => MP_E_DIVERGED; <= 0 means 1e6        */
 } mp_problem;
@@ -192,13 +203,16 @@ mp_status mp_resume(mp_rve* rve, const void* host_buf, size_t bytes, void* strea
 #define MP_KC_REDUCE 4    /* iteration error reduction                                   */
 #define MP_KC_START 5     /* increment start: initial state, predictor pass              */
 #define MP_KC_COMMIT 6    /* commit of a converged increment and homogenized averages    */
-#define MP_KC_COUNT 7
+#define MP_KC_SPECTRAL 7  /* fused pass: y fwd, z fwd, Green operator, z inv, y inv       */
+#define MP_KC_COUNT 8
 
-/* Enable / disable per-kernel CUDA-event timing of mp_rve_run's fixed-point
+/* Cells whose y and z lengths are 256 (FP32 fields) run classes 0-2 as the
+ * one fused launch of class 7; other cells run classes 0-2.
+ * Enable / disable per-kernel CUDA-event timing of mp_rve_run's fixed-point
  * loop (events recorded on the run's stream around every launch of classes
- * 0-4).  Launch counts are kept for every class regardless. */
+ * 0-4 and 7).  Launch counts are kept for every class regardless. */
 mp_status mp_rve_profile(mp_rve* rve, int32_t enable);
-/* Accumulated milliseconds (classes 0-4, while enabled) and launch counts
+/* Accumulated milliseconds (classes 0-4 and 7, while enabled) and launch counts
  * per class, MP_KC_COUNT entries each (either pointer may be NULL);
  * reset != 0 zeroes both afterwards. */
 mp_status mp_rve_profile_read(const mp_rve* rve, double* ms, int64_t* launches, int32_t reset);
@@ -284,7 +298,8 @@ mp_status mp_rve_trace(mp_rve* rve, int32_t enable);
 int64_t mp_rve_trace_read(mp_rve* rve, double* out, int64_t capacity, int32_t clear);
 
 /* Hot-path components on device buffers -----------------------------------
- * Real type of tensor buffers: double for precision 0, float for 1.
+ * Real type of tensor buffers: double for precision 0, float for 1 and 2
+ * (precision 2 selects the FP32 level return in mp_radial_return).
  *
  * mp_radial_return: Algorithm 1 at `count` material points.  Inputs e, g
  * (gamma), e_n, g_n, t_n, m_n are count*9 tensors, p_n, q_n count doubles,

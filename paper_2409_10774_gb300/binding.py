@@ -34,7 +34,7 @@ EXPORTED = ("mp_abi_version", "mp_create", "mp_destroy", "mp_last_error", "mp_va
             "mp_server_create", "mp_server_submit", "mp_server_wait",
             "mp_server_query", "mp_server_destroy")
 MP_STATIC_SCRATCH_BYTES = 8 * 1024 * 1024
-KERNEL_CLASSES = ("fft_y_fwd", "green_z", "fft_y_inv", "pass_a", "reduce", "start", "commit")
+KERNEL_CLASSES = ("fft_y_fwd", "green_z", "fft_y_inv", "pass_a", "reduce", "start", "commit", "spectral")
 
 
 class MicropolarError(RuntimeError):

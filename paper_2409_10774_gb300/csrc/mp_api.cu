@@ -201,8 +201,8 @@ mp_status validate_problem(const mp_problem* p, std::vector<long long>* counts_o
     msg = "ref_kind must be 0, 1 or 2";
     return MP_E_INVALID_ARG;
   }
-  if (p->precision != 0 && p->precision != 1) {
-    msg = "precision must be 0 or 1";
+  if (p->precision < 0 || p->precision > 2) {
+    msg = "precision must be 0, 1 or 2";
     return MP_E_INVALID_ARG;
   }
   if (!(p->precision == 0 ? sizes_fit<double>(p->n[0], p->n[1], p->n[2])
@@ -262,7 +262,7 @@ struct mp_rve {
   double div_limit = 1e6;
   double ref[6] = {0, 0, 0, 0, 0, 0};
   DevBuf spec, prev, hist, pq, elast, phase, phases, twx, twy, twz, partials, avgpart, errout, steprows,
-      status, tmean;
+      status, tmean, ctl;
   CellDev<float> cf{};
   CellDev<double> cd{};
   LaunchCfg L;
@@ -332,7 +332,7 @@ mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
   MP_CK(ctx, cudaMemsetAsync(r->tmean.ptr, 0, r->tmean.bytes, st));
   c.ref = ref_dev<R>(r->ref);
   std::vector<PhaseDev<R>> ph(p->n_phases);
-  for (int k = 0; k < p->n_phases; ++k) ph[k] = phase_dev<R>(p->phases[k]);
+  for (int k = 0; k < p->n_phases; ++k) ph[k] = phase_dev<R>(p->phases[k], p->precision == 2);
   std::vector<cpx<R>> t1, t2, t3;
   if ((s = make_axis<R>(ctx, c.n1, true, c.px, r->twx, st, t1)) != MP_OK) return s;
   if ((s = make_axis<R>(ctx, c.n2, false, c.py, r->twy, st, t2)) != MP_OK) return s;
@@ -348,6 +348,11 @@ mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
   if ((s = dalloc(ctx, r->avgpart, sizeof(double) * kAvgPartials * (size_t)r->L.grid_v)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->errout, sizeof(double) * 8)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->steprows, sizeof(double) * kAvgPartials * (size_t)r->n_steps)) != MP_OK) return s;
+  if constexpr (sizeof(R) == 4) {
+    if (spectral_fused_ok(c) &&
+        (s = dalloc(ctx, r->ctl, sizeof(int) * spectral_ctl_ints(c.kx))) != MP_OK)
+      return s;
+  }
   MP_CK(ctx, cudaMemsetAsync(r->steprows.ptr, 0, r->steprows.bytes, st));
   // host tables are stack-local: finish the uploads before returning
   MP_CK(ctx, cudaStreamSynchronize(st));
@@ -386,15 +391,25 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
     auto mark = [&](int k, int end) {
       if (prof) cudaEventRecord(r->ev[2 * k + end], st);
     };
-    mark(MP_KC_FFT_Y_FWD, 0);
-    MP_CK(ctx, launch_fft_y<R>(r->L, c, -1, st));
-    mark(MP_KC_FFT_Y_FWD, 1);
-    mark(MP_KC_GREEN_Z, 0);
-    MP_CK(ctx, launch_green_z<R>(r->L, c, st));
-    mark(MP_KC_GREEN_Z, 1);
-    mark(MP_KC_FFT_Y_INV, 0);
-    MP_CK(ctx, launch_fft_y<R>(r->L, c, +1, st));
-    mark(MP_KC_FFT_Y_INV, 1);
+    bool fused = false;
+    if constexpr (sizeof(R) == 4) fused = r->ctl.ptr != nullptr;
+    if (fused) {
+      if constexpr (sizeof(R) == 4) {
+        mark(MP_KC_SPECTRAL, 0);
+        MP_CK(ctx, launch_spectral(c, reinterpret_cast<int*>(r->ctl.ptr), ctx->nsm, st));
+        mark(MP_KC_SPECTRAL, 1);
+      }
+    } else {
+      mark(MP_KC_FFT_Y_FWD, 0);
+      MP_CK(ctx, launch_fft_y<R>(r->L, c, -1, st));
+      mark(MP_KC_FFT_Y_FWD, 1);
+      mark(MP_KC_GREEN_Z, 0);
+      MP_CK(ctx, launch_green_z<R>(r->L, c, st));
+      mark(MP_KC_GREEN_Z, 1);
+      mark(MP_KC_FFT_Y_INV, 0);
+      MP_CK(ctx, launch_fft_y<R>(r->L, c, +1, st));
+      mark(MP_KC_FFT_Y_INV, 1);
+    }
     mark(MP_KC_PASS_A, 0);
     MP_CK(ctx, launch_pass_a_iter<R>(r->L, c, parts, st));
     mark(MP_KC_PASS_A, 1);
@@ -403,16 +418,22 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
     mark(MP_KC_REDUCE, 1);
     MP_CK(ctx, cudaMemcpyAsync(r->err_host, r->errout.ptr, sizeof(double) * 6, cudaMemcpyDeviceToHost, st));
     MP_CK(ctx, cudaStreamSynchronize(st));
-    if (ydo) {
-      r->launches[MP_KC_FFT_Y_FWD]++;
-      r->launches[MP_KC_FFT_Y_INV]++;
+    if (fused) {
+      r->launches[MP_KC_SPECTRAL]++;
+    } else {
+      if (ydo) {
+        r->launches[MP_KC_FFT_Y_FWD]++;
+        r->launches[MP_KC_FFT_Y_INV]++;
+      }
+      r->launches[MP_KC_GREEN_Z]++;
     }
-    r->launches[MP_KC_GREEN_Z]++;
     r->launches[MP_KC_PASS_A]++;
     r->launches[MP_KC_REDUCE]++;
     if (prof) {
-      const int ks[5] = {MP_KC_FFT_Y_FWD, MP_KC_GREEN_Z, MP_KC_FFT_Y_INV, MP_KC_PASS_A, MP_KC_REDUCE};
+      const int ks[6] = {MP_KC_FFT_Y_FWD, MP_KC_GREEN_Z, MP_KC_FFT_Y_INV, MP_KC_PASS_A, MP_KC_REDUCE,
+                         MP_KC_SPECTRAL};
       for (int k : ks) {
+        if (fused ? (k <= MP_KC_FFT_Y_INV) : (k == MP_KC_SPECTRAL)) continue;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, r->ev[2 * k], r->ev[2 * k + 1]) == cudaSuccess) r->kernel_ms[k] += ms;
       }
@@ -506,7 +527,7 @@ void rve_free(mp_rve* r) {
   mp_ctx* ctx = r->ctx;
   DevBuf* bufs[] = {&r->spec, &r->prev, &r->hist, &r->pq, &r->elast, &r->phase, &r->phases,
                     &r->twx, &r->twy, &r->twz, &r->partials, &r->avgpart, &r->errout, &r->steprows,
-                    &r->status, &r->tmean};
+                    &r->status, &r->tmean, &r->ctl};
   for (DevBuf* b : bufs) dfree(ctx, *b);
   if (r->err_host) cudaFreeHost(r->err_host);
   r->err_host = nullptr;
@@ -886,7 +907,7 @@ mp_status mp_radial_return(mp_ctx* ctx, int32_t precision, int64_t count, const 
                            const double* p_n, const double* q_n, void* t, void* m, double* p,
                            double* q, void* stream) {
   if (!ctx) return set_error(nullptr, MP_E_INVALID_ARG, "ctx is NULL");
-  if (count < 0 || n_phases < 1 || !phases || (precision != 0 && precision != 1))
+  if (count < 0 || n_phases < 1 || !phases || precision < 0 || precision > 2)
     return set_error(ctx, MP_E_INVALID_ARG, "invalid arguments");
   if (count > 0 && (!phase || !e || !g || !e_n || !g_n || !t_n || !m_n || !p_n || !q_n || !t || !m || !p || !q))
     return set_error(ctx, MP_E_INVALID_ARG, "NULL buffer");
@@ -914,7 +935,7 @@ mp_status mp_radial_return(mp_ctx* ctx, int32_t precision, int64_t count, const 
     if (e1 != cudaSuccess) return set_error(ctx, MP_E_CUDA, "radial return: %s", cudaGetErrorString(e1));
   } else {
     std::vector<PhaseDev<float>> ph(n_phases);
-    for (int k = 0; k < n_phases; ++k) ph[k] = phase_dev<float>(phases[k]);
+    for (int k = 0; k < n_phases; ++k) ph[k] = phase_dev<float>(phases[k], precision == 2);
     if ((st = dalloc(ctx, tab, sizeof(PhaseDev<float>) * n_phases)) != MP_OK) return st;
     cudaError_t e1 = cudaMemcpyAsync(tab.ptr, ph.data(), tab.bytes, cudaMemcpyHostToDevice, cs);
     if (e1 == cudaSuccess)
@@ -946,7 +967,7 @@ mp_status green_apply_impl(mp_ctx* ctx, const int32_t n[3], double h, const doub
   c.inv_nvox = 1.0 / (double)c.nvox;
   for (int j = 0; j < 3; ++j) c.two_pi_over_L[j] = (R)(2.0 * M_PI / ((double)n[j] * h));
   c.ref = ref_dev<R>(ref);
-  DevBuf spec, tx, ty, tz, stat;
+  DevBuf spec, tx, ty, tz, stat, ctl;
   std::vector<cpx<R>> h1, h2, h3;
   mp_status st = dalloc(ctx, spec, sizeof(cpx<R>) * 18 * (size_t)c.nspec);
   if (st == MP_OK) st = dalloc(ctx, stat, sizeof(int) * 4);
@@ -956,12 +977,16 @@ mp_status green_apply_impl(mp_ctx* ctx, const int32_t n[3], double h, const doub
   if (st == MP_OK) st = make_axis<R>(ctx, c.n1, true, c.px, tx, cs, h1);
   if (st == MP_OK) st = make_axis<R>(ctx, c.n2, false, c.py, ty, cs, h2);
   if (st == MP_OK) st = make_axis<R>(ctx, c.n3, false, c.pz, tz, cs, h3);
+  if constexpr (sizeof(R) == 4) {
+    if (st == MP_OK && spectral_fused_ok(c)) st = dalloc(ctx, ctl, sizeof(int) * spectral_ctl_ints(c.kx));
+  }
   if (st == MP_OK) {
     c.spec = reinterpret_cast<cpx<R>*>(spec.ptr);
     LaunchCfg L = make_launch_cfg<R>(c, ctx->nsm);
     c.rows_a = L.rows;
     c.items_a = L.items_a;
-    cudaError_t e = launch_green_apply<R>(L, c, (const R*)tau, (const R*)mu, (R*)e_out, (R*)g_out, cs);
+    cudaError_t e = launch_green_apply<R>(L, c, (const R*)tau, (const R*)mu, (R*)e_out, (R*)g_out, cs,
+                                          reinterpret_cast<int*>(ctl.ptr), ctx->nsm);
     int flag = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, stat.ptr, sizeof(int), cudaMemcpyDeviceToHost, cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
@@ -974,6 +999,7 @@ mp_status green_apply_impl(mp_ctx* ctx, const int32_t n[3], double h, const doub
   dfree(ctx, tx);
   dfree(ctx, ty);
   dfree(ctx, tz);
+  dfree(ctx, ctl);
   return st;
 }
 }  // namespace
@@ -984,7 +1010,7 @@ mp_status mp_green_apply(mp_ctx* ctx, int32_t precision, const int32_t n[3], dou
                          const double ref_moduli[6], const void* tau, const void* mu, void* e_out,
                          void* g_out, void* stream) {
   if (!ctx) return set_error(nullptr, MP_E_INVALID_ARG, "ctx is NULL");
-  if (!n || !ref_moduli || !tau || !mu || !e_out || !g_out || (precision != 0 && precision != 1))
+  if (!n || !ref_moduli || !tau || !mu || !e_out || !g_out || precision < 0 || precision > 2)
     return set_error(ctx, MP_E_INVALID_ARG, "invalid arguments");
   for (int j = 0; j < 3; ++j)
     if (n[j] < 1 || !size_ok(n[j])) return set_error(ctx, MP_E_UNSUPPORTED_SIZE, "grid size %d unsupported", n[j]);

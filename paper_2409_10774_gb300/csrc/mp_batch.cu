@@ -323,7 +323,7 @@ class Engine {
           g.state = Progress::kStart;
           // an FP32-mixed cell that finished this increment in FP64 starts the
           // next one in FP32 again (it moves after this round's commit)
-          if (kFp64 && q.precision == 1) {
+          if (kFp64 && q.precision != 0) {
             g.demote = true;
             continue;
           }
@@ -462,7 +462,7 @@ class Engine {
       c.G[k] = (R)q->G[9 * s.g.s + k];
     }
     std::vector<PhaseDev<R>> ph(q->phases.size());
-    for (size_t k = 0; k < ph.size(); ++k) ph[k] = phase_dev<R>(q->phases[k]);
+    for (size_t k = 0; k < ph.size(); ++k) ph[k] = phase_dev<R>(q->phases[k], q->precision == 2);
     AxisPlan<R>* plans[3] = {&c.px, &c.py, &c.pz};
     std::vector<cpx<R>> tw[3];
     cudaError_t e = cudaSuccess;

@@ -52,6 +52,7 @@ struct PhaseDev {
   float inv_tf, inv_mf, ct_invf, tH_invf, cm_invf, mH_invf;  // the last six in single precision
   int elastic;
   int skew_m;                           // 1 when gamma > beta (b2 finite, skew part of m live)
+  int ret32;                            // FP32 fields only: form the level return in FP32 too
 };
 
 // Reference medium (A0, B0) in the field type.

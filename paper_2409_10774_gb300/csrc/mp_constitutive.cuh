@@ -44,12 +44,13 @@ __device__ __forceinline__ float float_rz(double x) {
   return __int_as_float(((ex - 1023 + 127) << 23) | ((hi & 0xfffff) << 3) | (int)(lo >> 29));
 }
 
-// Closed-form return of one level in single precision (FP32 fields): the
-// trial value q2 = (eq. stress)^2 is itself a single-precision quantity, so
-// the radius Y + H p_n, the multiplier increment and the scale factor are
-// formed in single precision too; only the accumulated multiplier p stays in
-// FP64, so that small increments are not lost against it.  Returns false on
-// the elastic branch.
+// Closed-form return of one level in single precision (precision 2 only: FP32
+// fields whose level return is FP32 as well).  The trial value q2 = (eq.
+// stress)^2 is itself a single-precision quantity there, so the radius
+// Y + H p_n, the multiplier increment and the scale factor are formed in
+// single precision; only the accumulated multiplier p stays in FP64, so that
+// small increments are not lost against it.  Returns false on the elastic
+// branch.  The default FP32-field precision (1) forms all of these in FP64.
 __device__ __forceinline__ bool return_level_f32(float q2, float Yf, float Hf, float inv, float c_inv, float H_inv,
                                                  double pn, double& p, float& f) {
   const float Rn = fmaf(Hf, float_rz(pn), Yf);
@@ -144,18 +145,21 @@ __device__ __forceinline__ void return_macro(const PhaseDev<R>& P, const R* e, c
     for (int i = 0; i < 9; ++i) s[i] = t[i];
     s[0] -= vol; s[4] -= vol; s[8] -= vol;
     const R teq2r = eq_sq(s, P.a1, P.a2, true);
-    if constexpr (sizeof(R) == 4) {
-      float f;
-      if (return_level_f32(teq2r, P.tYf, P.tHf, P.inv_tf, P.ct_invf, P.tH_invf, pn, p, f)) ft = f;
+    float f32;
+    if (sizeof(R) == 4 && P.ret32) {
+      if (return_level_f32((float)teq2r, P.tYf, P.tHf, P.inv_tf, P.ct_invf, P.tH_invf, pn, p, f32)) ft = (R)f32;
     } else {
+      // the scalar solve in FP64 (for FP32 fields the trial value teq2r is
+      // widened exactly)
+      const double q2 = (double)teq2r;
       const double R1n = fma(P.tH, pn, P.tY);
-      if (!(teq2r < R1n * R1n)) {  // plastic: t_eq^trial >= t_Y + t_H p_n
+      if (!(q2 < R1n * R1n)) {  // plastic: t_eq^trial >= t_Y + t_H p_n
         // eq. trial_stresses2: p - p_n = (t_eq^trial - R1(p_n)) / (t_H + 2 a1 mu).
         // Since R1(p) + 2 a1 mu (p - p_n) = t_eq^trial, the return factor
         // R1 / (R1 + 2 a1 mu (p - p_n)) = R1(p) / t_eq^trial
         //   = [2 a1 mu R1(p_n) + t_H t_eq^trial] / [(t_H + 2 a1 mu) t_eq^trial].
-        const double rinv = rsqrt_newton<2>(teq2r, (float)teq2r);
-        const double teq = teq2r * rinv;
+        const double rinv = rsqrt_newton<2>(q2, (float)teq2r);
+        const double teq = q2 * rinv;
         p = pn + (teq - R1n) * P.inv_t;
         ft = (R)fma(P.ct_inv * R1n, rinv, P.tH_inv);
       }
@@ -179,14 +183,15 @@ __device__ __forceinline__ void return_micro(const PhaseDev<R>& P, const R* g, c
   if (!P.elastic) {
     // eq. equiv_couple_stress on the trial couple stress
     const R meq2r = eq_sq(m, P.b1, P.b2, P.skew_m != 0);
-    if constexpr (sizeof(R) == 4) {
-      float f;
-      if (return_level_f32(meq2r, P.mYf, P.mHf, P.inv_mf, P.cm_invf, P.mH_invf, qn, q, f)) fm = f;
+    float f32;
+    if (sizeof(R) == 4 && P.ret32) {
+      if (return_level_f32((float)meq2r, P.mYf, P.mHf, P.inv_mf, P.cm_invf, P.mH_invf, qn, q, f32)) fm = (R)f32;
     } else {
+      const double q2 = (double)meq2r;
       const double R2n = fma(P.mH, qn, P.mY);
-      if (!(meq2r < R2n * R2n)) {
-        const double rinv = rsqrt_newton<2>(meq2r, (float)meq2r);
-        const double meq = meq2r * rinv;
+      if (!(q2 < R2n * R2n)) {
+        const double rinv = rsqrt_newton<2>(q2, (float)meq2r);
+        const double meq = q2 * rinv;
         q = qn + (meq - R2n) * P.inv_m;
         fm = (R)fma(P.cm_inv * R2n, rinv, P.mH_inv);
       }

@@ -80,10 +80,13 @@ struct DeviceScope {
 
 namespace mp {
 
-// Per-phase constants of Algorithm 1, prepared in FP64.
+// Per-phase constants of Algorithm 1, prepared in FP64.  ret32 (FP32 fields
+// only): the closed-form level return forms its radius, square root, plastic
+// multiplier increment and scale factor in FP32 instead of FP64.
 template <class R>
-PhaseDev<R> phase_dev(const mp_phase& ph) {
+PhaseDev<R> phase_dev(const mp_phase& ph, bool ret32 = false) {
   PhaseDev<R> d{};
+  d.ret32 = (ret32 && sizeof(R) == 4) ? 1 : 0;
   d.lam = (R)ph.lambda;
   d.mu = (R)ph.mu;
   d.kap = (R)ph.kappa;

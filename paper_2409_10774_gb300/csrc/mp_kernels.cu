@@ -36,17 +36,6 @@ __device__ __forceinline__ T shfl_sum(T v) {
   return v;
 }
 
-// Compensated (Kahan) accumulation s += x; c carries the rounding lost so far
-// (the sum is s - c).  Keeps per-thread running sums in the field type accurate
-// to a few units in the last place however many terms they take.
-template <class T>
-__device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
-  const T y = x - c;
-  const T t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
 template <class R>
 __device__ __forceinline__ R signed_freq_scale(int k, int n, R two_pi_over_L) {
   const int s = (k <= n / 2) ? k : k - n;
@@ -533,8 +522,8 @@ __device__ __forceinline__ void flag_timeout(int* status) {
 template <class R, int MODE, bool MULTI>
 __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item, unsigned char* smem_raw,
                                             uint32_t& parity, double* itm, R* tms, R (&tmax)[4],
-                                            R (&tsum)[4], R (&tcmp)[4], R (&rcar)[2], const R* fin_tau, const R* fin_mu, R* fout_e,
-                                            R* fout_g) {
+                                            double (&tsum)[4], double& rtot, const R* fin_tau, const R* fin_mu,
+                                            R* fout_e, R* fout_g) {
   const int rows = c.rows_a;
   const int N1 = c.n1;
   const int M = c.kx;                 // complex entries per row (N1 / 2, or 1)
@@ -840,55 +829,54 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
     bulk_commit();
   }
   // ---------------------------------------------------------- error partials of the item
-  // Reduced in the field type (on this part FP64 runs at a small fraction of
-  // the FP32 rate) and widened to FP64 once per item (multi-cell records) or
-  // once per kernel (single cell: per-thread compensated carries).
+  // Per-voxel norms of the FP32 (or FP64) field differences are formed in the
+  // field type; their maxima are exact in any precision, and their sums (the
+  // average measure) and the row sums behind the means are accumulated in FP64.
   if (MODE == kIter) {
     // the sums only enter the average measure (eq. err_average)
     const bool want_sum = c.err_kind != 0;
-    R* redr = reinterpret_cast<R*>(red);  // [warps][8] in the field type
     if constexpr (MULTI) {
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const R mx = shfl_max(dmax[a]);
-        const R sm = want_sum ? shfl_sum(dsum[a]) : R(0);
+        const double sm = want_sum ? shfl_sum((double)dsum[a]) : 0.0;
         if (lane == 0) {
-          redr[warp * 8 + a] = mx;
-          redr[warp * 8 + 4 + a] = sm;
+          red[warp * 8 + a] = (double)mx;
+          red[warp * 8 + 4 + a] = sm;
         }
       }
     } else {
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         tmax[a] = max(tmax[a], dmax[a]);
-        if (want_sum) kahan_add(tsum[a], tcmp[a], dsum[a]);
+        if (want_sum) tsum[a] += (double)dsum[a];
       }
     }
     // Row sums.  With the unnormalised inverse along x, sum_x e~ = N1 X_in[0],
     // so sum_x e = N1 (E + X_in[0]); the forward DC is sum_x tau.
-    R rsum = R(0);
+    double rsum = 0.0;
     const int q = threadIdx.x - 32;
     if (q >= 0 && q < 36) {
       if (q < 18) {
-        const R mean = (q < 9) ? c.E[q] : c.G[q - 9];
-        for (int rr = 0; rr < nr; ++rr) rsum += R(N1) * (mean + dcin[q * rows + rr]);
+        const double mean = (double)((q < 9) ? c.E[q] : c.G[q - 9]);
+        for (int rr = 0; rr < nr; ++rr) rsum += (double)N1 * (mean + (double)dcin[q * rows + rr]);
       } else {
-        for (int rr = 0; rr < nr; ++rr) rsum += X[rr * M * 18 + (q - 18)].x;
+        for (int rr = 0; rr < nr; ++rr) rsum += (double)X[rr * M * 18 + (q - 18)].x;
       }
-      if constexpr (!MULTI) kahan_add(rcar[0], rcar[1], rsum);
+      if constexpr (!MULTI) rtot += rsum;
     }
     if constexpr (MULTI) {
       __syncthreads();
       const int nwarp = blockDim.x >> 5;
       if (threadIdx.x < 8) {
-        R a = redr[threadIdx.x];
+        double a = red[threadIdx.x];
         for (int w = 1; w < nwarp; ++w) {
-          const R vv = redr[w * 8 + threadIdx.x];
-          a = (threadIdx.x < 4) ? max(a, vv) : a + vv;
+          const double vv = red[w * 8 + threadIdx.x];
+          a = (threadIdx.x < 4) ? fmax(a, vv) : a + vv;
         }
-        itm[threadIdx.x] = (double)a;
+        itm[threadIdx.x] = a;
       } else if (q >= 0 && q < 36) {
-        itm[8 + q] = (double)rsum;
+        itm[8 + q] = rsum;
       }
     }
   }
@@ -920,15 +908,15 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
   bool failed = false;
   int* status = c0.status;
   R tmax[4] = {R(0), R(0), R(0), R(0)};
-  R tsum[4] = {R(0), R(0), R(0), R(0)}, tcmp[4] = {R(0), R(0), R(0), R(0)};
-  R rcar[2] = {R(0), R(0)};  // threads 32..67: the block's row sum (and its compensation) of entry q
+  double tsum[4] = {0.0, 0.0, 0.0, 0.0};
+  double rtot = 0.0;  // threads 32..67: the block's row sum of entry q
   for_items<R, MULTI>(c0, c0.items_a, w, cs, [&](const CellDev<R>& c, long long item) {
     if (failed) {
       flag_timeout(c.status);  // every cell with a skipped item reports the failure
       return;
     }
-    if (!pass_a_item<R, MODE, MULTI>(c, item, smem_raw, parity, itm, tms, tmax, tsum, tcmp, rcar, fin_tau, fin_mu, fout_e,
-                                     fout_g)) {
+    if (!pass_a_item<R, MODE, MULTI>(c, item, smem_raw, parity, itm, tms, tmax, tsum, rtot, fin_tau, fin_mu,
+                                     fout_e, fout_g)) {
       failed = true;
       status = c.status;
       return;
@@ -948,7 +936,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const R mx = shfl_max(tmax[a]);
-      const double sm = shfl_sum((double)tsum[a] - (double)tcmp[a]);
+      const double sm = shfl_sum(tsum[a]);
       if (lane == 0) {
         red[warp * 8 + a] = (double)mx;
         red[warp * 8 + 4 + a] = sm;
@@ -964,7 +952,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
       acc[threadIdx.x] = a;
     }
     const int q = threadIdx.x - 32;
-    if (q >= 0 && q < 36) acc[8 + q] = (double)rcar[0] - (double)rcar[1];
+    if (q >= 0 && q < 36) acc[8 + q] = rtot;
     __syncthreads();
   }
   if (threadIdx.x == 0) bulk_wait_all();
@@ -1531,14 +1519,23 @@ cudaError_t launch_fields(const LaunchCfg& L, const CellDev<R>& c, int from_elas
 
 template <class R>
 cudaError_t launch_green_apply(const LaunchCfg& L, const CellDev<R>& c, const R* tau, const R* mu,
-                               R* e_out, R* g_out, cudaStream_t st) {
+                               R* e_out, R* g_out, cudaStream_t st, int* ctl, int nsm) {
   cudaError_t e = set_smem_attrs<R>();
   if (e != cudaSuccess) return e;
   const size_t sa = smem_pass_a<R>(c.n1, c.rows_a);
   k_pass_a<R, kXFwd, false><<<L.grid_a, kThreads, sa, st>>>(c, Work<R>{}, nullptr, tau, mu, nullptr, nullptr);
-  if (c.n2 > 1) k_fft_y<R, -1, false, 0><<<L.grid_y, kThreadsYZ, smem_line_pass<R>(c.n2), st>>>(c, Work<R>{});
-  k_green_z<R, false, 0><<<L.grid_z, kThreadsYZ, smem_line_pass<R>(c.n3), st>>>(c, Work<R>{});
-  if (c.n2 > 1) k_fft_y<R, +1, false, 0><<<L.grid_y, kThreadsYZ, smem_line_pass<R>(c.n2), st>>>(c, Work<R>{});
+  bool fused = false;
+  if constexpr (sizeof(R) == 4) {
+    if (ctl) {
+      fused = true;
+      if ((e = launch_spectral(c, ctl, nsm, st)) != cudaSuccess) return e;
+    }
+  }
+  if (!fused) {
+    if (c.n2 > 1) k_fft_y<R, -1, false, 0><<<L.grid_y, kThreadsYZ, smem_line_pass<R>(c.n2), st>>>(c, Work<R>{});
+    k_green_z<R, false, 0><<<L.grid_z, kThreadsYZ, smem_line_pass<R>(c.n3), st>>>(c, Work<R>{});
+    if (c.n2 > 1) k_fft_y<R, +1, false, 0><<<L.grid_y, kThreadsYZ, smem_line_pass<R>(c.n2), st>>>(c, Work<R>{});
+  }
   k_pass_a<R, kXInv, false><<<L.grid_a, kThreads, sa, st>>>(c, Work<R>{}, nullptr, nullptr, nullptr, e_out, g_out);
   return cudaGetLastError();
 }
@@ -1629,7 +1626,7 @@ bool sizes_fit(int n1, int n2, int n3) {
   template cudaError_t launch_fields<R>(const LaunchCfg&, const CellDev<R>&, int, double*, double*,   \
                                         double*, double*, double*, double*, cudaStream_t);           \
   template cudaError_t launch_green_apply<R>(const LaunchCfg&, const CellDev<R>&, const R*, const R*,  \
-                                             R*, R*, cudaStream_t);                                  \
+                                             R*, R*, cudaStream_t, int*, int);                       \
   template cudaError_t launch_radial_return<R>(int, long long, const uint16_t*, const PhaseDev<R>*,   \
                                                const R*, const R*, const R*, const R*, const R*,      \
                                                const R*, const double*, const double*, R*, R*,        \

@@ -70,15 +70,25 @@ size_t smem_line_pass(int n);
 template <class R>
 cudaError_t launch_fields(const LaunchCfg& L, const CellDev<R>& c, int from_elast, double* fe,
                           double* fg, double* ft, double* fm, double* fp, double* fq, cudaStream_t st);
+// ctl (FP32 cells with spectral_fused_ok only; else NULL): the fused spectral
+// pass's control words, which select it for the y / z work.
 template <class R>
 cudaError_t launch_green_apply(const LaunchCfg& L, const CellDev<R>& c, const R* tau, const R* mu,
-                               R* e_out, R* g_out, cudaStream_t st);
+                               R* e_out, R* g_out, cudaStream_t st, int* ctl = nullptr, int nsm = 0);
 template <class R>
 cudaError_t launch_radial_return(int nsm, long long count, const uint16_t* phase,
                                  const PhaseDev<R>* phases, const R* e, const R* g, const R* e_n,
                                  const R* g_n, const R* t_n, const R* m_n, const double* p_n,
                                  const double* q_n, R* t, R* m, double* p, double* q,
                                  cudaStream_t st);
+
+// Fused spectral pass (y forward, z forward, Green operator, z inverse, y
+// inverse in one persistent launch; mp_spectral.cu) for FP32 cells whose y
+// and z lengths are 256.  ctl: spectral_ctl_ints(c.kx) ints of device memory
+// (zeroed by the launcher on `st`).
+bool spectral_fused_ok(const CellDev<float>& c);
+size_t spectral_ctl_ints(int kx);
+cudaError_t launch_spectral(const CellDev<float>& c, int* ctl, int nsm, cudaStream_t st);
 
 // dst[i] = (D) src[i], i < n (state of a cell changing precision).
 template <class S, class D>

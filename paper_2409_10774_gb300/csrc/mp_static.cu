@@ -135,7 +135,7 @@ mp_status mp_green_apply_static(mp_ctx* ctx, int32_t precision, const int32_t n[
                                 const double ref_moduli[6], const void* tau, const void* mu,
                                 void* e_out, void* g_out, void* stream) {
   if (!ctx) return set_error(nullptr, MP_E_INVALID_ARG, "mp_green_apply_static: ctx is NULL");
-  if (!n || !ref_moduli || !tau || !mu || !e_out || !g_out || (precision != 0 && precision != 1))
+  if (!n || !ref_moduli || !tau || !mu || !e_out || !g_out || precision < 0 || precision > 2)
     return fail(ctx, MP_E_INVALID_ARG, "mp_green_apply_static: invalid arguments");
   for (int j = 0; j < 3; ++j)
     if (!axis_ok(n[j]))

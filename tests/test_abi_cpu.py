@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(lib_path):
 
 def test_binding_loads_and_reports_version(lib_path):
     import paper_2409_10774_gb300 as M
-    assert M.mp_abi_version() == 1
+    assert M.mp_abi_version() == 2
 
 
 def test_validation_without_gpu(lib_path):

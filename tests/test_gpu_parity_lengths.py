@@ -124,3 +124,44 @@ def test_voronoi_256_sampled_return_and_mean(ctx):
     assert np.abs(f["t"][z, y, x] - t).max() <= 2e-6 * np.abs(t).max()
     assert np.abs(f["m"][z, y, x] - m).max() <= 2e-6 * max(np.abs(m).max(), 1e-300) + 1e-12
     assert np.abs(f["p"][z, y, x] - pp).max() <= 2e-5 * pp.max()
+
+
+# ---------------------------------------------------------------- fused spectral pass
+# FP32 cells whose y and z lengths are 256 run the y forward, z forward, Green
+# operator, z inverse and y inverse transforms as one persistent launch that
+# takes each kx column-plane through all three phases while it is in L2.  It
+# must compute what the three separate passes compute.
+
+@pytest.mark.parametrize("n", [(2, 256, 256), (6, 256, 256), (16, 256, 256)])
+def test_green_apply_fused_spectral_pass(ctx, n):
+    import paper_2409_10774_gb300 as M
+    rng = np.random.default_rng(sum(n))
+    shape = (n[2], n[1], n[0], 3, 3)
+    tau = rng.standard_normal(shape)
+    mu = rng.standard_normal(shape)
+    h = 0.83
+    ref = (18.0, 11.0, 2.5, 0.4, 1.3, 1.7)
+    e_ref, g_ref = _oracle_green(n, h, ref, tau, mu)
+    e, g = M.mp_green_apply(ctx, 1, n, h, ref, torch.as_tensor(tau, dtype=torch.float32, device="cuda"),
+                            torch.as_tensor(mu, dtype=torch.float32, device="cuda"))
+    e = e.cpu().numpy().astype(np.float64)
+    g = g.cpu().numpy().astype(np.float64)
+    assert np.abs(e - e_ref).max() <= 2e-5 * np.abs(e_ref).max()
+    assert np.abs(g - g_ref).max() <= 2e-5 * np.abs(g_ref).max()
+
+
+def test_lockstep_solve_on_fused_spectral_pass(ctx):
+    import paper_2409_10774_gb300 as M
+    n = (2, 256, 256)
+    prob = _thin_problem(n, seed=7)
+    # ten iterations on both sides (the oracle needs ~2 s for each on this cell)
+    ref = OS.solve(prob, lockstep_iters=[10])
+    assert ref["status"] == "ok" and ref["P"][0] > 0.0
+    rve = M.Rve(ctx, prob, precision=1, lockstep_iters=ref["iters"])
+    rve.profile(True)
+    assert rve.run(len(ref["iters"])) == 0
+    prof = rve.profile_read()
+    res = rve.results(fields=True)
+    rve.close()
+    assert prof["spectral"][1] == int(np.sum(ref["iters"])) and prof["green_z"][1] == 0
+    _compare_solves(res, ref, 1e-6, 1e-5, h=prob["h"])

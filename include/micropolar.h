@@ -108,6 +108,15 @@ typedef struct mp_problem {
   int32_t precision;            /* MP_PRECISION_*: 0 FP64, 1 FP32 fields + FP64 scalars, 2 */
   const int32_t* lockstep_iters;/* optional host n_steps: run exactly these iterations    */
   double div_limit;             /* err above this => MP_E_DIVERGED; <= 0 means 1e6        */
+  /* Optional source term of a numerically manufactured solution (Appendix
+   * D.1, eq. manufactured_polarization_stress): at time index s the
+   * polarizations become tau = t - A0 e - t^m(s), mu = m - B0 gamma - m^m(s).
+   * Host arrays of (n_steps + 1) * N1*N2*N3 * 9 values, voxel-major per time
+   * (index 0, the zero state, is not read); both NULL (no source) or both
+   * given.  The library keeps a device copy of n_steps * N1*N2*N3 * 18
+   * values of the field type for the solve. */
+  const double* tau_m;
+  const double* mu_m;
 } mp_problem;
 
 /* Results (caller-allocated host buffers; any pointer may be NULL).

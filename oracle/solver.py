@@ -120,14 +120,31 @@ def polarization(t, m, e, g, A0, B0, tau_m=None, mu_m=None):
     return tau, mu
 
 
-def fixed_point_update(tau, mu, E, G, green):
+def _library_fftn(x):
+    return np.fft.fftn(x, axes=(0, 1, 2))
+
+
+def _library_ifftn(x):
+    return np.fft.ifftn(x, axes=(0, 1, 2))
+
+
+# The discrete Fourier transform of the scheme (same convention, unnormalised
+# forward, 1/V inverse), evaluated by the oracle's own FFT ("own", default)
+# or by numpy's FFT library routine ("library"), which computes the same
+# transform (tests/test_oracle_fft_green.py checks the two against each other
+# and against the brute-force triple sum) and is used for long reference runs.
+FFT_BACKENDS = {"own": (offt.fftn, offt.ifftn), "library": (_library_fftn, _library_ifftn)}
+
+
+def fixed_point_update(tau, mu, E, G, green, fft="own"):
     """One Lippmann-Schwinger update (Alg. 2 while-loop, transform / contract /
     inverse-transform steps): e = E + F^-1[G(tau^, mu^)], gamma likewise."""
-    tau_hat = offt.fftn(tau)
-    mu_hat = offt.fftn(mu)
+    fwd, inv = FFT_BACKENDS[fft]
+    tau_hat = fwd(tau)
+    mu_hat = fwd(mu)
     e_hat, g_hat = green(tau_hat, mu_hat)
-    e = E + offt.ifftn(e_hat).real
-    g = G + offt.ifftn(g_hat).real
+    e = E + inv(e_hat).real
+    g = G + inv(g_hat).real
     return e, g
 
 
@@ -143,7 +160,7 @@ def averages(fields, phase_map, phases):
 
 
 def solve(problem, lockstep_iters=None, source=None, keep_fields=False, div_limit=1e6,
-          max_steps=None, callback=None):
+          max_steps=None, callback=None, fft="own"):
     """Run Algorithm 2 on ``problem``.
 
     lockstep_iters: optional per-step iteration counts; when given, each step
@@ -155,6 +172,7 @@ def solve(problem, lockstep_iters=None, source=None, keep_fields=False, div_limi
     max_steps: stop after this many steps (bounded samples).
     callback: optional callable(step, iteration, err) called after every
         iteration (used for timing samples).
+    fft: 'own' (the oracle's FFT) or 'library' (numpy's), see FFT_BACKENDS.
 
     Returns a dict with per-step arrays and the final fields."""
     n = problem["n"]
@@ -179,7 +197,7 @@ def solve(problem, lockstep_iters=None, source=None, keep_fields=False, div_limi
     committed = [dict(e=z9.copy(), g=z9.copy())]  # converged e, gamma per step (s = 0 first)
 
     res = dict(T=[], M=[], Eavg=[], Gavg=[], P=[], Q=[], Teq=[], Meq=[], err=[], iters=[],
-               err_history=[], status="ok", failed_step=-1, fields=[])
+               err_history=[], err_parts=[], status="ok", failed_step=-1, fields=[])
     for s in range(1, n_steps + 1):
         E = Ep[s]
         G = Gp[s]
@@ -199,6 +217,7 @@ def solve(problem, lockstep_iters=None, source=None, keep_fields=False, div_limi
         err = 2.0 * tol
         it = 0
         errs = []
+        parts_s = []
         target = None if lockstep_iters is None else int(lockstep_iters[s - 1])
         while (err > tol) if target is None else (it < target):
             if target is None and it >= max_iter:
@@ -206,15 +225,16 @@ def solve(problem, lockstep_iters=None, source=None, keep_fields=False, div_limi
                 res["failed_step"] = s
                 break
             tau, mu = polarization(t, m, e, g, A0, B0, tau_m, mu_m)
-            e_new, g_new = fixed_point_update(tau, mu, E, G, green)
+            e_new, g_new = fixed_point_update(tau, mu, E, G, green, fft)
             t_new, m_new, p_new, q_new = radial_return_field(
                 e_new, g_new, hist["e"], hist["g"], hist["t"], hist["m"], hist["p"], hist["q"],
                 pm, phases)
-            err, _ = error_measure(dict(e=e_new, t=t_new, g=g_new, m=m_new),
-                                   dict(e=e, t=t, g=g, m=m), kind, h)
+            err, parts = error_measure(dict(e=e_new, t=t_new, g=g_new, m=m_new),
+                                       dict(e=e, t=t, g=g, m=m), kind, h)
             e, g, t, m, p, q = e_new, g_new, t_new, m_new, p_new, q_new
             it += 1
             errs.append(err)
+            parts_s.append((parts["e"], parts["t"], parts["g"], parts["m"]))
             if callback is not None:
                 callback(s, it, err)
             if not np.isfinite(err) or err > div_limit:
@@ -224,6 +244,7 @@ def solve(problem, lockstep_iters=None, source=None, keep_fields=False, div_limi
         res["iters"].append(it)
         res["err"].append(err)
         res["err_history"].append(errs)
+        res["err_parts"].append(parts_s)
         # commit (Alg. 2, last line of the time loop)
         hist = dict(e=e, g=g, t=t, m=m, p=p, q=q)
         committed.append(dict(e=e, g=g))

@@ -57,7 +57,8 @@ class mp_problem(C.Structure):
                 ("G", C.POINTER(C.c_double)), ("tol", C.c_double), ("err_kind", C.c_int32),
                 ("max_iter", C.c_int32), ("ref_kind", C.c_int32),
                 ("ref_moduli", C.POINTER(C.c_double)), ("precision", C.c_int32),
-                ("lockstep_iters", C.POINTER(C.c_int32)), ("div_limit", C.c_double)]
+                ("lockstep_iters", C.POINTER(C.c_int32)), ("div_limit", C.c_double),
+                ("tau_m", C.POINTER(C.c_double)), ("mu_m", C.POINTER(C.c_double))]
 
 
 _DP = C.POINTER(C.c_double)
@@ -183,6 +184,15 @@ class _Problem:
         self.ref = None
         if p.get("ref_moduli") is not None:
             self.ref = np.ascontiguousarray(p["ref_moduli"], dtype=np.float64)
+        # manufactured source (both or neither; the library checks the pairing)
+        self.tau_m = self.mu_m = None
+        nel = (n_steps + 1) * n[0] * n[1] * n[2] * 9
+        for key in ("tau_m", "mu_m"):
+            if p.get(key) is not None:
+                arr = np.ascontiguousarray(p[key], dtype=np.float64).reshape(-1)
+                if arr.size != nel:
+                    raise ValueError(f"{key} must hold (n_steps + 1) * N1*N2*N3 * 9 values")
+                setattr(self, key, arr)
         self.lock = None
         if lockstep_iters is not None:
             self.lock = np.ascontiguousarray(lockstep_iters, dtype=np.int32)
@@ -205,6 +215,8 @@ class _Problem:
         self.st.precision = int(prec)
         self.st.lockstep_iters = self.lock.ctypes.data_as(C.POINTER(C.c_int32)) if self.lock is not None else None
         self.st.div_limit = float(div_limit)
+        self.st.tau_m = _dptr(self.tau_m) if self.tau_m is not None else None
+        self.st.mu_m = _dptr(self.mu_m) if self.mu_m is not None else None
         self.n = n
         self.n_steps = n_steps
 

@@ -210,6 +210,18 @@ mp_status validate_problem(const mp_problem* p, std::vector<long long>* counts_o
     msg = "grid too large for the kernels' shared-memory tiles at this precision";
     return MP_E_UNSUPPORTED_SIZE;
   }
+  if ((p->tau_m == nullptr) != (p->mu_m == nullptr)) {
+    msg = "tau_m and mu_m must be given together";
+    return MP_E_INVALID_ARG;
+  }
+  if (p->tau_m) {
+    const size_t nsrc = (size_t)(p->n_steps + 1) * (size_t)p->n[0] * p->n[1] * p->n[2] * 9;
+    for (size_t i = 0; i < nsrc; ++i)
+      if (!finite(p->tau_m[i]) || !finite(p->mu_m[i])) {
+        msg = "manufactured source not finite";
+        return MP_E_INVALID_ARG;
+      }
+  }
   if (p->lockstep_iters)
     for (int s = 0; s < p->n_steps; ++s)
       if (p->lockstep_iters[s] < 1) {
@@ -262,7 +274,7 @@ struct mp_rve {
   double div_limit = 1e6;
   double ref[6] = {0, 0, 0, 0, 0, 0};
   DevBuf spec, prev, hist, pq, elast, phase, phases, twx, twy, twz, partials, avgpart, errout, steprows,
-      status, tmean, ctl;
+      status, tmean, ctl, src;
   CellDev<float> cf{};
   CellDev<double> cd{};
   LaunchCfg L;
@@ -348,6 +360,12 @@ mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
   if ((s = dalloc(ctx, r->avgpart, sizeof(double) * kAvgPartials * (size_t)r->L.grid_v)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->errout, sizeof(double) * 8)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->steprows, sizeof(double) * kAvgPartials * (size_t)r->n_steps)) != MP_OK) return s;
+  std::vector<R> src_host;
+  if (p->tau_m) {
+    centred_source<R>(p->tau_m, p->mu_m, p->n_steps, r->nvox, src_host);
+    if ((s = dalloc(ctx, r->src, sizeof(R) * src_host.size())) != MP_OK) return s;
+    MP_CK(ctx, cudaMemcpyAsync(r->src.ptr, src_host.data(), sizeof(R) * src_host.size(), cudaMemcpyHostToDevice, st));
+  }
   if constexpr (sizeof(R) == 4) {
     if (spectral_fused_ok(c) &&
         (s = dalloc(ctx, r->ctl, sizeof(int) * spectral_ctl_ints(c.kx))) != MP_OK)
@@ -373,6 +391,7 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
   mp_ctx* ctx = r->ctx;
   CellDev<R>& c = cell_of<R>(r);
   set_load(c, r, s);
+  c.src = r->src.ptr ? reinterpret_cast<const R*>(r->src.ptr) + (size_t)(s - 1) * (size_t)r->nvox * 18 : nullptr;
   MP_CK(ctx, launch_start<R>(r->L, c, s == 1 ? 1 : 0, st));
   r->launches[MP_KC_START] += (s == 1) ? 2 : 1;
   double err = 2.0 * r->tol;
@@ -511,6 +530,11 @@ uint64_t problem_digest(const mp_problem* p, const double ref[6]) {
   f.add(&p->tol, sizeof(p->tol));
   f.add(&p->err_kind, sizeof(p->err_kind));
   f.add(ref, sizeof(double) * 6);
+  if (p->tau_m) {
+    const size_t nsrc = (size_t)(p->n_steps + 1) * (size_t)nvox * 9;
+    f.add(p->tau_m, sizeof(double) * nsrc);
+    f.add(p->mu_m, sizeof(double) * nsrc);
+  }
   return f.h;
 }
 
@@ -527,7 +551,7 @@ void rve_free(mp_rve* r) {
   mp_ctx* ctx = r->ctx;
   DevBuf* bufs[] = {&r->spec, &r->prev, &r->hist, &r->pq, &r->elast, &r->phase, &r->phases,
                     &r->twx, &r->twy, &r->twz, &r->partials, &r->avgpart, &r->errout, &r->steprows,
-                    &r->status, &r->tmean, &r->ctl};
+                    &r->status, &r->tmean, &r->ctl, &r->src};
   for (DevBuf* b : bufs) dfree(ctx, *b);
   if (r->err_host) cudaFreeHost(r->err_host);
   r->err_host = nullptr;

@@ -55,6 +55,7 @@ struct Request {
   double tol = 1e-6, div_limit = 1e6;
   int err_kind = 0, max_iter = 10000;
   std::vector<int> lockstep;
+  std::vector<double> tau_m, mu_m;  // manufactured source ((n_steps + 1) * nvox * 9 each), or empty
   double ref[6] = {0, 0, 0, 0, 0, 0};
   mp_result* res = nullptr;  // caller's host buffers (written when the solve ends)
   bool want_fields = false;
@@ -83,6 +84,11 @@ mp_status make_request(const mp_problem* p, mp_result* res, Request& q) {
   q.err_kind = p->err_kind;
   q.max_iter = p->max_iter > 0 ? p->max_iter : 10000;
   if (p->lockstep_iters) q.lockstep.assign(p->lockstep_iters, p->lockstep_iters + p->n_steps);
+  if (p->tau_m) {
+    const size_t nsrc = (size_t)(p->n_steps + 1) * (size_t)q.nvox * 9;
+    q.tau_m.assign(p->tau_m, p->tau_m + nsrc);
+    q.mu_m.assign(p->mu_m, p->mu_m + nsrc);
+  }
   q.div_limit = p->div_limit > 0 ? p->div_limit : 1e6;
   q.res = res;
   q.want_fields = res && (res->e || res->g || res->t || res->m || res->p || res->q);
@@ -154,7 +160,7 @@ struct BlockPool final : Pool {
 // ------------------------------------------------------------------ cell arena layout
 template <class R>
 struct ArenaLayout {
-  size_t spec, prev, hist, pq, elast, phase, phases, tw[3], status, tmean, ipart, apart, rows, fields, total;
+  size_t spec, prev, hist, pq, elast, phase, phases, tw[3], status, tmean, ipart, apart, rows, src, fields, total;
   ArenaLayout(const Request& q, long long items_a) {
     const long long kx = q.n[0] > 1 ? q.n[0] / 2 : 1;
     const size_t nspec = (size_t)kx * q.n[1] * q.n[2];
@@ -179,6 +185,7 @@ struct ArenaLayout {
     ipart = put(sizeof(double) * kErrPartials * (size_t)items_a);
     apart = put(sizeof(double) * kAvgPartials * chunks);
     rows = put(sizeof(double) * kAvgPartials * (size_t)q.n_steps);
+    src = put(q.tau_m.empty() ? 0 : sizeof(R) * 18 * nv * (size_t)q.n_steps);
     fields = q.want_fields ? put(sizeof(double) * 38 * nv) : o;
     total = o;
   }
@@ -231,6 +238,7 @@ struct Slot {
   LaunchCfg L;
   double* rows = nullptr;    // [n_steps][kAvgPartials] per-increment results
   double* fields = nullptr;  // [38][nvox] FP64 final fields (when requested)
+  const R* src = nullptr;    // [n_steps][nvox][18] manufactured source, or NULL
 };
 
 template <class R>
@@ -334,6 +342,7 @@ class Engine {
           c.E[k] = (R)q.E[9 * g.s + k];
           c.G[k] = (R)q.G[9 * g.s + k];
         }
+        c.src = sl.src ? sl.src + (size_t)(g.s - 1) * (size_t)q.nvox * 18 : nullptr;
         if (g.state == Progress::kInit) l_init.push_back(i);
         l_start.push_back(i);
         g.state = Progress::kIter;
@@ -459,6 +468,7 @@ class Engine {
     c.err_kind = q->err_kind;
     for (int k = 0; k < 9; ++k) {  // load of the current increment (a cell may move mid-increment)
       c.E[k] = (R)q->E[9 * s.g.s + k];
+      c.src = nullptr;
       c.G[k] = (R)q->G[9 * s.g.s + k];
     }
     std::vector<PhaseDev<R>> ph(q->phases.size());
@@ -479,6 +489,14 @@ class Engine {
     if (e == cudaSuccess) e = cudaMemsetAsync(b + A.status, 0, sizeof(int) * 4, st_);
     if (e == cudaSuccess) e = cudaMemsetAsync(b + A.tmean, 0, sizeof(double) * 18, st_);
     if (e == cudaSuccess && fresh) e = cudaMemsetAsync(s.rows, 0, sizeof(double) * kAvgPartials * q->n_steps, st_);
+    std::vector<R> src_host;
+    if (!q->tau_m.empty()) {
+      centred_source<R>(q->tau_m.data(), q->mu_m.data(), q->n_steps, q->nvox, src_host);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + A.src, src_host.data(), sizeof(R) * src_host.size(), cudaMemcpyHostToDevice, st_);
+      s.src = reinterpret_cast<const R*>(b + A.src);
+      c.src = s.src + (size_t)(s.g.s - 1) * (size_t)q->nvox * 18;
+    }
     // the host tables above are locals: the copies must have read them
     if (e == cudaSuccess) e = cudaStreamSynchronize(st_);
     if (e != cudaSuccess) {

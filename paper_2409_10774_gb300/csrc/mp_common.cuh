@@ -110,6 +110,9 @@ struct CellDev {
   double* tmean;          // [18] <t>, <m> of the last iteration (constants subtracted before transforms)
   int predict;            // commit: write the next increment's predictor
   double ratio;           // commit: (t_{n+1} - t_n) / (t_n - t_{n-1})
+  // Manufactured source of the current increment ([nvox][18]: t^m - <t^m>,
+  // m^m - <m^m>), subtracted from the polarization; NULL without a source.
+  const R* src;
 };
 
 // Columns per tile of the y / z passes for a transform length n: short

@@ -122,11 +122,23 @@ __device__ __forceinline__ R scaled_t(R ttr, bool diag, R vol, R ft) {
   return diag ? fma(ft, ttr - vol, vol) : ttr * ft;
 }
 
+// A level whose trial value q2 (FP32 fields) lies clearly inside the yield
+// surface of radius Y + H p_n, judged in single precision with a margin well
+// above its rounding, is elastic without the FP64 test; the other voxels take
+// the FP64 test, whose outcome this screen never contradicts.
+__device__ __forceinline__ bool surely_elastic_f32(float q2, float Yf, float Hf, double pn) {
+  const float Rn = fmaf(Hf, (float)pn, Yf);
+  return q2 < 0.999996f * (Rn * Rn);
+}
+
 // Algorithm 1, one level at a time: the macro level maps e (with the history
 // ht, p_n) to t, p and the scale factor ft; the micro level maps gamma (hm,
 // q_n) to m, q, fm.  The two levels share nothing but the phase, so a caller
 // short of registers can run them one after the other.
-template <class R>
+// NEWTON: Newton steps of the FP64 reciprocal square root (2 reach FP64
+// rounding; 1 leaves a relative error near 1e-14, ample for a scale factor
+// that is rounded to FP32 fields, and is what the FP32-field iteration uses).
+template <class R, int NEWTON = 2>
 __device__ __forceinline__ void return_macro(const PhaseDev<R>& P, const R* e, const R* ht, double pn, R* t,
                                              double& p, R& ft) {
   const R tre = (e[0] + e[4]) + e[8];
@@ -148,7 +160,7 @@ __device__ __forceinline__ void return_macro(const PhaseDev<R>& P, const R* e, c
     float f32;
     if (sizeof(R) == 4 && P.ret32) {
       if (return_level_f32((float)teq2r, P.tYf, P.tHf, P.inv_tf, P.ct_invf, P.tH_invf, pn, p, f32)) ft = (R)f32;
-    } else {
+    } else if (!(sizeof(R) == 4 && surely_elastic_f32((float)teq2r, P.tYf, P.tHf, pn))) {
       // the scalar solve in FP64 (for FP32 fields the trial value teq2r is
       // widened exactly)
       const double q2 = (double)teq2r;
@@ -158,7 +170,7 @@ __device__ __forceinline__ void return_macro(const PhaseDev<R>& P, const R* e, c
         // Since R1(p) + 2 a1 mu (p - p_n) = t_eq^trial, the return factor
         // R1 / (R1 + 2 a1 mu (p - p_n)) = R1(p) / t_eq^trial
         //   = [2 a1 mu R1(p_n) + t_H t_eq^trial] / [(t_H + 2 a1 mu) t_eq^trial].
-        const double rinv = rsqrt_newton<2>(q2, (float)teq2r);
+        const double rinv = rsqrt_newton<NEWTON>(q2, (float)teq2r);
         const double teq = q2 * rinv;
         p = pn + (teq - R1n) * P.inv_t;
         ft = (R)fma(P.ct_inv * R1n, rinv, P.tH_inv);
@@ -169,7 +181,7 @@ __device__ __forceinline__ void return_macro(const PhaseDev<R>& P, const R* e, c
   for (int i = 0; i < 9; ++i) t[i] = scaled_t(t[i], i % 4 == 0, vol, ft);
 }
 
-template <class R>
+template <class R, int NEWTON = 2>
 __device__ __forceinline__ void return_micro(const PhaseDev<R>& P, const R* g, const R* hm, double qn, R* m,
                                              double& q, R& fm) {
   const R trg = (g[0] + g[4]) + g[8];
@@ -186,11 +198,11 @@ __device__ __forceinline__ void return_micro(const PhaseDev<R>& P, const R* g, c
     float f32;
     if (sizeof(R) == 4 && P.ret32) {
       if (return_level_f32((float)meq2r, P.mYf, P.mHf, P.inv_mf, P.cm_invf, P.mH_invf, qn, q, f32)) fm = (R)f32;
-    } else {
+    } else if (!(sizeof(R) == 4 && surely_elastic_f32((float)meq2r, P.mYf, P.mHf, qn))) {
       const double q2 = (double)meq2r;
       const double R2n = fma(P.mH, qn, P.mY);
       if (!(q2 < R2n * R2n)) {
-        const double rinv = rsqrt_newton<2>(q2, (float)meq2r);
+        const double rinv = rsqrt_newton<NEWTON>(q2, (float)meq2r);
         const double meq = q2 * rinv;
         q = qn + (meq - R2n) * P.inv_m;
         fm = (R)fma(P.cm_inv * R2n, rinv, P.mH_inv);

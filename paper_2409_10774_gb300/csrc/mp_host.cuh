@@ -124,6 +124,36 @@ PhaseDev<R> phase_dev(const mp_phase& ph, bool ret32 = false) {
   return d;
 }
 
+// The manufactured source of a problem (Appendix D.1) as the kernels read it:
+// for each increment s = 1..n_steps, [nvox][18] values t^m - <t^m>,
+// m^m - <m^m> in the field type.  The subtracted constants only change the
+// zero-frequency term of the polarization, which the Green operator
+// discards, so the iterates are those of eq. manufactured_polarization_stress.
+template <class R>
+void centred_source(const double* tau_m, const double* mu_m, int n_steps, long long nvox, std::vector<R>& out) {
+  out.assign((size_t)n_steps * (size_t)nvox * 18, R(0));
+  for (int s = 1; s <= n_steps; ++s) {
+    const double* ts = tau_m + (size_t)s * nvox * 9;
+    const double* ms = mu_m + (size_t)s * nvox * 9;
+    double mt[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, mm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long v = 0; v < nvox; ++v)
+      for (int q = 0; q < 9; ++q) {
+        mt[q] += ts[v * 9 + q];
+        mm[q] += ms[v * 9 + q];
+      }
+    for (int q = 0; q < 9; ++q) {
+      mt[q] /= (double)nvox;
+      mm[q] /= (double)nvox;
+    }
+    R* o = out.data() + (size_t)(s - 1) * (size_t)nvox * 18;
+    for (long long v = 0; v < nvox; ++v)
+      for (int q = 0; q < 9; ++q) {
+        o[v * 18 + q] = (R)(ts[v * 9 + q] - mt[q]);
+        o[v * 18 + 9 + q] = (R)(ms[v * 9 + q] - mm[q]);
+      }
+  }
+}
+
 template <class R>
 RefDev<R> ref_dev(const double ref[6]) {
   RefDev<R> r;

@@ -570,6 +570,10 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
     }
   }
   cpx<R>* zbuf = b0;  // buffer holding the packed real rows
+  // Without loads to wait for (forward-only mode), the barrier that orders
+  // thread 0's wait for the previous item's bulk stores (which may still be
+  // reading b0) before every thread's writes to b0 must be explicit.
+  if (!use_spec_in && !use_vox) __syncthreads();
   // ---------------------------------------------------------- inverse x
   if (use_spec_in) {
     const bool ok = mbar_wait(&bars[0], parity);
@@ -635,6 +639,7 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
       const R fto = pv[18], fmo = pv[19];
       const R a0 = c.ref.mu + c.ref.kap, b0 = c.ref.mu - c.ref.kap;
       const bool din = MODE == kIter && c.delta_in != 0, dout = MODE == kIter && c.delta_out != 0;
+      const R* sv = c.src ? c.src + v * 18 : nullptr;
       R ft, fm, e8;
       // ---- macro level
       {
@@ -661,7 +666,8 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
 #pragma unroll
         for (int q = 0; q < 9; ++q) e[q] = (MODE == kIter) ? (din ? eo[q] : c.E[q]) + de9[q] : eo[q];
         double pn = pq.x;
-        return_macro<R>(P, e, ht, pn, t, pn, ft);
+        // the pass needs the scale factor only (p is formed at the commit)
+        return_macro<R, sizeof(R) == 4 ? 1 : 2>(P, e, ht, pn, t, pn, ft);
         if (MODE == kIter) {
           if (dout) {
 #pragma unroll
@@ -690,6 +696,9 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
               // tau(e^i) - tau(e^{i-1}) = (t - t_prev) - A0 (e^i - e^{i-1}).
               R ae = a0 * de9[i] + b0 * de9[j];
               if (k == l) ae += c.ref.lam * trd;
+              // manufactured source (eq. manufactured_polarization_stress); it
+              // cancels in the increment form
+              if (sv && !dout) ae += sv[i];
               zr[2 * i] = (t[i] - (dout ? to : tms[i])) - ae;
             }
           }
@@ -708,6 +717,7 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
               const int i = 3 * k + l, j = 3 * l + k;
               R ae = a0 * de9[i] + b0 * de9[j];
               if (k == l) ae += c.ref.lam * trd;
+              if (sv) ae += sv[i];
               zr[2 * i] = (t[i] - tms[i]) - ae;
             }
           }
@@ -744,7 +754,7 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
 #pragma unroll
         for (int q = 0; q < 9; ++q) g[q] = (MODE == kIter) ? (din ? go[q] : c.G[q]) + dg9[q] : go[q];
         double qn = pq.y;
-        return_micro<R>(P, g, hm, qn, m, qn, fm);
+        return_micro<R, sizeof(R) == 4 ? 1 : 2>(P, g, hm, qn, m, qn, fm);
         if (MODE == kIter) {
           if (dout) {
 #pragma unroll
@@ -764,6 +774,7 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
               dm += d4 * d4;
               R bg = c.ref.beta * dg9[i] + c.ref.gamma * dg9[j];
               if (k == l) bg += c.ref.alpha * trd;
+              if (sv && !dout) bg += sv[9 + i];
               zr[2 * (9 + i)] = (m[i] - (dout ? mo : tms[9 + i])) - bg;
             }
           }
@@ -782,6 +793,7 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
               const int i = 3 * k + l, j = 3 * l + k;
               R bg = c.ref.beta * dg9[i] + c.ref.gamma * dg9[j];
               if (k == l) bg += c.ref.alpha * trd;
+              if (sv) bg += sv[9 + i];
               zr[2 * (9 + i)] = (m[i] - tms[9 + i]) - bg;
             }
           }

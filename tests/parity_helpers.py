@@ -18,7 +18,9 @@ def compare_solves(res, ref, tol_hom, tol_fields=None, h=1.0):
     scaleM = max(np.abs(ref["M"]).max(), h * scaleT)
     assert np.abs(res["T"] - ref["T"]).max() <= tol_hom * scaleT
     assert np.abs(res["M"] - ref["M"]).max() <= tol_hom * scaleM
-    scales = {"P": np.abs(ref["P"]).max(), "Q": max(np.abs(ref["Q"]).max(), np.abs(ref["P"]).max()),
+    # Q (a plastic curvature, 1 / length) is floored by its dimensional
+    # partner P / h, as M is by h T
+    scales = {"P": np.abs(ref["P"]).max(), "Q": max(np.abs(ref["Q"]).max(), np.abs(ref["P"]).max() / h),
               "Teq": np.abs(ref["Teq"]).max(), "Meq": max(np.abs(ref["Meq"]).max(), h * np.abs(ref["Teq"]).max())}
     for k, sc in scales.items():
         assert np.abs(res[k] - ref[k]).max() <= tol_hom * max(sc, 1e-300), k

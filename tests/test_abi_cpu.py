@@ -70,6 +70,17 @@ def test_validation_without_gpu(lib_path):
     assert M.mp_validate(dict(p, time=t))[0] == 1
     # gamma == beta is admitted (the skew couple stress then vanishes)
     assert (p["phases"]["beta"] == p["phases"]["gamma"]).all()
+    # a manufactured source needs both its fields, finite
+    nsrc = np.zeros((len(p["time"]),) + p["phase"].shape + (3, 3))
+    assert M.mp_validate(dict(p, tau_m=nsrc, mu_m=nsrc))[0] == 0
+    st, msg = M.mp_validate(dict(p, tau_m=nsrc))
+    assert st == 1 and "together" in msg
+    bad = nsrc.copy()
+    bad[2, 0, 0, 0, 1, 1] = np.nan
+    assert M.mp_validate(dict(p, tau_m=nsrc, mu_m=bad))[0] == 1
+    # precision 0, 1 and 2 are the accepted arithmetics
+    assert M.mp_validate(p, precision=2)[0] == 0
+    assert M.mp_validate(p, precision=3)[0] == 1
 
 
 def test_no_cpu_fallback(lib_path):

@@ -18,7 +18,12 @@ is used):
   (and likewise for the other fields under other loads).  Each denominator is
   floored by its dimensional partner through the voxel size h:
       den_e = max(|<e>|, h |<gamma>|),   den_gamma = max(|<gamma>|, |<e>| / h),
-      den_t = max(|<t>|, |<m>| / h),     den_m = max(|<m>|, h |<t>|).
+      den_t = max(|<t>|, |<m>| / h),     den_m = max(|<m>|, h |<t>|),
+  where, so that a cyclic load passing through a zero mean (the unloaded state
+  of Sec. 3.2, or a mean stress changing sign) keeps a finite measure, each
+  |<a>| is the larger of the field's mean norm now and the largest one it
+  reached at any earlier converged step of the load path (the scale of the
+  loading history; zero at the first step).
   A zero numerator over a zero denominator counts as zero.
 * divergence: a non-finite error, or one above ``div_limit`` (default 1e6),
   stops the solve with status 'diverged'; more than ``max_iter`` iterations in
@@ -85,12 +90,16 @@ def _norm(V):
     return np.sqrt(np.einsum("...kl,...kl->...", V, V))
 
 
-def error_measure(new, old, kind, h):
+def error_measure(new, old, kind, h, history=None):
     """eq. err with eq. err_local ('local') or eq. err_average ('average').
 
-    ``new`` / ``old``: dicts with fields 'e', 't', 'g', 'm' (N3, N2, N1, 3, 3).
+    ``new`` / ``old``: dicts with fields 'e', 't', 'g', 'm' (N3, N2, N1, 3, 3);
+    ``history``: the largest ||<a>|| of each field at earlier converged steps
+    (the denominator floors of the module docstring), or None.
     Returns (err, per-field dict)."""
-    means = {a: _norm(new[a].mean(axis=(0, 1, 2))) for a in ("e", "t", "g", "m")}
+    hist = history or {}
+    # each field's magnitude: its mean now or the largest earlier one
+    means = {a: max(_norm(new[a].mean(axis=(0, 1, 2))), hist.get(a, 0.0)) for a in ("e", "t", "g", "m")}
     den = {
         "e": max(means["e"], h * means["g"]),
         "g": max(means["g"], means["e"] / h),
@@ -195,6 +204,7 @@ def solve(problem, lockstep_iters=None, source=None, keep_fields=False, div_limi
     hist = dict(e=z9.copy(), g=z9.copy(), t=z9.copy(), m=z9.copy(),
                 p=np.zeros(shape), q=np.zeros(shape))
     committed = [dict(e=z9.copy(), g=z9.copy())]  # converged e, gamma per step (s = 0 first)
+    scale = dict(e=0.0, t=0.0, g=0.0, m=0.0)       # largest ||<a>|| of the converged steps so far
 
     res = dict(T=[], M=[], Eavg=[], Gavg=[], P=[], Q=[], Teq=[], Meq=[], err=[], iters=[],
                err_history=[], err_parts=[], status="ok", failed_step=-1, fields=[])
@@ -230,7 +240,7 @@ def solve(problem, lockstep_iters=None, source=None, keep_fields=False, div_limi
                 e_new, g_new, hist["e"], hist["g"], hist["t"], hist["m"], hist["p"], hist["q"],
                 pm, phases)
             err, parts = error_measure(dict(e=e_new, t=t_new, g=g_new, m=m_new),
-                                       dict(e=e, t=t, g=g, m=m), kind, h)
+                                       dict(e=e, t=t, g=g, m=m), kind, h, scale)
             e, g, t, m, p, q = e_new, g_new, t_new, m_new, p_new, q_new
             it += 1
             errs.append(err)
@@ -251,6 +261,8 @@ def solve(problem, lockstep_iters=None, source=None, keep_fields=False, div_limi
         avg = averages(hist, pm, phases)
         for k, v in avg.items():
             res[k].append(v)
+        for a, key in (("e", "Eavg"), ("t", "T"), ("g", "Gavg"), ("m", "M")):
+            scale[a] = max(scale[a], float(_norm(avg[key])))
         if keep_fields:
             res["fields"].append({k: v.copy() for k, v in hist.items()})
         if res["status"] != "ok":

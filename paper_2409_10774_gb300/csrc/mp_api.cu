@@ -325,7 +325,7 @@ mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
   if ((s = dalloc(ctx, r->prev, sizeof(R) * 20 * (size_t)c.nvox)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->hist, sizeof(R) * 20 * (size_t)c.nvox)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->status, sizeof(int) * 4)) != MP_OK) return s;
-  if ((s = dalloc(ctx, r->tmean, sizeof(double) * 18)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->tmean, sizeof(double) * kCellScalars)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->pq, sizeof(double) * 2 * (size_t)c.nvox)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->elast, sizeof(R) * 18 * (size_t)c.nvox)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->phase, sizeof(uint16_t) * (size_t)c.nvox)) != MP_OK) return s;

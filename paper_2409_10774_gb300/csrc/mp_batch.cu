@@ -181,7 +181,7 @@ struct ArenaLayout {
     phases = put(sizeof(PhaseDev<R>) * q.phases.size());
     for (int a = 0; a < 3; ++a) tw[a] = put(sizeof(cpx<R>) * q.n[a]);
     status = put(sizeof(int) * 4);
-    tmean = put(sizeof(double) * 18);
+    tmean = put(sizeof(double) * kCellScalars);
     ipart = put(sizeof(double) * kErrPartials * (size_t)items_a);
     apart = put(sizeof(double) * kAvgPartials * chunks);
     rows = put(sizeof(double) * kAvgPartials * (size_t)q.n_steps);
@@ -487,7 +487,7 @@ class Engine {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(b + A.phases, ph.data(), sizeof(PhaseDev<R>) * ph.size(), cudaMemcpyHostToDevice, st_);
     if (e == cudaSuccess) e = cudaMemsetAsync(b + A.status, 0, sizeof(int) * 4, st_);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b + A.tmean, 0, sizeof(double) * 18, st_);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b + A.tmean, 0, sizeof(double) * kCellScalars, st_);
     if (e == cudaSuccess && fresh) e = cudaMemsetAsync(s.rows, 0, sizeof(double) * kAvgPartials * q->n_steps, st_);
     std::vector<R> src_host;
     if (!q->tau_m.empty()) {
@@ -767,7 +767,7 @@ int migrate(Engine<RA>& from, Engine<RB>& to) {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dst.c.pq, src.c.pq, sizeof(double) * 2 * nv, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(dst.c.tmean, src.c.tmean, sizeof(double) * 18, cudaMemcpyDeviceToDevice, st);
+      e = cudaMemcpyAsync(dst.c.tmean, src.c.tmean, sizeof(double) * kCellScalars, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dst.rows, src.rows, sizeof(double) * kAvgPartials * q.n_steps, cudaMemcpyDeviceToDevice,
                           st);

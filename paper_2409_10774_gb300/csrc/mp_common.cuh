@@ -107,7 +107,10 @@ struct CellDev {
   // delta_in: the transformed field is e^{i+1} - e^i (else e^{i+1} - E);
   // delta_out: the polarization written is tau(e^i) - tau(e^{i-1}) (else tau - tau_c).
   int delta_in, delta_out;
-  double* tmean;          // [18] <t>, <m> of the last iteration (constants subtracted before transforms)
+  double* tmean;          // [kCellScalars]: <t>, <m> of the last iteration (18 constants subtracted
+                          // before the transforms), then the loading-history magnitudes of the error
+                          // measure: the largest ||<e>||, ||<t>||, ||<gamma>||, ||<m>|| of the
+                          // converged increments so far
   int predict;            // commit: write the next increment's predictor
   double ratio;           // commit: (t_{n+1} - t_n) / (t_n - t_{n-1})
   // Manufactured source of the current increment ([nvox][18]: t^m - <t^m>,
@@ -150,6 +153,8 @@ struct Work {
 // Number of doubles in one block partial of the iteration error reduction:
 // 4 maxima of |delta a|, 4 sums of |delta a|, 36 sums of e, t, gamma, m.
 constexpr int kErrPartials = 44;
+// Per-cell scalars kept on the device between launches (CellDev::tmean).
+constexpr int kCellScalars = 22;
 // Number of doubles in one block partial of the commit reduction:
 // T (9), M (9), <e> (9), <gamma> (9), P, Q, T_eq, M_eq.
 constexpr int kAvgPartials = 40;

@@ -988,7 +988,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
 // eq. err with eq. err_local (max) or eq. err_average (mean).  Denominators
 // ||<a>|| are floored by their dimensional partner through the voxel size h
 // (den_e >= h |<gamma>|, den_gamma >= |<e>| / h, den_t >= |<m>| / h,
-// den_m >= h |<t>|), since ||<gamma>|| = 0 whenever the mean curvature is zero.
+// den_m >= h |<t>|), since ||<gamma>|| = 0 whenever the mean curvature is zero,
+// each ||<a>|| taken as the larger of its value now and the largest of the
+// converged increments so far (a cyclic load passes through zero means).
 // out[0] = err, out[1..4] = err_e, err_t, err_gamma, err_m, out[5] = status.
 template <class R>
 __device__ void finish_err(const CellDev<R>& c, const double* s, int err_kind, double* out) {
@@ -1029,6 +1031,12 @@ __device__ void finish_err(const CellDev<R>& c, const double* s, int err_kind, d
       ne += me[q] * me[q]; ng += mg[q] * mg[q]; nt += mt[q] * mt[q]; nm += mm[q] * mm[q];
     }
     ne = sqrt(ne); ng = sqrt(ng); nt = sqrt(nt); nm = sqrt(nm);
+    // magnitudes: the means now or, if larger, the largest of the converged
+    // increments so far (a cyclic load passing through a zero mean)
+    ne = fmax(ne, c.tmean[18]);
+    nt = fmax(nt, c.tmean[19]);
+    ng = fmax(ng, c.tmean[20]);
+    nm = fmax(nm, c.tmean[21]);
     const double h = c.h;
     const double den[4] = {fmax(ne, h * ng), fmax(nt, nm / h), fmax(ng, ne / h), fmax(nm, h * nt)};
     double err = 0.0;
@@ -1241,13 +1249,29 @@ __global__ void __launch_bounds__(256) k_commit(CellDev<R> c0, Work<R> w, double
   }
 }
 
+// The loading-history magnitudes of the error measure (cell scalars 18..21)
+// after a committed increment whose averages are row[0..35] (T, M, <e>, <gamma>).
+__device__ __forceinline__ void update_history(const double* row, double* scalars) {
+  double n[4] = {0.0, 0.0, 0.0, 0.0};  // ||<e>||, ||T||, ||<gamma>||, ||M||
+  for (int q = 0; q < 9; ++q) {
+    n[0] += row[18 + q] * row[18 + q];
+    n[1] += row[q] * row[q];
+    n[2] += row[27 + q] * row[27 + q];
+    n[3] += row[9 + q] * row[9 + q];
+  }
+  for (int a = 0; a < 4; ++a) scalars[18 + a] = fmax(scalars[18 + a], sqrt(n[a]));
+}
+
 // Sum of the commit partials in a fixed order, divided by the voxel count.
-__global__ void k_reduce_avg(const double* partials, int nparts, double inv_nvox, double* out) {
+__global__ void k_reduce_avg(const double* partials, int nparts, double inv_nvox, double* out, double* scalars) {
+  __shared__ double row[kAvgPartials];
   if (threadIdx.x < kAvgPartials) {
     double s = 0.0;
     for (int b = 0; b < nparts; ++b) s += partials[(long long)b * kAvgPartials + threadIdx.x];
-    out[threadIdx.x] = s * inv_nvox;
+    out[threadIdx.x] = row[threadIdx.x] = s * inv_nvox;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) update_history(row, scalars);
 }
 
 // One block per entry: the cell's chunk records in chunk order -> c.avg_out.
@@ -1256,12 +1280,15 @@ __global__ void k_reduce_avg_multi(Work<R> w) {
   __shared__ CellDev<R> cs;
   load_cell(cs, w.cells + w.act[blockIdx.x]);
   __syncthreads();
+  __shared__ double row[kAvgPartials];
   if (threadIdx.x < kAvgPartials) {
     const long long n = (cs.nvox + 255) / 256;
     double s = 0.0;
     for (long long b = 0; b < n; ++b) s += cs.apart[b * kAvgPartials + threadIdx.x];
-    cs.avg_out[threadIdx.x] = s * cs.inv_nvox;
+    cs.avg_out[threadIdx.x] = row[threadIdx.x] = s * cs.inv_nvox;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) update_history(row, cs.tmean);
 }
 
 // Final-state fields in FP64: e, gamma from `src` (prev or elast), t = h_t + A e,
@@ -1467,7 +1494,7 @@ template <class R>
 cudaError_t launch_commit(const LaunchCfg& L, const CellDev<R>& c, double* partials, double* avg_out,
                           cudaStream_t st) {
   k_commit<R, false><<<L.grid_v, 256, kCommitSmem, st>>>(c, Work<R>{}, partials);
-  k_reduce_avg<<<1, 64, 0, st>>>(partials, L.grid_v, c.inv_nvox, avg_out);
+  k_reduce_avg<<<1, 64, 0, st>>>(partials, L.grid_v, c.inv_nvox, avg_out, c.tmean);
   return cudaGetLastError();
 }
 

@@ -39,7 +39,7 @@ constexpr int kLines = 18;         // components per spectral point
 constexpr int kSpecThreads = 288;  // 18 lines x 16 butterflies
 constexpr int kPhaseItems = kN;    // items per phase and plane (z or ky values)
 constexpr int kTile = kN * kLines; // complex values of one column tile
-constexpr int kPieces = kN * kLines * 8 / 16;  // 16-byte pieces of a tile
+constexpr int kPieces = kN * kLines * 8 / 16;  // 16-byte pieces of a tile (9 per point)
 
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
   int v;
@@ -62,11 +62,6 @@ __device__ __forceinline__ void cp_async_cg16(void* dst_smem, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
                "l"(src)
                : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ void stcg(cpx<float>* p, cpx<float> v) {
@@ -105,35 +100,6 @@ __device__ __forceinline__ cpx<float>* column(const CellDev<float>& c, const Ite
   return c.spec + ((long long)q.idx * c.n2 * c.kx + q.g) * kLines;
 }
 
-// Asynchronous copy of an item's column into a shared-memory tile laid out
-// as the spectrum stores a point ([point][18 lines], 144 bytes apart): 16-byte
-// pieces, several per thread, completion through the thread's copy groups.
-__device__ __forceinline__ void issue_column(const CellDev<float>& c, const Item& q, cpx<float>* tile) {
-  long long stride;
-  const cpx<float>* col = column(c, q, stride);
-  const char* src = reinterpret_cast<const char*>(col);
-  char* dst = reinterpret_cast<char*>(tile);
-  for (int k = threadIdx.x; k < kPieces; k += kSpecThreads) {
-    const int pt = k / 9, piece = k - pt * 9;
-    cp_async_cg16(dst + pt * 144 + piece * 16, src + (long long)pt * stride * 8 + piece * 16);
-  }
-}
-
-// Stage one of a 256-point transform on the tile: thread (c, j) takes points
-// j + 16 r (r < 16) of line c, forms their 16-point DFT and, once every
-// thread has read its inputs, writes output r to position 16 j + r.
-template <int DIR>
-__device__ __forceinline__ void stage1(cpx<float>* w, int c, int j) {
-  cpx<float> v[16];
-#pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = w[(j + 16 * r) * kLines + c];
-  dft16<float, DIR>(v);
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < 16; ++r) w[(16 * j + r) * kLines + c] = v[r];
-  __syncthreads();
-}
-
 // Stage two: thread (c, j) takes positions 16 r + j of line c, multiplies
 // position r by W_256^(r j) (conjugated for the inverse) and forms the 16-point
 // DFT; output k is point j + 16 k of the transformed line.
@@ -145,32 +111,98 @@ __device__ __forceinline__ void stage2(const cpx<float>* w, const cpx<float>* tw
   dft16<float, DIR>(v);
 }
 
+// ------------------------------------------------------------------ pipeline
+// Warp-specialised blocks: warps 0-8 (288 threads) transform tiles, warp 9
+// fetches work.  The producer warp takes the next item from the queue, waits
+// (bounded) until the items it depends on have finished, and copies its
+// column into a free tile slot with 16-byte asynchronous copies whose
+// completion is signalled on the slot's "full" mbarrier; the consumer warps
+// wait on that barrier, transform the tile, store their results, signal the
+// item's completion counter and release the slot through its "empty" barrier.
+// Consumers never wait for the queue or for other blocks, so their barriers
+// only order work within the tile.
+constexpr int kStages = 3;
+constexpr int kConsumers = kSpecThreads;           // 9 warps
+constexpr int kBlock = kSpecThreads + 32;          // + the producer warp
+constexpr int kTimeoutSpins = 1 << 22;
+
+struct SlotInfo {
+  int phase, g, idx, last;  // last != 0: no more items for this block
+};
+
+__device__ __forceinline__ uint32_t sptr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mb_init(uint64_t* b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sptr(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sptr(b)) : "memory");
+}
+// arrive on b once all of this thread's earlier cp.async copies are complete
+__device__ __forceinline__ void mb_arrive_cp_async(uint64_t* b) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(sptr(b)) : "memory");
+}
+__device__ __forceinline__ bool mb_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(sptr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of b; gives up early once a failure is recorded.
+__device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t parity, const int* status) {
+  for (int i = 0; i < kTimeoutSpins; ++i) {
+    if (mb_try(b, parity)) return true;
+    if ((i & 255) == 255 && ld_acquire_gpu(status) != 0) return false;
+    if (i > 256) __nanosleep(64);
+  }
+  return false;
+}
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory"); }
+
+// The in-tile transforms of the consumers: the same stages as above with the
+// consumers' named barrier in place of __syncthreads.
 template <int DIR>
-__device__ __forceinline__ void y_compute(const CellDev<float>& c, const Item& q, cpx<float>* w, const cpx<float>* tw,
+__device__ __forceinline__ void stage1_c(cpx<float>* w, int c, int j) {
+  cpx<float> v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = w[(j + 16 * r) * kLines + c];
+  dft16<float, DIR>(v);
+  consumer_sync();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) w[(16 * j + r) * kLines + c] = v[r];
+  consumer_sync();
+}
+
+template <int DIR>
+__device__ __forceinline__ void y_consume(const CellDev<float>& c, const Item& q, cpx<float>* w, const cpx<float>* tw,
                                           int line, int j) {
   long long stride;
   cpx<float>* col = column(c, q, stride) + line;
-  stage1<DIR>(w, line, j);
+  stage1_c<DIR>(w, line, j);
   cpx<float> v[16];
   stage2<DIR>(w, tw, line, j, v);
 #pragma unroll
   for (int k = 0; k < 16; ++k) stcg(col + (long long)(j + 16 * k) * stride, v[k]);
 }
 
-__device__ __forceinline__ void z_compute(const CellDev<float>& c, const Item& q, cpx<float>* w, const cpx<float>* tw,
+__device__ __forceinline__ void z_consume(const CellDev<float>& c, const Item& q, cpx<float>* w, const cpx<float>* tw,
                                           int line, int j) {
   long long stride;
   cpx<float>* col = column(c, q, stride) + line;
   const int ky = q.idx, kx = q.g;
-  stage1<-1>(w, line, j);
+  stage1_c<-1>(w, line, j);
   {
     cpx<float> v[16];
     stage2<-1>(w, tw, line, j, v);
-    __syncthreads();  // every thread has read its stage-two inputs
+    consumer_sync();  // every consumer has read its stage-two inputs
 #pragma unroll
     for (int k = 0; k < 16; ++k) w[(j + 16 * k) * kLines + line] = v[k];
   }
-  __syncthreads();
+  consumer_sync();
   // Green operator at each point kz of the column (one thread per point)
   const int kz = threadIdx.x;
   if (kz < kN) {
@@ -187,8 +219,8 @@ __device__ __forceinline__ void z_compute(const CellDev<float>& c, const Item& q
       green_point<float>(c.ref, x1, x2, x3, pt, (float)c.inv_nvox);
     }
   }
-  __syncthreads();
-  stage1<+1>(w, line, j);
+  consumer_sync();
+  stage1_c<+1>(w, line, j);
   cpx<float> v[16];
   stage2<+1>(w, tw, line, j, v);
 #pragma unroll
@@ -197,96 +229,97 @@ __device__ __forceinline__ void z_compute(const CellDev<float>& c, const Item& q
 
 // ctl[0]: work-queue head; ctl[1 + p * KX + g]: finished items of phase p
 // (0 = Y forward, 1 = Z) of plane g.  Zeroed before every launch.
-//
-// Each block keeps two column tiles: while it transforms the current item in
-// one, the next item's column is already being copied into the other (when
-// that item's inputs are complete; otherwise the copy is issued after the
-// current item, which may be one the next item waits for).
-__global__ void __launch_bounds__(kSpecThreads, 3) k_spectral(CellDev<float> c, int* ctl) {
+__global__ void __launch_bounds__(kBlock, 2) k_spectral(CellDev<float> c, int* ctl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<float>* tiles = reinterpret_cast<cpx<float>*>(smem_raw);  // [2][kTile]
-  cpx<float>* tw = tiles + 2 * kTile;                            // W_256^k (the y and z tables coincide)
-  __shared__ long long item_s;
-  __shared__ int ready_s;
-  const int line = threadIdx.x % kLines, j = threadIdx.x / kLines;
+  cpx<float>* tiles = reinterpret_cast<cpx<float>*>(smem_raw);                 // [kStages][kTile]
+  cpx<float>* tw = tiles + kStages * kTile;                                     // W_256^k (y and z alike)
+  uint64_t* full = reinterpret_cast<uint64_t*>(tw + kN);                       // [kStages]
+  uint64_t* empty = full + kStages;                                             // [kStages]
+  SlotInfo* info = reinterpret_cast<SlotInfo*>(empty + kStages);               // [kStages]
   for (int k = threadIdx.x; k < kN; k += blockDim.x) tw[k] = c.py.tw[k];
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mb_init(&full[s], 33);  // the producer's 32 lanes once their copies have landed, + lane 0's slot info
+      mb_init(&empty[s], 1);  // the consumers' leader, once the tile is free
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
   const int KX = c.kx;
   const long long total = ((long long)KX + 2) * 3 * kPhaseItems;
   int* status = c.status;
-  auto dep_counter = [&](const Item& q) { return &ctl[1 + (q.phase - 1) * KX + q.g]; };
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // first item: fetch, wait for its inputs, copy
-  if (threadIdx.x == 0) {
-    long long it;
+  if (warp == kConsumers / 32) {
+    // ---------------------------------------------------------------- producer
+    for (long long k = 0;; ++k) {
+      const int s = (int)(k % kStages);
+      const uint32_t round = (uint32_t)(k / kStages);
+      // the slot's previous item has been consumed
+      if (round > 0 && !mb_wait(&empty[s], (round - 1) & 1u, status)) {
+        if (lane == 0) atomicOr(status, 1);
+        return;
+      }
+      long long it = 0;
+      Item q{};
+      if (lane == 0) {
+        do {  // skip the empty slots of the first and last super-steps
+          it = atomicAdd(&ctl[0], 1);
+          q = decode(it, KX);
+        } while (it < total && !q.valid);
+        if (it < total && q.phase > 0 &&
+            !wait_count(&ctl[1 + (q.phase - 1) * KX + q.g], kPhaseItems, status)) {
+          atomicOr(status, 1);
+          it = total;
+        }
+        info[s] = SlotInfo{q.phase, q.g, q.idx, it >= total ? 1 : 0};
+      }
+      it = __shfl_sync(0xffffffffu, it, 0);
+      __syncwarp();
+      if (it < total) {
+        q = decode(it, KX);
+        long long stride;
+        const char* src = reinterpret_cast<const char*>(column(c, q, stride));
+        char* dst = reinterpret_cast<char*>(tiles + s * kTile);
+        for (int p = lane; p < kPieces; p += 32) {
+          const int pt = p / 9, piece = p - pt * 9;
+          cp_async_cg16(dst + pt * 144 + piece * 16, src + (long long)pt * stride * 8 + piece * 16);
+        }
+      }
+      if (lane == 0) mb_arrive(&full[s]);  // releases the slot info written above
+      mb_arrive_cp_async(&full[s]);        // (an item-less slot completes at once)
+      if (it >= total) return;
+    }
+  }
+  // ------------------------------------------------------------------ consumers
+  const int line = threadIdx.x % kLines, j = threadIdx.x / kLines;
+  for (long long k = 0;; ++k) {
+    const int s = (int)(k % kStages);
+    const uint32_t round = (uint32_t)(k / kStages);
+    if (!mb_wait(&full[s], round & 1u, status)) {
+      if (threadIdx.x == 0) atomicOr(status, 1);
+      return;
+    }
+    const SlotInfo si = info[s];
+    if (si.last) return;
     Item q;
-    do {  // skip the empty slots of the first super-steps
-      it = atomicAdd(&ctl[0], 1);
-      q = decode(it, KX);
-    } while (it < total && !q.valid);
-    bool ok = true;
-    if (it < total && q.phase > 0) {
-      ok = wait_count(dep_counter(q), kPhaseItems, status);
-      if (!ok) atomicOr(status, 1);
-      __threadfence();
-    }
-    item_s = ok ? it : total;
-  }
-  __syncthreads();
-  long long cur = item_s;
-  int b = 0;
-  if (cur < total) issue_column(c, decode(cur, KX), tiles);
-  cp_async_commit();
-  while (cur < total) {
-    const Item q = decode(cur, KX);
-    // next item: fetch it and, when its inputs are complete, start its copy
+    q.phase = si.phase;
+    q.g = si.g;
+    q.idx = si.idx;
+    q.valid = true;
+    cpx<float>* w = tiles + s * kTile;
+    if (q.phase == 0) y_consume<-1>(c, q, w, tw, line, j);
+    else if (q.phase == 1) z_consume(c, q, w, tw, line, j);
+    else y_consume<+1>(c, q, w, tw, line, j);
+    consumer_sync();  // the item's stores are issued and its tile is read
     if (threadIdx.x == 0) {
-      long long it;
-      Item n;
-      do {
-        it = atomicAdd(&ctl[0], 1);
-        n = decode(it, KX);
-      } while (it < total && !n.valid);
-      int ready = 1;
-      if (it < total && n.phase > 0) {
-        ready = ld_acquire_gpu(dep_counter(n)) >= kPhaseItems;
-        if (ready) __threadfence();
-      }
-      item_s = it;
-      ready_s = ready;
-    }
-    __syncthreads();
-    const long long nxt = item_s;
-    const bool ready = ready_s != 0;
-    cpx<float>* wcur = tiles + b * kTile;
-    cpx<float>* wnxt = tiles + (b ^ 1) * kTile;
-    if (nxt < total && ready) issue_column(c, decode(nxt, KX), wnxt);
-    cp_async_commit();
-    cp_async_wait<1>();  // the current item's copy (the older group)
-    __syncthreads();
-    if (q.phase == 0) y_compute<-1>(c, q, wcur, tw, line, j);
-    else if (q.phase == 1) z_compute(c, q, wcur, tw, line, j);
-    else y_compute<+1>(c, q, wcur, tw, line, j);
-    __syncthreads();  // the item's stores are issued and its tile is free
-    if (q.phase < 2 && threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(&ctl[1 + q.phase * KX + q.g], 1);
-    }
-    if (nxt < total && !ready) {
-      // the next item waits (bounded) for its inputs, then copies
-      if (threadIdx.x == 0) {
-        const Item n = decode(nxt, KX);
-        const bool ok = wait_count(dep_counter(n), kPhaseItems, status);
-        if (!ok) atomicOr(status, 1);
+      if (q.phase < 2) {
         __threadfence();
+        atomicAdd(&ctl[1 + q.phase * KX + q.g], 1);
       }
-      __syncthreads();
-      issue_column(c, decode(nxt, KX), wnxt);
-      cp_async_commit();
+      mb_arrive(&empty[s]);
     }
-    cur = nxt;
-    b ^= 1;
   }
-  cp_async_wait<0>();
 }
 
 }  // namespace
@@ -297,20 +330,21 @@ bool spectral_fused_ok(const CellDev<float>& c) {
   return c.n1 >= 2 && c.n2 == kN && c.n3 == kN && c.kx == c.n1 / 2;
 }
 
-constexpr size_t kSpecSmem = (2 * (size_t)kTile + kN) * sizeof(cpx<float>);
+constexpr size_t kSpecSmem = ((size_t)kStages * kTile + kN) * sizeof(cpx<float>) +
+                             2 * kStages * sizeof(uint64_t) + kStages * sizeof(SlotInfo);
 
 cudaError_t launch_spectral(const CellDev<float>& c, int* ctl, int nsm, cudaStream_t st) {
   static int per_sm = 0;
   if (per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(k_spectral, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpecSmem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spectral, kSpecThreads, kSpecSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spectral, kBlock, kSpecSmem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
   }
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(int) * spectral_ctl_ints(c.kx), st);
   if (e != cudaSuccess) return e;
-  k_spectral<<<per_sm * nsm, kSpecThreads, kSpecSmem, st>>>(c, ctl);
+  k_spectral<<<per_sm * nsm, kBlock, kSpecSmem, st>>>(c, ctl);
   return cudaGetLastError();
 }
 

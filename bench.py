@@ -275,49 +275,66 @@ def run_ours(args, rank, world, local_rank):
     ctx = M.Context(local_rank)
 
     # ---------------- device-resident timed run (value)
-    rve = M.Rve(ctx, prob, precision=1, stream=stream)
+    def timed_run(precision, profile, steps, warmup):
+        """K load increments of the path (wrapping around its 20 increments)
+        after W untimed ones, timed with CUDA events on the run's stream.
+        profile: per-kernel CUDA events (the host then decides each
+        fixed-point loop); otherwise the loop is decided on the device (one
+        graph launch per increment).  Returns (iterations, ms, per-kernel
+        profile, clocks)."""
+        rve = M.Rve(ctx, prob, precision=precision, stream=stream)
 
-    def advance(k):
-        """Run k load increments (wrapping around the 20-increment path) and
-        return the fixed-point iterations they took, counted per increment:
-        a reset zeroes the cell's own running total."""
-        done, iters = 0, 0
-        while done < k:
-            if rve.steps_done >= n_steps:
-                rve.reset(stream=stream)  # wrap around the 20-increment path
-            before = rve.iterations
-            st = rve.run(1, stream=stream)
-            if st != 0:
-                raise RuntimeError(f"increment failed: {M.binding.last_error(ctx.ptr)}")
-            iters += rve.iterations - before
-            done += 1
-        return iters
+        def advance(k):
+            # iterations counted per increment: a reset zeroes the cell's total
+            done, its = 0, 0
+            while done < k:
+                if rve.steps_done >= n_steps:
+                    rve.reset(stream=stream)  # wrap around the 20-increment path
+                before = rve.iterations
+                st = rve.run(1, stream=stream)
+                if st != 0:
+                    raise RuntimeError(f"increment failed: {M.binding.last_error(ctx.ptr)}")
+                its += rve.iterations - before
+                done += 1
+            return its
 
-    advance(args.warmup)
-    torch.cuda.synchronize(dev)
-    rve.profile(True)
-    rve.profile_read(reset=True)
-    sampler = ClockSampler(local_rank)
-    sampler.start()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize(dev)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    iters = advance(args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
-    clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    prof = rve.profile_read(reset=True)
-    if iters <= 0 or prof["pass_a"][1] != iters:
-        raise RuntimeError(f"timed iteration count {iters} disagrees with the pass-A launches "
-                           f"{prof['pass_a'][1]}")
-    rve.profile(False)
-    rve.close()
+        advance(warmup)
+        torch.cuda.synchronize(dev)
+        rve.profile(profile)
+        rve.profile_read(reset=True)
+        sampler = ClockSampler(local_rank)
+        sampler.start()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        its = advance(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        clk = sampler.stop()
+        prof_ = rve.profile_read(reset=True)
+        if its <= 0 or prof_["pass_a"][1] != its:
+            raise RuntimeError(f"timed iteration count {its} disagrees with the pass-A launches "
+                               f"{prof_['pass_a'][1]}")
+        rve.profile(False)
+        rve.close()
+        return its, ev0.elapsed_time(ev1), prof_, clk
+
+    iters, ms, prof, clocks = timed_run(1, True, args.steps, args.warmup)
+    # the same increments with the loop decided on the device, and with the
+    # level return in FP32 (precision 2), for comparison
+    extra = {}
+    if not args.no_variants:
+        for key, prec, prf in (("device_loop", 1, False), ("fp32_return", 2, True)):
+            it_v, ms_v, _, clk_v = timed_run(prec, prf, args.steps, args.warmup)
+            extra[key] = {"value": it_v * nvox / (ms_v / 1e3), "unit": UNIT, "ms_per_step": ms_v / args.steps,
+                          "iterations_timed": it_v, "precision": prec,
+                          "loop": "host, per-kernel events" if prf else "device (graph WHILE node)",
+                          "clocks": clk_v}
 
     ms_max, vox_it = combine_ranks(ms, float(iters) * nvox, world)
     value = vox_it / (ms_max / 1e3)
@@ -416,6 +433,7 @@ def run_ours(args, rank, world, local_rank):
         "fp64_gpu": fp64,
         "speedup_vs_fp64_gpu": (value / world / fp64["value"]) if fp64 else None,
         "fp32_vs_fp64_gpu": fp32_err,
+        "variants": extra,
         "clocks": clocks,
         "cpu_baseline": cpu_block,
     }
@@ -671,6 +689,8 @@ def main():
     ap.add_argument("--requests", type=int, default=6)
     ap.add_argument("--serve-fp64-sample", type=int, default=2)
     ap.add_argument("--no-cufft", action="store_true", help="leave the cuFFT timing out of the line")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="leave out the device-loop and FP32-return repeats of the timed increments")
     ap.add_argument("--no-batch", action="store_true", help="leave the batch sub-object out of the line")
     ap.add_argument("--no-serve", action="store_true", help="leave the serving sub-object out of the line")
     ap.add_argument("--budget-gb", type=int, default=64)

@@ -204,6 +204,19 @@ void mp_rve_destroy(mp_rve* rve);
 mp_status mp_checkpoint(mp_rve* rve, void* host_buf, size_t* bytes, void* stream);
 mp_status mp_resume(mp_rve* rve, const void* host_buf, size_t bytes, void* stream);
 
+/* Launch-schedule autotuner (on by default for a new context).  When on,
+ * mp_rve_create (and so mp_solve) times the candidate schedules of a new
+ * cell shape and precision on the cell's first load increment - pass-A rows
+ * per work item (the default, half, a quarter), and for cells with the fused
+ * spectral pass that pass or the three separate column passes - keeps the
+ * fastest, caches it in the context for later cells of the same shape and
+ * resets the cell to its zero state.  Schedules only split the work
+ * differently: results agree to rounding.  mp_rve_config writes up to n of
+ * {rows per pass-A item, fused spectral pass (1/0), pass-A grid, y grid,
+ * z grid, schedule timed or cached (1/0)}. */
+mp_status mp_set_autotune(mp_ctx* ctx, int32_t enable);
+mp_status mp_rve_config(const mp_rve* rve, int32_t* cfg, int32_t n);
+
 /* Kernel classes of the per-increment work, for launch counts and timings. */
 #define MP_KC_FFT_Y_FWD 0 /* y-direction forward transform pass                        */
 #define MP_KC_GREEN_Z 1   /* z forward + Green operator + z inverse pass                */

@@ -32,7 +32,7 @@ EXPORTED = ("mp_abi_version", "mp_create", "mp_destroy", "mp_last_error", "mp_va
             "mp_rve_profile_read", "mp_radial_return", "mp_green_apply", "mp_green_apply_static",
             "mp_rve_trace", "mp_rve_trace_read", "mp_checkpoint", "mp_resume", "mp_batch_solve",
             "mp_server_create", "mp_server_submit", "mp_server_wait",
-            "mp_server_query", "mp_server_destroy")
+            "mp_server_query", "mp_server_destroy", "mp_set_autotune", "mp_rve_config")
 MP_STATIC_SCRATCH_BYTES = 8 * 1024 * 1024
 KERNEL_CLASSES = ("fft_y_fwd", "green_z", "fft_y_inv", "pass_a", "reduce", "start", "commit", "spectral")
 
@@ -134,6 +134,8 @@ def _load():
         "mp_server_wait": (C.c_int, [V, C.c_uint64, C.c_int32]),
         "mp_server_query": (C.c_int, [V, P(mp_server_stats)]),
         "mp_server_destroy": (None, [V]),
+        "mp_set_autotune": (C.c_int, [V, C.c_int32]),
+        "mp_rve_config": (C.c_int, [V, P(C.c_int32), C.c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -325,6 +327,12 @@ class Context:
     def error(self):
         return last_error(self.ptr)
 
+    def set_autotune(self, enable=True):
+        """mp_set_autotune: time candidate launch schedules for new cell shapes."""
+        st = LIB.mp_set_autotune(self.ptr, 1 if enable else 0)
+        if st != MP_OK:
+            raise MicropolarError(st, self.error())
+
 
 # ---------------------------------------------------------------- entry points
 
@@ -425,6 +433,13 @@ class Rve:
         buf = np.zeros((max(n, 1), 7))
         LIB.mp_rve_trace_read(self.ptr, buf.ctypes.data_as(_DP), n, 1 if clear else 0)
         return buf[:n]
+
+    def config(self):
+        """The cell's launch schedule (mp_rve_config)."""
+        cfg = (C.c_int32 * 6)()
+        LIB.mp_rve_config(self.ptr, cfg, 6)
+        return {"rows_per_item": cfg[0], "fused_spectral": bool(cfg[1]), "grid_a": cfg[2], "grid_y": cfg[3],
+                "grid_z": cfg[4], "tuned": bool(cfg[5])}
 
     @property
     def steps_done(self):

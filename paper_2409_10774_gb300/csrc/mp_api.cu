@@ -1,5 +1,6 @@
 // C ABI of the micropolar FFT solver: validation, device state, and the
 // host-side load-step / fixed-point loop of Algorithm 2 around the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -297,6 +298,8 @@ struct mp_rve {
   // device-decided fixed-point loop (CUDA graph with a conditional WHILE node)
   cudaStream_t capture = nullptr;  // private stream the loop graph is captured on
   bool device_loop = true;         // false once a graph call failed (then the host decides)
+  bool use_fused = true;           // the fused spectral pass, where the cell has one (autotuner's choice)
+  bool tuned = false;              // launch schedule chosen by timing candidates
 };
 
 namespace {
@@ -359,7 +362,10 @@ mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
   r->L = make_launch_cfg<R>(c, ctx->nsm);
   c.rows_a = r->L.rows;
   c.items_a = r->L.items_a;
-  if ((s = dalloc(ctx, r->partials, sizeof(double) * kErrPartials * (size_t)r->L.grid_a)) != MP_OK) return s;
+  // per-block error partials for the largest pass-A grid any schedule can take
+  // (pass A keeps at most two blocks on an SM)
+  const size_t max_grid = std::max<size_t>((size_t)r->L.grid_a, 2 * (size_t)ctx->nsm);
+  if ((s = dalloc(ctx, r->partials, sizeof(double) * kErrPartials * max_grid)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->avgpart, sizeof(double) * kAvgPartials * (size_t)r->L.grid_v)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->errout, sizeof(double) * 8)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->steprows, sizeof(double) * kAvgPartials * (size_t)r->n_steps)) != MP_OK) return s;
@@ -397,7 +403,7 @@ cudaError_t launch_iteration_kernels(mp_rve* r, CellDev<R>& c, cudaStream_t st, 
   double* eout = reinterpret_cast<double*>(r->errout.ptr);
   cudaError_t e = cudaSuccess;
   bool fused = false;
-  if constexpr (sizeof(R) == 4) fused = r->ctl.ptr != nullptr;
+  if constexpr (sizeof(R) == 4) fused = r->use_fused && r->ctl.ptr != nullptr;
   if (fused) {
     if constexpr (sizeof(R) == 4) e = launch_spectral(c, reinterpret_cast<int*>(r->ctl.ptr), r->ctx->nsm, st);
   } else {
@@ -464,6 +470,82 @@ cudaError_t device_loop(mp_rve* r, CellDev<R>& c, cudaStream_t st, int& it, doub
   return e;
 }
 
+// Launch-schedule autotuner.  Candidates: pass A with the default rows per
+// item, half and a quarter of them (a smaller tile per block, more blocks),
+// and, for cells with a fused spectral pass, that pass or the three separate
+// column passes.  Each is timed (CUDA events) over three fixed-point
+// iterations of the cell's first load increment after one untimed; the
+// fastest is kept for the cell and cached in the context for its shape and
+// precision.  The cell is then reset to its zero state (the solve starts
+// from k_init as always).  Schedules differ only in how the work is split,
+// so results agree to rounding (the error partials are summed in another
+// order).
+template <class R>
+mp_status rve_autotune(mp_rve* r, cudaStream_t st) {
+  mp_ctx* ctx = r->ctx;
+  CellDev<R>& c = cell_of<R>(r);
+  const int rows0 = r->L.rows;
+  std::vector<int> rows_c{rows0};
+  for (int d : {2, 4})
+    if (rows0 / d >= 1 && std::find(rows_c.begin(), rows_c.end(), rows0 / d) == rows_c.end()) rows_c.push_back(rows0 / d);
+  std::vector<int> fused_c{0};
+  if (r->ctl.ptr) fused_c = {1, 0};
+  const std::array<int, 4> key{r->n[0], r->n[1], r->n[2], r->precision};
+  auto apply = [&](int rows, int fused) {
+    r->L = make_launch_cfg<R>(c, ctx->nsm, rows);
+    c.rows_a = r->L.rows;
+    c.items_a = r->L.items_a;
+    r->use_fused = fused != 0;
+  };
+  {
+    std::lock_guard<std::mutex> lock(ctx->tune_mu);
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+      apply(it->second[0], it->second[1]);
+      r->tuned = true;
+      return MP_OK;
+    }
+  }
+  if (rows_c.size() * fused_c.size() < 2) return MP_OK;
+  cudaEvent_t e0, e1;
+  MP_CK(ctx, cudaEventCreate(&e0));
+  MP_CK(ctx, cudaEventCreate(&e1));
+  set_load(c, r, 1);
+  c.src = r->src.ptr ? reinterpret_cast<const R*>(r->src.ptr) : nullptr;
+  float best = INFINITY;
+  int best_rows = rows0, best_fused = fused_c[0];
+  cudaError_t err = launch_start<R>(r->L, c, 1, st);
+  for (int fused : fused_c)
+    for (int rows : rows_c) {
+      if (err != cudaSuccess) break;
+      apply(rows, fused);
+      err = launch_iteration_kernels<R>(r, c, st, nullptr);
+      if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+      for (int k = 0; k < 3 && err == cudaSuccess; ++k) err = launch_iteration_kernels<R>(r, c, st, nullptr);
+      if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err == cudaSuccess && ms < best) {
+        best = ms;
+        best_rows = rows;
+        best_fused = fused;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  MP_CK(ctx, err);
+  apply(best_rows, best_fused);
+  // back to the zero state
+  MP_CK(ctx, cudaMemsetAsync(r->tmean.ptr, 0, r->tmean.bytes, st));
+  MP_CK(ctx, cudaMemsetAsync(r->status.ptr, 0, r->status.bytes, st));
+  MP_CK(ctx, cudaStreamSynchronize(st));
+  r->tuned = true;
+  std::lock_guard<std::mutex> lock(ctx->tune_mu);
+  ctx->tuned[key] = {best_rows, best_fused};
+  return MP_OK;
+}
+
 // One load increment s (1-based): predictor, fixed-point loop, commit.
 template <class R>
 mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
@@ -489,7 +571,7 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
       on_device = true;
       err = r->err_host[0];
       bool fused = false;
-      if constexpr (sizeof(R) == 4) fused = r->ctl.ptr != nullptr;
+      if constexpr (sizeof(R) == 4) fused = r->use_fused && r->ctl.ptr != nullptr;
       if (fused) {
         r->launches[MP_KC_SPECTRAL] += it;
       } else {
@@ -519,7 +601,7 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
       if (prof) cudaEventRecord(r->ev[2 * k + end], st);
     };
     bool fused = false;
-    if constexpr (sizeof(R) == 4) fused = r->ctl.ptr != nullptr;
+    if constexpr (sizeof(R) == 4) fused = r->use_fused && r->ctl.ptr != nullptr;
     if (fused) {
       if constexpr (sizeof(R) == 4) {
         mark(MP_KC_SPECTRAL, 0);
@@ -753,6 +835,8 @@ mp_status mp_rve_create(mp_ctx* ctx, const mp_problem* p, mp_rve** out, void* st
   for (int i = 0; i < 8; ++i) r->err_host[i] = 0.0;
   r->digest = problem_digest(p, ref);
   st = (r->precision == 0) ? rve_setup<double>(r, p, cs) : rve_setup<float>(r, p, cs);
+  if (st == MP_OK && ctx->autotune)
+    st = (r->precision == 0) ? rve_autotune<double>(r, cs) : rve_autotune<float>(r, cs);
   if (st != MP_OK) {
     rve_free(r);
     delete r;
@@ -897,6 +981,20 @@ mp_status mp_rve_run(mp_rve* r, int32_t n_steps, void* stream) {
 }
 
 int32_t mp_rve_steps_done(const mp_rve* r) { return r ? r->steps_done : 0; }
+
+mp_status mp_set_autotune(mp_ctx* ctx, int32_t enable) {
+  if (!ctx) return set_error(nullptr, MP_E_INVALID_ARG, "ctx is NULL");
+  ctx->autotune = enable != 0;
+  return MP_OK;
+}
+
+mp_status mp_rve_config(const mp_rve* r, int32_t* cfg, int32_t n) {
+  if (!r || !cfg || n < 0) return set_error(nullptr, MP_E_INVALID_ARG, "NULL argument");
+  bool fused = r->use_fused && r->ctl.ptr != nullptr;
+  const int32_t v[6] = {r->L.rows, fused ? 1 : 0, r->L.grid_a, r->L.grid_y, r->L.grid_z, r->tuned ? 1 : 0};
+  for (int i = 0; i < n && i < 6; ++i) cfg[i] = v[i];
+  return MP_OK;
+}
 
 mp_status mp_rve_profile(mp_rve* r, int32_t enable) {
   if (!r) return set_error(nullptr, MP_E_INVALID_ARG, "rve is NULL");

@@ -4,7 +4,10 @@
 // library.
 #pragma once
 
+#include <array>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -20,6 +23,11 @@ struct mp_ctx {
   mp_alloc alloc{};
   bool has_alloc = false;
   std::string last_error;
+  // launch schedules chosen by the autotuner, per (N1, N2, N3, precision):
+  // {pass-A rows per item, fused spectral pass}
+  bool autotune = true;
+  std::mutex tune_mu;
+  std::map<std::array<int, 4>, std::array<int, 2>> tuned;
 };
 
 namespace mp {

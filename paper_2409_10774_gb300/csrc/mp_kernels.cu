@@ -1680,11 +1680,12 @@ template cudaError_t launch_convert<float, double>(const float*, double*, long l
 template cudaError_t launch_convert<double, float>(const double*, float*, long long, int, cudaStream_t);
 
 template <class R>
-LaunchCfg make_launch_cfg(const CellDev<R>& c, int nsm) {
+LaunchCfg make_launch_cfg(const CellDev<R>& c, int nsm, int rows_wanted) {
   set_smem_attrs<R>();
   LaunchCfg L;
-  // rows per pass-A item: about 256 voxels per block, within the shared-memory budget
-  int rows = c.n1 >= 256 ? 1 : 256 / c.n1;
+  // rows per pass-A item: about 256 voxels per block (or as asked), within the
+  // shared-memory budget
+  int rows = rows_wanted > 0 ? rows_wanted : (c.n1 >= 256 ? 1 : 256 / c.n1);
   while (rows > 1 && smem_pass_a<R>(c.n1, rows) > kSmemBudget) rows /= 2;
   if ((long long)rows > (long long)c.n2 * c.n3) rows = (int)((long long)c.n2 * c.n3);
   L.rows = rows;
@@ -1740,7 +1741,7 @@ bool sizes_fit(int n1, int n2, int n3) {
                                                const R*, const R*, const R*, const R*, const R*,      \
                                                const R*, const double*, const double*, R*, R*,        \
                                                double*, double*, cudaStream_t);                       \
-  template LaunchCfg make_launch_cfg<R>(const CellDev<R>&, int);                                       \
+  template LaunchCfg make_launch_cfg<R>(const CellDev<R>&, int, int);                                  \
   template bool sizes_fit<R>(int, int, int);
 
 MP_INSTANTIATE(float)

@@ -14,8 +14,9 @@ struct LaunchCfg {
   int grid_v = 1;  // per-voxel kernels (init, commit, fields)
 };
 
+// rows_wanted > 0: that many rows per pass-A item (halved until the tile fits).
 template <class R>
-LaunchCfg make_launch_cfg(const CellDev<R>& c, int nsm);
+LaunchCfg make_launch_cfg(const CellDev<R>& c, int nsm, int rows_wanted = 0);
 // Whether the kernels' shared-memory tiles fit for this grid in precision R.
 template <class R>
 bool sizes_fit(int n1, int n2, int n3);

@@ -246,8 +246,14 @@ def combine_ranks(ms, voxel_iters, world):
     return float(t[0]), float(tot[0])
 
 
+def _shape(args):
+    return tuple(int(v) for v in args.shape.split(",")) if args.shape else None
+
+
 def _config(args):
-    return {"workload": f"voronoi{args.cells}-{args.n}^3", "n": args.n, "cells": args.cells,
+    shape = _shape(args)
+    name = f"voronoi{args.cells}-" + ("x".join(map(str, shape)) if shape else f"{args.n}^3")
+    return {"workload": name, "n": list(shape) if shape else args.n, "cells": args.cells,
             "increments": 20, "load": "E11 to 1%", "tol": 1e-6, "err": "local",
             "ref_medium": "mean", "fields": "fp32", "scalars": "fp64 p, q, totals",
             "l2": "no flush: the cell's device state (~5.3 GB) exceeds L2",
@@ -268,7 +274,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    prob = W.workload_voronoi(n=args.n, n_cells=args.cells)
+    prob = W.workload_voronoi(n=args.n, n_cells=args.cells, shape=_shape(args))
     n = prob["n"]
     nvox = n[0] * n[1] * n[2]
     n_steps = len(prob["time"]) - 1
@@ -439,8 +445,14 @@ def run_ours(args, rank, world, local_rank):
     }
     if not args.no_cufft:
         line["cufft"] = cufft_comparison(n)
-        line["cufft"]["ours_y_ms"] = kernels["fft_y_fwd"]["ms_per_launch"]
-        line["cufft"]["ours_green_z_ms"] = kernels["green_z"]["ms_per_launch"]
+        if kernels["spectral"]["launches"]:
+            # the fused pass does both y transforms and the z pass in one launch
+            line["cufft"]["ours_spectral_ms"] = kernels["spectral"]["ms_per_launch"]
+            line["cufft"]["library_same_work_ms"] = (2 * line["cufft"]["y_one_direction_ms"]
+                                                     + line["cufft"]["z_forward_inverse_ms"])
+        else:
+            line["cufft"]["ours_y_ms"] = kernels["fft_y_fwd"]["ms_per_launch"]
+            line["cufft"]["ours_green_z_ms"] = kernels["green_z"]["ms_per_launch"]
     if world == 1 and not args.no_batch:
         line["batch"] = batch_measure(args)
     if world == 1 and not args.no_serve:
@@ -676,6 +688,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--cells", type=int, default=200)
+    ap.add_argument("--shape", default=None,
+                    help="N1,N2,N3: the Voronoi cell on a box-shaped grid instead of n^3 (profiling cases)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")

@@ -230,11 +230,12 @@ mp_status mp_rve_config(const mp_rve* rve, int32_t* cfg, int32_t n);
 
 /* Cells whose y and z lengths are 256 (FP32 fields) run classes 0-2 as the
  * one fused launch of class 7; other cells run classes 0-2.
- * Enable / disable per-kernel CUDA-event timing of mp_rve_run's fixed-point
- * loop (events recorded on the run's stream around every launch of classes
- * 0-4 and 7).  Launch counts are kept for every class regardless. */
+ * Enable / disable per-kernel CUDA-event timing of mp_rve_run (events
+ * recorded on the run's stream around every launch of every class; the
+ * host waits for each increment's commit while enabled).  Launch counts are
+ * kept for every class regardless. */
 mp_status mp_rve_profile(mp_rve* rve, int32_t enable);
-/* Accumulated milliseconds (classes 0-4 and 7, while enabled) and launch counts
+/* Accumulated milliseconds (every class, while enabled) and launch counts
  * per class, MP_KC_COUNT entries each (either pointer may be NULL);
  * reset != 0 zeroes both afterwards. */
 mp_status mp_rve_profile_read(const mp_rve* rve, double* ms, int64_t* launches, int32_t reset);

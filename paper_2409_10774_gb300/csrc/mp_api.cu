@@ -553,7 +553,10 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
   CellDev<R>& c = cell_of<R>(r);
   set_load(c, r, s);
   c.src = r->src.ptr ? reinterpret_cast<const R*>(r->src.ptr) + (size_t)(s - 1) * (size_t)r->nvox * 18 : nullptr;
+  const bool prof_step = r->profiling;
+  if (prof_step) cudaEventRecord(r->ev[2 * MP_KC_START], st);
   MP_CK(ctx, launch_start<R>(r->L, c, s == 1 ? 1 : 0, st));
+  if (prof_step) cudaEventRecord(r->ev[2 * MP_KC_START + 1], st);
   r->launches[MP_KC_START] += (s == 1) ? 2 : 1;
   double err = 2.0 * r->tol;
   int it = 0;
@@ -674,10 +677,21 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
       predict ? (r->time[s + 1] - r->time[s]) / (r->time[s] - r->time[s - 1]) : 0.0;
   c.predict = predict ? 1 : 0;
   c.ratio = ratio;
+  if (prof_step) cudaEventRecord(r->ev[2 * MP_KC_COMMIT], st);
   MP_CK(ctx, launch_commit<R>(r->L, c, reinterpret_cast<double*>(r->avgpart.ptr),
                               reinterpret_cast<double*>(r->steprows.ptr) + (size_t)kAvgPartials * (s - 1),
                               st));
   r->launches[MP_KC_COMMIT] += 2;
+  if (prof_step) {
+    // once per increment: the start and commit launches' times (the commit
+    // class covers the commit and its averaging launch)
+    MP_CK(ctx, cudaEventRecord(r->ev[2 * MP_KC_COMMIT + 1], st));
+    MP_CK(ctx, cudaEventSynchronize(r->ev[2 * MP_KC_COMMIT + 1]));
+    for (int k : {MP_KC_START, MP_KC_COMMIT}) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r->ev[2 * k], r->ev[2 * k + 1]) == cudaSuccess) r->kernel_ms[k] += ms;
+    }
+  }
   r->err_steps.push_back(err);
   r->iters_steps.push_back(it);
   r->steps_done = s;

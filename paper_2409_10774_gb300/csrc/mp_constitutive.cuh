@@ -223,23 +223,19 @@ __device__ __forceinline__ void radial_return(const PhaseDev<R>& P, const R* e, 
   return_micro<R>(P, g, hm, qn, m, q, fm);
 }
 
-// eq_sq for a full (non-deviatoric) couple stress: m_eq^2 uses m itself.
-// (eq_sq works on any tensor; for t the caller passes the deviator.)
-
-// t_eq(t) and m_eq(m) of returned stresses, in FP64 (homogenized outputs).
+// t_eq(t) and m_eq(m) of returned stresses (eq. equiv_stress and
+// equiv_couple_stress), in the field type: for FP32 fields the stresses are
+// themselves single-precision values, and their voxel averages are summed in
+// FP64 (or compensated FP32) by the caller.
 template <class R>
-__device__ __forceinline__ void equivalents(const PhaseDev<R>& P, const R* t, const R* m,
-                                            double& teq, double& meq) {
-  double s[9], mm[9];
-  const double vol = ((double)t[0] + (double)t[4] + (double)t[8]) / 3.0;
+__device__ __forceinline__ void equivalents(const PhaseDev<R>& P, const R* t, const R* m, R& teq, R& meq) {
+  const R vol = vol_of(t[0], t[4], t[8]);
+  R s[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    s[i] = (double)t[i];
-    mm[i] = (double)m[i];
-  }
+  for (int i = 0; i < 9; ++i) s[i] = t[i];
   s[0] -= vol; s[4] -= vol; s[8] -= vol;
-  teq = sqrt(eq_sq(s, (double)P.a1, (double)P.a2, true));
-  meq = sqrt(eq_sq(mm, (double)P.b1, (double)P.b2, P.skew_m != 0));
+  teq = sqrt(eq_sq(s, P.a1, P.a2, true));
+  meq = sqrt(eq_sq(m, P.b1, P.b2, P.skew_m != 0));
 }
 
 }  // namespace mp

@@ -1194,18 +1194,36 @@ __global__ void __launch_bounds__(256) k_init(CellDev<R> c0, Work<R> w) {
 }
 
 // ------------------------------------------------------------------ commit
+// Error-free sum of two single-precision values (Knuth's TwoSum): s + err =
+// a + b exactly.  Accumulating x into (hi, lo) as hi, err = TwoSum(hi, x),
+// lo += err is compensated summation: the pair carries the running sum to
+// about 2^-48 of its magnitude, so per-thread sums of FP32 values lose
+// nothing against an FP64 accumulator at the voxel counts of one thread, at
+// six single-precision additions instead of one FP64 addition.
+__device__ __forceinline__ void two_sum_acc(float2& acc, float x) {
+  const float s = __fadd_rn(acc.x, x);
+  const float bb = __fsub_rn(s, acc.x);
+  const float err = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  acc.x = s;
+  acc.y = __fadd_rn(acc.y, err);
+}
+
 // Algorithm 2, end of a load increment: the converged iterate becomes the
 // history of Algorithm 1; homogenized sums; when c.predict, the linear-
 // extrapolation predictor of the next increment, e' = e_n + ratio (e_n - e_{n-1}).
-// Per 256-voxel chunk: sums of t (9), m (9), e (9), gamma (9), p, q, t_eq, m_eq.
+// Per 256-voxel chunk: sums of t (9), m (9), e (9), gamma (9), p, q, t_eq, m_eq
+// in that order (p and q are FP64 values, the others field-type values).
 // COLS: instead of reducing the chunk, add the thread's values to its own
-// column of `cols` ([kAvgPartials][blockDim] doubles; single-cell commit).
+// column of `cols` ([kAvgPartials][blockDim] 8-byte slots; single-cell
+// commit): FP64 columns for FP64 fields and for p, q, compensated FP32
+// (hi, lo) pairs for the field-type values of FP32 fields.
 template <class R, bool COLS>
 __device__ __forceinline__ void commit_chunk(const CellDev<R>& c, long long chunk, double* out40,
                                              double (*red)[kAvgPartials], double* cols) {
-  double acc[kAvgPartials];
+  R val[kAvgPartials];  // [36], [37] unused (p, q are FP64)
 #pragma unroll
-  for (int i = 0; i < kAvgPartials; ++i) acc[i] = 0.0;
+  for (int i = 0; i < kAvgPartials; ++i) val[i] = R(0);
+  double p = 0.0, q = 0.0;
   const long long v = chunk * 256 + threadIdx.x;
   if (threadIdx.x < 256 && v < c.nvox) {
     // records move in 16- / 8-byte pieces (they are 80 / 72 bytes apart)
@@ -1219,7 +1237,6 @@ __device__ __forceinline__ void commit_chunk(const CellDev<R>& c, long long chun
     const PhaseDev<R>& P = c.phases[(int)hr[18]];
     double2 pq = reinterpret_cast<const double2*>(c.pq)[v];
     R t[9], m[9];
-    double p, q;
     R ft, fm;
     radial_return<R>(P, e, g, hr, hr + 9, pq.x, pq.y, t, m, p, q, ft, fm);
     R ae[9], bg[9];
@@ -1227,21 +1244,16 @@ __device__ __forceinline__ void commit_chunk(const CellDev<R>& c, long long chun
     apply_B<R>(P.alpha, P.beta, P.gamma, g, bg);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      acc[i] = (double)t[i];
-      acc[9 + i] = (double)m[i];
-      acc[18 + i] = (double)e[i];
-      acc[27 + i] = (double)g[i];
+      val[i] = t[i];
+      val[9 + i] = m[i];
+      val[18 + i] = e[i];
+      val[27 + i] = g[i];
       hr[i] = t[i] - ae[i];
       hr[9 + i] = m[i] - bg[i];
     }
     store_rec(hv, hr);
     reinterpret_cast<double2*>(c.pq)[v] = make_double2(p, q);
-    double teq, meq;
-    equivalents<R>(P, t, m, teq, meq);
-    acc[36] = p;
-    acc[37] = q;
-    acc[38] = teq;
-    acc[39] = meq;
+    equivalents<R>(P, t, m, val[38], val[39]);
     if (c.predict) {
       const R ratio = (R)c.ratio;
       R* el = c.elast + v * 18;
@@ -1253,34 +1265,51 @@ __device__ __forceinline__ void commit_chunk(const CellDev<R>& c, long long chun
       store_rec(pv, pr);    // the predictor, with the last scale factors
     }
   }
+  const int bd = (int)blockDim.x;
   if constexpr (COLS) {
     // thread-private columns: no cross-thread work per chunk
+    double* dc = cols + threadIdx.x;
 #pragma unroll
-    for (int i = 0; i < kAvgPartials; ++i) cols[i * blockDim.x + threadIdx.x] += acc[i];
+    for (int i = 0; i < kAvgPartials; ++i) {
+      if (i == 36) {
+        dc[i * bd] += p;
+      } else if (i == 37) {
+        dc[i * bd] += q;
+      } else if constexpr (sizeof(R) == 4) {
+        float2* fc = reinterpret_cast<float2*>(dc + i * bd);
+        float2 a = *fc;
+        two_sum_acc(a, (float)val[i]);
+        *fc = a;
+      } else {
+        dc[i * bd] += (double)val[i];
+      }
+    }
     return;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < kAvgPartials; ++i) {
-    const double sm = shfl_sum(acc[i]);
+    const double x = (i == 36) ? p : (i == 37) ? q : (double)val[i];
+    const double sm = shfl_sum(x);
     if (lane == 0) red[warp][i] = sm;
   }
   __syncthreads();
   if (threadIdx.x < kAvgPartials) {
     double sm = 0.0;
-    for (int wq = 0; wq < (int)(blockDim.x >> 5); ++wq) sm += red[wq][threadIdx.x];
+    for (int wq = 0; wq < (bd >> 5); ++wq) sm += red[wq][threadIdx.x];
     out40[threadIdx.x] = sm;
   }
   __syncthreads();
 }
 
-// Single: each thread accumulates its voxels' values in FP64 in its own
-// shared-memory column across the block's chunks; the block folds the columns
-// once into partials[block][40] (a fixed grid gives a fixed order).  Multi:
+// Single: each thread accumulates its voxels' values in its own shared-memory
+// column across the block's chunks (FP64, or compensated FP32 pairs for the
+// values of FP32 fields); the block folds the columns once, in FP64, into
+// partials[block][40] (a fixed grid gives a fixed order).  Multi:
 // per-chunk records in each cell's apart.
 template <class R, bool MULTI>
 __global__ void __launch_bounds__(256) k_commit(CellDev<R> c0, Work<R> w, double* partials) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];  // single: [kAvgPartials][256] doubles
+  extern __shared__ __align__(16) unsigned char smem_raw[];  // single: [kAvgPartials][256] 8-byte slots
   __shared__ CellDev<R> cs;
   __shared__ double red[8][kAvgPartials];
   __shared__ double chunk_sum[kAvgPartials];
@@ -1299,8 +1328,16 @@ __global__ void __launch_bounds__(256) k_commit(CellDev<R> c0, Work<R> w, double
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = warp; i < kAvgPartials; i += nw) {
+      const bool pair = sizeof(R) == 4 && i != 36 && i != 37;  // compensated FP32 (hi, lo) column
       double sm = 0.0;
-      for (int k = lane; k < (int)blockDim.x; k += 32) sm += cols[i * blockDim.x + k];
+      for (int k = lane; k < (int)blockDim.x; k += 32) {
+        if (pair) {
+          const float2 a = reinterpret_cast<const float2*>(cols)[i * blockDim.x + k];
+          sm += (double)a.x + (double)a.y;
+        } else {
+          sm += cols[i * blockDim.x + k];
+        }
+      }
       sm = shfl_sum(sm);
       if (lane == 0) partials[(long long)blockIdx.x * kAvgPartials + i] = sm;
     }

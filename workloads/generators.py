@@ -150,9 +150,9 @@ def voronoi_seeds(n_cells, box, seed):
 
 def voronoi_map(n, seeds, scale=1.0):
     """Periodic Voronoi tessellation: each voxel gets the index of its nearest
-    seed (minimum-image distance, ties to the lowest index).  ``scale`` maps
-    seed coordinates into this grid's voxel units (1/4 for the 64^3
-    regeneration of a 256^3 cell)."""
+    seed (minimum-image distance, ties to the lowest index).  ``scale`` (one
+    number, or one per axis) maps seed coordinates into this grid's voxel
+    units (1/4 for the 64^3 regeneration of a 256^3 cell)."""
     n = tuple(int(v) for v in n)
     best = np.full((n[2], n[1], n[0]), np.inf)
     owner = np.zeros((n[2], n[1], n[0]), dtype=np.uint16)
@@ -283,19 +283,27 @@ def voronoi_phase_table(n_cells, seed):
 
 
 def workload_voronoi(n=256, n_cells=200, n_steps=20, tol=1e-6, seed=None, cell_box=256,
-                     ref_kind="mean"):
+                     ref_kind="mean", shape=None):
     """Periodic Voronoi polycrystal-like cell.  Seeds live in a box of side
     ``cell_box`` voxels; generating at ``n = cell_box / 4`` gives the
     downsampled regeneration of the same tessellation and the same cell
-    parameters."""
+    parameters.  ``shape = (N1, N2, N3)`` instead of ``n`` maps the seed box
+    onto a box-shaped grid, each axis scaled by its own N / cell_box (the same
+    grains, stretched; smaller grids of the 256^3 cell's kernels)."""
     seed = seed_for(2) if seed is None else seed
     seeds = voronoi_seeds(n_cells, cell_box, seed)
-    phase = voronoi_map((n, n, n), seeds, scale=n / cell_box)
+    if shape is None:
+        dims, scale, tag = (n, n, n), n / cell_box, f"{n}^3"
+    else:
+        dims = tuple(int(v) for v in shape)
+        scale = np.asarray(dims, dtype=np.float64) / cell_box
+        tag = "x".join(str(v) for v in dims)
+    phase = voronoi_map(dims, seeds, scale=scale)
     phases = voronoi_phase_table(n_cells, seed)
     E = np.zeros((3, 3)); E[0, 0] = 0.01
     time, Ep, Gp = ramp_path(n_steps, E)
-    return _problem((n, n, n), phase, phases, time, Ep, Gp, tol, ref_kind=ref_kind,
-                    name=f"voronoi{n_cells}-{n}^3")
+    return _problem(dims, phase, phases, time, Ep, Gp, tol, ref_kind=ref_kind,
+                    name=f"voronoi{n_cells}-{tag}")
 
 
 def workload_batch(count=512, seed=None, sizes=(16, 24, 32, 48), n_steps=10, tol=1e-6,

@@ -67,15 +67,15 @@ def _source_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel):
+def _traffic(kernel, workload="voronoi200-256^3"):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", "traffic_pass_a_voronoi256.txt")
+    the current kernel sources for this workload."""
+    path = os.path.join(ROOT, "profiles", "traffic_voronoi256.txt")
     try:
         data = json.load(open(path))
     except (OSError, ValueError):
         return None
-    if data.get("source_hash") != _source_hash():
+    if data.get("source_hash") != _source_hash() or data.get("workload") != workload:
         return None
     return data.get("bytes_per_launch", {}).get(kernel)
 
@@ -434,7 +434,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": _traffic(dom), "algorithmic_bytes_per_launch": abytes[dom]},
+                     "traffic": _traffic(dom, _config(args)["workload"]), "algorithmic_bytes_per_launch": abytes[dom]},
         "kernels": kernels,
         "fp64_gpu": fp64,
         "speedup_vs_fp64_gpu": (value / world / fp64["value"]) if fp64 else None,

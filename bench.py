@@ -645,7 +645,8 @@ def serve_measure(args):
                     "statuses": {s_: status.count(s_) for s_ in set(status)}, "clocks": clocks})
     # baseline: plain FP64 single-instance solves, one by one
     service = []
-    for r in reqs[: args.serve_fp64_sample]:
+    n_base = n_req if args.serve_fp64_sample < 0 else min(n_req, args.serve_fp64_sample)
+    for r in reqs[:n_base]:
         torch.cuda.synchronize(dev)
         t1 = time.perf_counter()
         M.mp_solve(ctx, r, precision=0)
@@ -701,7 +702,8 @@ def main():
     ap.add_argument("--fp64-sample", type=int, default=16)
     ap.add_argument("--rates", default="0.25")
     ap.add_argument("--requests", type=int, default=6)
-    ap.add_argument("--serve-fp64-sample", type=int, default=2)
+    ap.add_argument("--serve-fp64-sample", type=int, default=-1,
+                    help="requests of the plain-FP64 one-by-one baseline (-1: all of them)")
     ap.add_argument("--no-cufft", action="store_true", help="leave the cuFFT timing out of the line")
     ap.add_argument("--no-variants", action="store_true",
                     help="leave out the device-loop and FP32-return repeats of the timed increments")

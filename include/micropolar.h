@@ -246,6 +246,10 @@ mp_status mp_rve_profile_read(const mp_rve* rve, double* ms, int64_t* launches, 
  * runs one fixed-point iteration of Algorithm 2 for every cell still
  * iterating, in launches shared by all of them, and each cell leaves its
  * loop, commits and starts its next increment on its own error (eq. err).
+ * Rounds run in windows of 8 launched back to back: each cell's loop test
+ * is taken on the device after every round, a cell whose loop ended skips
+ * the window's remaining rounds, and the host reads the window's errors
+ * once (commits and starts happen between windows).
  * A cell's results are identical (bit for bit) whichever cells it shares the
  * batch with; they agree with mp_solve's to rounding (mp_solve runs
  * separately compiled single-cell forms of the kernels and sums its error
@@ -260,11 +264,11 @@ mp_status mp_rve_profile_read(const mp_rve* rve, double* ms, int64_t* launches, 
  * its tolerance (the floor set by the rounding of its FP32 transforms) continues
  * the increment in the increment form e^{i+1} = e^i - Gamma0 * (tau^i -
  * tau^{i-1}), whose transforms round relative to the change of the
- * polarization; if that sets no new low for 1024 iterations, it finishes the
+ * polarization; if that sets no new low for 128 iterations, it finishes the
  * increment in FP64 (iters_fp64).  A prescribed iteration schedule disables
  * both. */
 typedef struct mp_batch_stats {
-  int64_t rounds;              /* rounds of the FP32 and of the FP64 engine                 */
+  int64_t rounds;              /* iteration rounds of the FP32 and of the FP64 engine       */
   int64_t rounds_fp64;
   int64_t voxel_iters;         /* voxels x fixed-point iterations, all cells               */
   int64_t voxel_iters_fp64;    /* ... of them run in FP64                                  */

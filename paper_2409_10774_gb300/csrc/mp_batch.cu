@@ -6,7 +6,10 @@
 // kernels mp_solve uses (y transform, z transform + Green operator, pass A
 // with Algorithm 1, error reduction), preceded by the commits of cells whose
 // increment converged in the previous round and the starts of their next
-// increments.  Each cell decides its own loop exit from its own error, so a
+// increments.  Rounds run in windows of kRoundWindow, launched back to back
+// with each cell's loop test taken on the device (RoundCtl) and replayed on
+// the host from the window's error rows; a cell whose loop ended skips the
+// rest of its window.  Each cell decides its own loop exit from its own error, so a
 // cell's iterate sequence is exactly the one it has when solved alone: its
 // work items are processed by whichever block picks them up, but every
 // per-cell reduction (iteration error, homogenized averages) is folded from
@@ -221,13 +224,23 @@ struct Progress {
 // slowly but steadily converging cell keeps setting new lows and stays as it
 // is).  It continues in the increment form, whose transforms round relative to
 // the shrinking change of the polarization.
-// That form has no such floor above the tolerance (an increment below the
-// rounding of e leaves e unchanged and the measured change at zero), so a stall
-// there is slow convergence, which FP64 would not speed up: only a cell that
-// sets no new low for kStagnationItersDelta iterations finishes in FP64.
+// That form removes the floor of the transforms, but not the one of the FP32
+// stresses that enter the local error measure (a voxel's stress rounds at
+// ~6e-8 of its own magnitude, which at stress concentrations can reach the
+// tolerance relative to the mean): a cell that sets no new low for
+// kStagnationItersDelta iterations there finishes the increment in FP64, which
+// then takes a few to a few hundred iterations.  (Cells that converge in the
+// increment form set a new low every few iterations.)
 constexpr int kStagnationIters = 64;
-constexpr int kStagnationItersDelta = 1024;
+constexpr int kStagnationItersDelta = 128;
 constexpr double kStagnationDrop = 0.01;
+
+// Iteration rounds per window: a window's launches run back to back on the
+// device, each cell's loop test is taken there (RoundCtl) and the host
+// reads the window's error rows once.  A cell whose loop ends inside a window
+// idles for the window's remaining rounds (its commit waits for the window's
+// end), so the window stays short against the typical increment.
+constexpr int kRoundWindow = 8;
 
 template <class R>
 struct Slot {
@@ -298,9 +311,10 @@ class Engine {
     slots_.clear();
   }
 
-  // One round.  Requests whose solve ended are appended to `finished` (their
-  // results written, their arenas released).  A CUDA failure fails every
-  // resident request and returns MP_E_CUDA.
+  // One window: the host's state changes (commits, starts), then up to
+  // kRoundWindow iteration rounds.  Requests whose solve ended are appended
+  // to `finished` (their results written, their arenas released).  A CUDA
+  // failure fails every resident request and returns MP_E_CUDA.
   mp_status round(std::vector<Request*>& finished) {
     if (slots_.empty()) return MP_OK;
     ++rounds_;
@@ -359,65 +373,60 @@ class Engine {
         l_iter.push_back(i);
       }
     }
-    mp_status st = upload_and_launch(l_commit, l_init, l_start, l_iter);
+    // the window's loop control, one record per iterating cell
+    const int K = l_iter.empty() ? 1 : kRoundWindow;
+    mp_status st = ensure_meta(n);
     if (st != MP_OK) return fail_all(finished, st);
-    // decisions (Algorithm 2's loop test, per cell)
-    for (size_t k = 0; k < l_iter.size(); ++k) {
-      Slot<R>& sl = slots_[l_iter[k]];
-      Progress& g = sl.g;
+    RoundCtl* hctl = reinterpret_cast<RoundCtl*>(static_cast<unsigned char*>(h_meta_) + meta_.ctl);
+    RoundCtl* dctl = reinterpret_cast<RoundCtl*>(static_cast<unsigned char*>(d_meta_) + meta_.ctl);
+    double* derr = reinterpret_cast<double*>(static_cast<unsigned char*>(d_meta_) + meta_.err);
+    for (int i = 0; i < n; ++i) slots_[i].c.rctl = nullptr;
+    for (int i : l_iter) {
+      Slot<R>& sl = slots_[i];
+      const Progress& g = sl.g;
       const Request& q = *g.req;
-      const double* e = h_err_ + 8 * (size_t)l_iter[k];
-      g.err = e[0];
-      g.it += 1;
-      if (kFp64) g.it64 += 1;
-      if (g.delta == 1) g.delta = 2;  // this round wrote the first increment
-      voxel_iters_ += q.nvox;
       const int target = q.lockstep.empty() ? -1 : q.lockstep[g.s - 1];
-      mp_status out = MP_OK;
-      bool leave = false;
-      if (e[5] != 0.0) {
-        out = MP_E_TIMEOUT;
-        leave = true;
-      } else if (!std::isfinite(g.err) || g.err > q.div_limit) {
-        out = MP_E_DIVERGED;
-        leave = true;
-      } else {
-        const bool more = target >= 0 ? g.it < target : g.err > q.tol;
-        if (!more) leave = true;
-        else if (target < 0 && g.it >= q.max_iter) {
-          out = MP_E_NOT_CONVERGED;
-          leave = true;
-        }
+      RoundCtl& rc = hctl[i];
+      rc = RoundCtl{};
+      rc.tol = q.tol;
+      rc.div_limit = q.div_limit;
+      rc.ref_err = g.ref_err;
+      rc.drop = 1.0 - kStagnationDrop;
+      rc.rows = derr + (size_t)8 * kRoundWindow * i;
+      rc.it = g.it;
+      rc.target = target;
+      rc.max_iter = q.max_iter;
+      rc.it_ref = g.it_ref;
+      rc.stag_iters = (!kFp64 && target < 0) ? (g.delta ? kStagnationItersDelta : kStagnationIters) : 0;
+      // the first round of the increment form changes the next round's inputs
+      rc.max_rounds = (g.delta == 1) ? 1 : K;
+      sl.c.rctl = dctl + i;
+    }
+    st = upload_and_launch(l_commit, l_init, l_start, l_iter, K);
+    if (st != MP_OK) return fail_all(finished, st);
+    rounds_ += K - 1;
+    // decisions: the window's rows through Algorithm 2's loop test, per cell,
+    // in round order (the device stopped each cell at its first decision)
+    for (int i : l_iter) {
+      Slot<R>& sl = slots_[i];
+      Progress& g = sl.g;
+      const RoundCtl& rc = hctl[i];
+      const int ran = rc.rounds;
+      bool iterating = true;
+      bool agree = ran >= 1 && ran <= rc.max_rounds;
+      for (int r = 0; agree && r < ran; ++r) {
+        const double* e = h_err_ + (size_t)8 * (kRoundWindow * (size_t)i + r);
+        iterating = decide(sl, e);
+        if (!iterating && r != ran - 1) agree = false;
       }
-      if (!leave) {
-        // FP32 stagnation watch (not under a prescribed iteration schedule)
-        if (!kFp64 && target < 0) {
-          if (g.it_ref == 0 || g.err < (1.0 - kStagnationDrop) * g.ref_err) {
-            g.ref_err = g.err;
-            g.it_ref = g.it;
-          } else if (g.it - g.it_ref >= (g.delta ? kStagnationItersDelta : kStagnationIters)) {
-            if (g.delta == 0) {
-              g.delta = 1;
-              g.ref_err = g.err;
-              g.it_ref = g.it;
-              ++delta_switches_;
-            } else {
-              g.escalate = true;
-            }
-          }
-        }
-        continue;
-      }
-      g.step_status = out;
-      if (out == MP_E_TIMEOUT) {
+      if (iterating && ran < rc.max_rounds) agree = false;
+      if (!agree) {
+        // the device's and the host's loop tests took different decisions
+        g.step_status = MP_E_CUDA;
         g.failed_step = g.s;
         g.steps_done = g.s - 1;
+        g.req->message = "internal: device and host loop decisions differ";
         g.state = Progress::kFinished;
-      } else {
-        g.err_steps.push_back(g.err);
-        g.iters_steps.push_back(g.it);
-        g.iters64_steps.push_back(g.it64);
-        g.state = Progress::kCommit;
       }
     }
     // harvest
@@ -437,6 +446,72 @@ class Engine {
   }
 
  private:
+  // Algorithm 2's loop test for one cell after one iteration whose error row
+  // is e (err, four terms, status), with the FP32 stagnation watch.  Returns
+  // true while the cell keeps iterating with an unchanged schedule; false when
+  // its loop ended (it moves on to the commit, or finishes) or its schedule
+  // changes (increment form switched on, or escalation to FP64).
+  bool decide(Slot<R>& sl, const double* e) {
+    constexpr bool kFp64 = sizeof(R) == 8;
+    Progress& g = sl.g;
+    const Request& q = *g.req;
+    g.err = e[0];
+    g.it += 1;
+    if (kFp64) g.it64 += 1;
+    if (g.delta == 1) g.delta = 2;  // this round wrote the first increment
+    voxel_iters_ += q.nvox;
+    const int target = q.lockstep.empty() ? -1 : q.lockstep[g.s - 1];
+    mp_status out = MP_OK;
+    bool leave = false;
+    if (e[5] != 0.0) {
+      out = MP_E_TIMEOUT;
+      leave = true;
+    } else if (!std::isfinite(g.err) || g.err > q.div_limit) {
+      out = MP_E_DIVERGED;
+      leave = true;
+    } else {
+      const bool more = target >= 0 ? g.it < target : g.err > q.tol;
+      if (!more) {
+        leave = true;
+      } else if (target < 0 && g.it >= q.max_iter) {
+        out = MP_E_NOT_CONVERGED;
+        leave = true;
+      }
+    }
+    if (!leave) {
+      // FP32 stagnation watch (not under a prescribed iteration schedule)
+      if (!kFp64 && target < 0) {
+        if (g.it_ref == 0 || g.err < (1.0 - kStagnationDrop) * g.ref_err) {
+          g.ref_err = g.err;
+          g.it_ref = g.it;
+        } else if (g.it - g.it_ref >= (g.delta ? kStagnationItersDelta : kStagnationIters)) {
+          if (g.delta == 0) {
+            g.delta = 1;
+            g.ref_err = g.err;
+            g.it_ref = g.it;
+            ++delta_switches_;
+          } else {
+            g.escalate = true;
+          }
+          return false;
+        }
+      }
+      return true;
+    }
+    g.step_status = out;
+    if (out == MP_E_TIMEOUT) {
+      g.failed_step = g.s;
+      g.steps_done = g.s - 1;
+      g.state = Progress::kFinished;
+    } else {
+      g.err_steps.push_back(g.err);
+      g.iters_steps.push_back(g.it);
+      g.iters64_steps.push_back(g.it64);
+      g.state = Progress::kCommit;
+    }
+    return false;
+  }
+
   // Arena and device tables of the slot's request at this precision (rows
   // zeroed when fresh).
   mp_status build_slot(Slot<R>& s, bool fresh) {
@@ -533,7 +608,7 @@ class Engine {
   // Metadata block (device and pinned host mirror): the descriptor table,
   // the per-family entry lists and item prefixes, and the error rows.
   struct Meta {
-    size_t cells, act[6], pre[6], err, total;
+    size_t cells, act[6], pre[6], err, ctl, total;
   };
   Meta layout(int cap) const {
     Meta m;
@@ -546,7 +621,8 @@ class Engine {
     m.cells = put(sizeof(CellDev<R>) * cap);
     for (int f = 0; f < 6; ++f) m.act[f] = put(sizeof(int) * cap);
     for (int f = 0; f < 6; ++f) m.pre[f] = put(sizeof(long long) * (cap + 1));
-    m.err = put(sizeof(double) * 8 * cap);
+    m.err = put(sizeof(double) * 8 * kRoundWindow * cap);
+    m.ctl = put(sizeof(RoundCtl) * cap);
     m.total = o;
     return m;
   }
@@ -579,17 +655,19 @@ class Engine {
 
   enum Family { kFY = 0, kFZ, kFA, kFS, kFV, kFV0 };
 
+  // One window: the commits and starts of this round, then `rounds`
+  // iteration rounds of the cells in l_iter (each cell's loop test on the
+  // device, its RoundCtl uploaded with the descriptors), then the window's
+  // error rows and loop controls back to the host.
   mp_status upload_and_launch(const std::vector<int>& l_commit, const std::vector<int>& l_init,
-                              const std::vector<int>& l_start, const std::vector<int>& l_iter) {
+                              const std::vector<int>& l_start, const std::vector<int>& l_iter, int rounds) {
     const int n = (int)slots_.size();
     mp_status st = ensure_meta(n);
     if (st != MP_OK) return st;
     unsigned char* hb = static_cast<unsigned char*>(h_meta_);
     unsigned char* db = static_cast<unsigned char*>(d_meta_);
     h_err_ = reinterpret_cast<double*>(hb + meta_.err);
-    double* d_err = reinterpret_cast<double*>(db + meta_.err);
     CellDev<R>* hc = reinterpret_cast<CellDev<R>*>(hb + meta_.cells);
-    for (int i : l_iter) slots_[i].c.err_out = d_err + 8 * (size_t)i;
     for (int i = 0; i < n; ++i) hc[i] = slots_[i].c;
     MultiCfg<R> m;
     long long* items[6] = {&m.items_y, &m.items_z, &m.items_a, &m.items_s, &m.items_v, &m.items_v0};
@@ -627,12 +705,19 @@ class Engine {
     }
     for (int i : l_start) m.smem_a = std::max(m.smem_a, smem_pass_a<R>(slots_[i].c.n1, slots_[i].c.rows_a));
     multi_grids<R>(m, ctx_->nsm);
+    // descriptors and lists, then the loop controls (the error rows between
+    // them are device-written only)
     cudaError_t e = cudaMemcpyAsync(d_meta_, h_meta_, meta_.err, cudaMemcpyHostToDevice, st_);
+    if (e == cudaSuccess && !l_iter.empty())
+      e = cudaMemcpyAsync(db + meta_.ctl, hb + meta_.ctl, sizeof(RoundCtl) * n, cudaMemcpyHostToDevice, st_);
     if (e == cudaSuccess && !l_commit.empty()) e = launch_multi_commit<R>(m, st_);
     if (e == cudaSuccess && !l_start.empty()) e = launch_multi_start<R>(m, st_);
-    if (e == cudaSuccess && !l_iter.empty()) e = launch_multi_iteration<R>(m, st_);
+    for (int r = 0; e == cudaSuccess && !l_iter.empty() && r < rounds; ++r) e = launch_multi_iteration<R>(m, st_);
     if (e == cudaSuccess && !l_iter.empty())
-      e = cudaMemcpyAsync(h_err_, d_err, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost, st_);
+      e = cudaMemcpyAsync(h_err_, db + meta_.err, sizeof(double) * 8 * kRoundWindow * n, cudaMemcpyDeviceToHost,
+                          st_);
+    if (e == cudaSuccess && !l_iter.empty())
+      e = cudaMemcpyAsync(hb + meta_.ctl, db + meta_.ctl, sizeof(RoundCtl) * n, cudaMemcpyDeviceToHost, st_);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st_);
     if (e != cudaSuccess) {
       last_cuda_ = cudaGetErrorString(e);

@@ -74,6 +74,28 @@ struct AxisPlan {
   const cpx<R>* tw;  // table of length n (n >= 1)
 };
 
+// Loop control of one cell over a window of batched rounds: Algorithm 2's
+// convergence test (and the FP32 stagnation watch of the batched engine)
+// taken on the device.  The error reduction of every round writes the cell's
+// error row, counts the iteration and sets `stop` at the iteration where the
+// host's test would end the cell's loop or change its schedule; the later
+// rounds of the window skip a stopped cell.  The host then replays the rows
+// through the same test.
+struct RoundCtl {
+  double tol, div_limit;
+  double ref_err;    // stagnation watch: error at the last significant new low
+  double drop;       // a significant new low: err < drop * ref_err
+  double* rows;      // [max_rounds][8] the window's error rows
+  int it;            // iterations of the current increment so far
+  int target;        // prescribed iteration count of the increment, or -1
+  int max_iter;
+  int it_ref;        // iteration of the last significant new low (0: none yet)
+  int stag_iters;    // iterations without a new low that stop the window (0: no watch)
+  int max_rounds;    // rounds the window may run for this cell
+  int rounds;        // rounds run (device-written)
+  int stop;          // 1: no further round in this window (device-written)
+};
+
 // Per-cell device descriptor.
 template <class R>
 struct CellDev {
@@ -116,6 +138,9 @@ struct CellDev {
   // Manufactured source of the current increment ([nvox][18]: t^m - <t^m>,
   // m^m - <m^m>), subtracted from the polarization; NULL without a source.
   const R* src;
+  // Batched rounds: the cell's loop control for the current window (NULL
+  // outside a window; single-cell launches never set it).
+  RoundCtl* rctl;
 };
 
 // Columns per tile of the y / z passes for a transform length n: short

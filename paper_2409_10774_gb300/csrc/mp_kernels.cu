@@ -104,7 +104,10 @@ __device__ __forceinline__ void load_cell(CellDev<R>& dst, const CellDev<R>* src
 
 // Runs `body(cell, local_item)` over a launch's items: the single cell `c0`
 // (items 0..n0-1), or, for MULTI, every entry of `w` with its cell staged in
-// shared memory `cs` (reloaded when a block moves to the next cell).
+// shared memory `cs` (reloaded when a block moves to the next cell).  A cell
+// whose round control says stop (a later round of a batched window after
+// its loop ended) has its items skipped; the flag only changes between
+// launches, so every thread of the block reads the same value.
 template <class R, bool MULTI, class Body>
 __device__ __forceinline__ void for_items(const CellDev<R>& c0, long long n0, const Work<R>& w,
                                           CellDev<R>& cs, Body body) {
@@ -119,6 +122,7 @@ __device__ __forceinline__ void for_items(const CellDev<R>& c0, long long n0, co
     if (g0 >= g1) return;
     int e = find_entry(w.pre, w.n_act, g0);
     int cur = -1;
+    bool halted = false;
     for (long long g = g0; g < g1; ++g) {
       while (g >= w.pre[e + 1]) ++e;
       const int slot = w.act[e];
@@ -127,8 +131,9 @@ __device__ __forceinline__ void for_items(const CellDev<R>& c0, long long n0, co
         load_cell(cs, w.cells + slot);
         __syncthreads();
         cur = slot;
+        halted = cs.rctl != nullptr && __ldcg(&cs.rctl->stop) != 0;
       }
-      body(cs, g - w.pre[e]);
+      if (!halted) body(cs, g - w.pre[e]);
     }
   }
 }
@@ -1148,6 +1153,38 @@ __global__ void __launch_bounds__(256) k_reduce_err_loop(CellDev<R> c, const dou
 }
 
 // One block per entry: the cell's per-item partials in item order.
+// Algorithm 2's loop test for one batched cell after an iteration whose error
+// row is e (err, four terms, status), with the batched engine's FP32
+// stagnation watch; the same comparisons, in the same order and arithmetic,
+// as the host's replay of the rows.
+__device__ void round_decide(RoundCtl& rc, const double* e) {
+  const double err = e[0];
+  rc.it += 1;
+  rc.rounds += 1;
+  bool stop = false;
+  if (e[5] != 0.0) {
+    stop = true;  // a bounded wait expired
+  } else if (!isfinite(err) || err > rc.div_limit) {
+    stop = true;  // diverged
+  } else {
+    const bool more = rc.target >= 0 ? rc.it < rc.target : err > rc.tol;
+    if (!more) {
+      stop = true;  // converged, or the prescribed count reached
+    } else if (rc.target < 0 && rc.it >= rc.max_iter) {
+      stop = true;  // not converged
+    } else if (rc.stag_iters > 0) {
+      if (rc.it_ref == 0 || err < rc.drop * rc.ref_err) {
+        rc.ref_err = err;
+        rc.it_ref = rc.it;
+      } else if (rc.it - rc.it_ref >= rc.stag_iters) {
+        stop = true;  // the host switches the schedule here
+      }
+    }
+  }
+  if (rc.rounds >= rc.max_rounds) stop = true;
+  rc.stop = stop ? 1 : 0;
+}
+
 template <class R>
 __global__ void __launch_bounds__(256) k_reduce_err_multi(Work<R> w) {
   __shared__ double s[kErrPartials];
@@ -1155,8 +1192,18 @@ __global__ void __launch_bounds__(256) k_reduce_err_multi(Work<R> w) {
   __shared__ CellDev<R> cs;
   load_cell(cs, w.cells + w.act[blockIdx.x]);
   __syncthreads();
+  RoundCtl* rc = cs.rctl;
+  if (rc != nullptr && __ldcg(&rc->stop) != 0) return;  // uniform: one flag per block
   fold_partials(cs.ipart, cs.items_a, s, wred);
-  if (threadIdx.x == 0) finish_err<R>(cs, s, cs.err_kind, cs.err_out);
+  if (threadIdx.x == 0) {
+    if (rc != nullptr) {
+      double* out = rc->rows + 8 * rc->rounds;
+      finish_err<R>(cs, s, cs.err_kind, out);
+      round_decide(*rc, out);
+    } else {
+      finish_err<R>(cs, s, cs.err_kind, cs.err_out);
+    }
+  }
 }
 
 // ------------------------------------------------------------------ state set-up

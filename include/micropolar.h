@@ -26,7 +26,16 @@
  *         accumulated plastic strains p, q in FP64, the error measure's sums,
  *         means and ratios (eq. err) in FP64 (the per-voxel norms of FP32
  *         field differences are FP32 quantities and their maxima are exact),
- *         and the homogenized averages summed in FP64;
+ *         and the homogenized averages summed in FP64.  Without a
+ *         prescribed iteration schedule or a manufactured source, an
+ *         increment whose error sets no new low (below 0.99 times the last
+ *         one) in 64 iterations while above the tolerance (the FP32
+ *         rounding floor) continues in the increment form e^{i+1} = e^i -
+ *         Gamma0 * (tau^i - tau^{i-1}); one that stalls there for 128
+ *         iterations (or, if longer, twice the longest gap between its
+ *         earlier lows) finishes in FP64 (an FP64 copy of the cell's state,
+ *         allocated at the first such increment) and returns to FP32 for
+ *         the next increment; iters_fp64 counts those FP64 iterations;
  *     2 = as 1, but the level return's radius, square root, multiplier
  *         increment and scale factor are formed in FP32 (the trial
  *         equivalent stress is itself an FP32 quantity); p, q and every sum
@@ -264,7 +273,8 @@ mp_status mp_rve_profile_read(const mp_rve* rve, double* ms, int64_t* launches, 
  * its tolerance (the floor set by the rounding of its FP32 transforms) continues
  * the increment in the increment form e^{i+1} = e^i - Gamma0 * (tau^i -
  * tau^{i-1}), whose transforms round relative to the change of the
- * polarization; if that sets no new low for 128 iterations, it finishes the
+ * polarization; if that sets no new low for 128 iterations (or twice the
+ * longest gap between its earlier lows, if longer), it finishes the
  * increment in FP64 (iters_fp64).  A prescribed iteration schedule disables
  * both. */
 typedef struct mp_batch_stats {

@@ -285,7 +285,7 @@ struct mp_rve {
   int failed_step = 0;
   std::vector<double> err_steps;
   std::vector<int> iters_steps;
-  double* err_host = nullptr;  // pinned, 8 doubles
+  double* err_host = nullptr;  // pinned, 16 doubles
   uint64_t digest = 0;         // of the problem the cell was created from (checkpoint check)
   // per-kernel-class launch counters and (when profiling) CUDA-event timings
   long long launches[MP_KC_COUNT] = {0};
@@ -300,6 +300,19 @@ struct mp_rve {
   bool device_loop = true;         // false once a graph call failed (then the host decides)
   bool use_fused = true;           // the fused spectral pass, where the cell has one (autotuner's choice)
   bool tuned = false;              // launch schedule chosen by timing candidates
+  // loop bounds of the next device-decided loop: iteration budget and the
+  // stagnation window (0: no watch)
+  int loop_budget = 0, loop_stag = 0, loop_adapt = 0;
+  // FP32-mixed increments whose iteration stalls above the tolerance
+  // (precision 1 without a prescribed schedule) continue in the increment
+  // form and, if that stalls too, finish in FP64: FP64 copies of the
+  // precision-dependent state (cell cd), allocated at the first such increment.
+  std::vector<mp_phase> phases_host;
+  DevBuf spec64, prev64, hist64, elast64, phases64, twx64, twy64, twz64, partials64, avgpart64;
+  LaunchCfg L64;
+  bool twin = false;
+  std::vector<int> iters64_steps;  // iterations of each increment run in FP64
+  long long delta_switches = 0, escalations = 0;
 };
 
 namespace {
@@ -310,6 +323,19 @@ template <>
 CellDev<float>& cell_of<float>(mp_rve* r) { return r->cf; }
 template <>
 CellDev<double>& cell_of<double>(mp_rve* r) { return r->cd; }
+
+// Launch configuration and reduction buffers of the cell of type R: the
+// cell's own, or those of the FP64 copy of an FP32-mixed cell.
+template <class R>
+LaunchCfg& cfg_of(mp_rve* r) { return (sizeof(R) == 8 && r->precision != 0) ? r->L64 : r->L; }
+template <class R>
+double* partials_of(mp_rve* r) {
+  return reinterpret_cast<double*>((sizeof(R) == 8 && r->precision != 0) ? r->partials64.ptr : r->partials.ptr);
+}
+template <class R>
+double* avgpart_of(mp_rve* r) {
+  return reinterpret_cast<double*>((sizeof(R) == 8 && r->precision != 0) ? r->avgpart64.ptr : r->avgpart.ptr);
+}
 
 template <class R>
 mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
@@ -367,7 +393,7 @@ mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
   const size_t max_grid = std::max<size_t>((size_t)r->L.grid_a, 2 * (size_t)ctx->nsm);
   if ((s = dalloc(ctx, r->partials, sizeof(double) * kErrPartials * max_grid)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->avgpart, sizeof(double) * kAvgPartials * (size_t)r->L.grid_v)) != MP_OK) return s;
-  if ((s = dalloc(ctx, r->errout, sizeof(double) * 8)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->errout, sizeof(double) * 16)) != MP_OK) return s;
   if ((s = dalloc(ctx, r->steprows, sizeof(double) * kAvgPartials * (size_t)r->n_steps)) != MP_OK) return s;
   std::vector<R> src_host;
   if (p->tau_m) {
@@ -387,6 +413,61 @@ mp_status rve_setup(mp_rve* r, const mp_problem* p, cudaStream_t st) {
   return MP_OK;
 }
 
+// The FP64 copy of an FP32-mixed cell: its own spectrum, records, phase
+// table, twiddles and reduction buffers; the FP64 state (p, q), the cell
+// scalars, the phase map, the status word and the result rows are shared
+// with the FP32 cell.
+mp_status twin_setup(mp_rve* r, cudaStream_t st) {
+  if (r->twin) return MP_OK;
+  mp_ctx* ctx = r->ctx;
+  const CellDev<float>& f = r->cf;
+  CellDev<double>& c = r->cd;
+  c = CellDev<double>{};
+  c.n1 = f.n1;
+  c.n2 = f.n2;
+  c.n3 = f.n3;
+  c.kx = f.kx;
+  c.nvox = f.nvox;
+  c.nspec = f.nspec;
+  c.h = f.h;
+  c.inv_nvox = f.inv_nvox;
+  for (int j = 0; j < 3; ++j) c.two_pi_over_L[j] = 2.0 * M_PI / ((double)r->n[j] * r->h);
+  mp_status s;
+  if ((s = dalloc(ctx, r->spec64, sizeof(cpx<double>) * 18 * (size_t)c.nspec)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->prev64, sizeof(double) * 20 * (size_t)c.nvox)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->hist64, sizeof(double) * 20 * (size_t)c.nvox)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->elast64, sizeof(double) * 18 * (size_t)c.nvox)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->phases64, sizeof(PhaseDev<double>) * r->phases_host.size())) != MP_OK) return s;
+  c.spec = reinterpret_cast<cpx<double>*>(r->spec64.ptr);
+  c.prev = reinterpret_cast<double*>(r->prev64.ptr);
+  c.hist = reinterpret_cast<double*>(r->hist64.ptr);
+  c.elast = reinterpret_cast<double*>(r->elast64.ptr);
+  c.phases = reinterpret_cast<const PhaseDev<double>*>(r->phases64.ptr);
+  c.pq = f.pq;
+  c.phase = f.phase;
+  c.status = f.status;
+  c.tmean = f.tmean;
+  c.err_kind = r->err_kind;
+  c.ref = ref_dev<double>(r->ref);
+  std::vector<PhaseDev<double>> ph(r->phases_host.size());
+  for (size_t k = 0; k < ph.size(); ++k) ph[k] = phase_dev<double>(r->phases_host[k], false);
+  std::vector<cpx<double>> t1, t2, t3;
+  if ((s = make_axis<double>(ctx, c.n1, true, c.px, r->twx64, st, t1)) != MP_OK) return s;
+  if ((s = make_axis<double>(ctx, c.n2, false, c.py, r->twy64, st, t2)) != MP_OK) return s;
+  if ((s = make_axis<double>(ctx, c.n3, false, c.pz, r->twz64, st, t3)) != MP_OK) return s;
+  MP_CK(ctx, cudaMemcpyAsync(r->phases64.ptr, ph.data(), sizeof(PhaseDev<double>) * ph.size(),
+                             cudaMemcpyHostToDevice, st));
+  r->L64 = make_launch_cfg<double>(c, ctx->nsm);
+  c.rows_a = r->L64.rows;
+  c.items_a = r->L64.items_a;
+  const size_t max_grid = std::max<size_t>((size_t)r->L64.grid_a, 2 * (size_t)ctx->nsm);
+  if ((s = dalloc(ctx, r->partials64, sizeof(double) * kErrPartials * max_grid)) != MP_OK) return s;
+  if ((s = dalloc(ctx, r->avgpart64, sizeof(double) * kAvgPartials * (size_t)r->L64.grid_v)) != MP_OK) return s;
+  MP_CK(ctx, cudaStreamSynchronize(st));  // the host tables are locals
+  r->twin = true;
+  return MP_OK;
+}
+
 template <class R>
 void set_load(CellDev<R>& c, const mp_rve* r, int s) {
   for (int q = 0; q < 9; ++q) {
@@ -399,7 +480,8 @@ void set_load(CellDev<R>& c, const mp_rve* r, int s) {
 // the loop-deciding error reduction when `handle` is given.
 template <class R>
 cudaError_t launch_iteration_kernels(mp_rve* r, CellDev<R>& c, cudaStream_t st, const cudaGraphConditionalHandle* handle) {
-  double* parts = reinterpret_cast<double*>(r->partials.ptr);
+  const LaunchCfg& L = cfg_of<R>(r);
+  double* parts = partials_of<R>(r);
   double* eout = reinterpret_cast<double*>(r->errout.ptr);
   cudaError_t e = cudaSuccess;
   bool fused = false;
@@ -407,22 +489,23 @@ cudaError_t launch_iteration_kernels(mp_rve* r, CellDev<R>& c, cudaStream_t st, 
   if (fused) {
     if constexpr (sizeof(R) == 4) e = launch_spectral(c, reinterpret_cast<int*>(r->ctl.ptr), r->ctx->nsm, st);
   } else {
-    e = launch_fft_y<R>(r->L, c, -1, st);
-    if (e == cudaSuccess) e = launch_green_z<R>(r->L, c, st);
-    if (e == cudaSuccess) e = launch_fft_y<R>(r->L, c, +1, st);
+    e = launch_fft_y<R>(L, c, -1, st);
+    if (e == cudaSuccess) e = launch_green_z<R>(L, c, st);
+    if (e == cudaSuccess) e = launch_fft_y<R>(L, c, +1, st);
   }
-  if (e == cudaSuccess) e = launch_pass_a_iter<R>(r->L, c, parts, st);
+  if (e == cudaSuccess) e = launch_pass_a_iter<R>(L, c, parts, st);
   if (e != cudaSuccess) return e;
   if (handle)
-    return launch_reduce_err_loop<R>(r->L, c, parts, r->err_kind, eout, r->tol, r->max_iter, r->div_limit, *handle,
-                                     st);
-  return launch_reduce_err<R>(r->L, c, parts, r->err_kind, eout, st);
+    return launch_reduce_err_loop<R>(L, c, parts, r->err_kind, eout, r->tol, r->loop_budget, r->div_limit,
+                                     r->loop_stag, r->loop_adapt, *handle, st);
+  return launch_reduce_err<R>(L, c, parts, r->err_kind, eout, st);
 }
 
 // Algorithm 2's while loop of one increment decided on the device: a graph
 // whose conditional WHILE node repeats the iteration kernels while the error
-// reduction finds err > tol (and no failure, fewer than max_iter
-// iterations), launched once; the host reads the outcome after it ends.
+// reduction finds err > tol (and no failure, fewer than r->loop_budget
+// iterations, no stall under a window r->loop_stag > 0), launched once; the
+// host reads the outcome (out[0..9]) after it ends.
 // Returns cudaErrorNotSupported (nothing launched) when a graph call fails.
 template <class R>
 cudaError_t device_loop(mp_rve* r, CellDev<R>& c, cudaStream_t st, int& it, double* out) {
@@ -460,9 +543,12 @@ cudaError_t device_loop(mp_rve* r, CellDev<R>& c, cudaStream_t st, int& it, doub
     return cudaErrorNotSupported;
   }
   double* eout = reinterpret_cast<double*>(r->errout.ptr);
-  e = cudaMemsetAsync(eout + 6, 0, sizeof(double), st);
+  // loop count and stagnation watch from zero; the longest gap between lows
+  // (out[10]) carried in from the increment's earlier stages
+  e = cudaMemsetAsync(eout + 6, 0, sizeof(double) * 4, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(eout + 10, out + 10, sizeof(double), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(out, eout, sizeof(double) * 7, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, eout, sizeof(double) * 11, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaGraphExecDestroy(ge);
   cudaGraphDestroy(g);
@@ -546,65 +632,86 @@ mp_status rve_autotune(mp_rve* r, cudaStream_t st) {
   return MP_OK;
 }
 
-// One load increment s (1-based): predictor, fixed-point loop, commit.
+// Outcome of one stage of an increment's fixed-point loop.
+struct LoopOut {
+  int it = 0;                // iterations run by the stage
+  double err = 0.0;          // error of its last iteration
+  bool stalled = false;      // ended by the stagnation watch
+  mp_status status = MP_OK;  // MP_E_TIMEOUT, MP_E_DIVERGED, or MP_E_NOT_CONVERGED (budget spent above tol)
+};
+
+// One stage of Algorithm 2's loop for increment s on cell c: exactly `target`
+// iterations when target >= 0, else iterations until err <= tol, a failure,
+// `budget` iterations, or (stag > 0) a stall of the error (stall_step with
+// window stag, widening when adapt; gap: the longest gap between lows, carried
+// between the increment's stages).  it0: iterations of the increment before
+// the stage (trace numbering).  The loop runs on the device
+// (one graph launch) unless a prescribed count, per-kernel timing or the
+// trace needs the host between iterations.
 template <class R>
-mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
+mp_status run_loop(mp_rve* r, CellDev<R>& c, int s, cudaStream_t st, int target, int budget, int stag, bool adapt,
+                   int& gap, int it0, LoopOut& o) {
   mp_ctx* ctx = r->ctx;
-  CellDev<R>& c = cell_of<R>(r);
-  set_load(c, r, s);
-  c.src = r->src.ptr ? reinterpret_cast<const R*>(r->src.ptr) + (size_t)(s - 1) * (size_t)r->nvox * 18 : nullptr;
-  const bool prof_step = r->profiling;
-  if (prof_step) cudaEventRecord(r->ev[2 * MP_KC_START], st);
-  MP_CK(ctx, launch_start<R>(r->L, c, s == 1 ? 1 : 0, st));
-  if (prof_step) cudaEventRecord(r->ev[2 * MP_KC_START + 1], st);
-  r->launches[MP_KC_START] += (s == 1) ? 2 : 1;
-  double err = 2.0 * r->tol;
-  int it = 0;
-  const int target = r->lockstep.empty() ? -1 : r->lockstep[s - 1];
-  mp_status status = MP_OK;
-  // the loop decided on the device when nothing needs the host between
-  // iterations (no prescribed schedule, per-kernel timing or trace)
-  bool on_device = false;
+  o = LoopOut{};
+  bool fused = false;
+  if constexpr (sizeof(R) == 4) fused = r->use_fused && r->ctl.ptr != nullptr;
+  auto count = [&](int n) {
+    if (fused) {
+      r->launches[MP_KC_SPECTRAL] += n;
+    } else {
+      if (c.n2 > 1) {
+        r->launches[MP_KC_FFT_Y_FWD] += n;
+        r->launches[MP_KC_FFT_Y_INV] += n;
+      }
+      r->launches[MP_KC_GREEN_Z] += n;
+    }
+    r->launches[MP_KC_PASS_A] += n;
+    r->launches[MP_KC_REDUCE] += n;
+  };
+  auto classify = [&](const double* e) {
+    if (e[5] != 0.0) o.status = MP_E_TIMEOUT;
+    else if (!std::isfinite(e[0]) || e[0] > r->div_limit) o.status = MP_E_DIVERGED;
+  };
+  if (budget <= 0) {
+    o.status = MP_E_NOT_CONVERGED;
+    o.err = 2.0 * r->tol;
+    return MP_OK;
+  }
   if (target < 0 && !r->profiling && !r->tracing && r->device_loop) {
-    const cudaError_t e = device_loop<R>(r, c, st, it, r->err_host);
+    r->loop_budget = budget;
+    r->loop_stag = stag;
+    r->loop_adapt = adapt ? 1 : 0;
+    r->err_host[10] = (double)gap;
+    const cudaError_t e = device_loop<R>(r, c, st, o.it, r->err_host);
     if (e == cudaErrorNotSupported) {
-      r->device_loop = false;
+      r->device_loop = false;  // the host decides from now on
     } else {
       MP_CK(ctx, e);
-      on_device = true;
-      err = r->err_host[0];
-      bool fused = false;
-      if constexpr (sizeof(R) == 4) fused = r->use_fused && r->ctl.ptr != nullptr;
-      if (fused) {
-        r->launches[MP_KC_SPECTRAL] += it;
-      } else {
-        if (c.n2 > 1) {
-          r->launches[MP_KC_FFT_Y_FWD] += it;
-          r->launches[MP_KC_FFT_Y_INV] += it;
-        }
-        r->launches[MP_KC_GREEN_Z] += it;
+      count(o.it);
+      gap = (int)r->err_host[10];
+      o.err = r->err_host[0];
+      classify(r->err_host);
+      if (o.status == MP_OK) {
+        if (r->err_host[9] != 0.0) o.stalled = true;
+        else if (o.err > r->tol) o.status = MP_E_NOT_CONVERGED;
       }
-      r->launches[MP_KC_PASS_A] += it;
-      r->launches[MP_KC_REDUCE] += it;
-      if (r->err_host[5] != 0.0) status = MP_E_TIMEOUT;
-      else if (!std::isfinite(err) || err > r->div_limit) status = MP_E_DIVERGED;
-      else if (err > r->tol) status = MP_E_NOT_CONVERGED;
+      return MP_OK;
     }
   }
-  while (!on_device && (target >= 0 ? it < target : err > r->tol)) {
-    if (target < 0 && it >= r->max_iter) {
-      status = MP_E_NOT_CONVERGED;
+  double err = 2.0 * r->tol, ref_err = 0.0;
+  int it_ref = 0;
+  const LaunchCfg& L = cfg_of<R>(r);
+  double* parts = partials_of<R>(r);
+  double* eout = reinterpret_cast<double*>(r->errout.ptr);
+  const bool prof = r->profiling;
+  auto mark = [&](int k, int end) {
+    if (prof) cudaEventRecord(r->ev[2 * k + end], st);
+  };
+  while (target >= 0 ? o.it < target : err > r->tol) {
+    if (target < 0 && o.it >= budget) {
+      o.status = MP_E_NOT_CONVERGED;
       break;
     }
-    double* parts = reinterpret_cast<double*>(r->partials.ptr);
-    double* eout = reinterpret_cast<double*>(r->errout.ptr);
-    const bool ydo = c.n2 > 1;
-    const bool prof = r->profiling;
-    auto mark = [&](int k, int end) {
-      if (prof) cudaEventRecord(r->ev[2 * k + end], st);
-    };
-    bool fused = false;
-    if constexpr (sizeof(R) == 4) fused = r->use_fused && r->ctl.ptr != nullptr;
     if (fused) {
       if constexpr (sizeof(R) == 4) {
         mark(MP_KC_SPECTRAL, 0);
@@ -613,34 +720,24 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
       }
     } else {
       mark(MP_KC_FFT_Y_FWD, 0);
-      MP_CK(ctx, launch_fft_y<R>(r->L, c, -1, st));
+      MP_CK(ctx, launch_fft_y<R>(L, c, -1, st));
       mark(MP_KC_FFT_Y_FWD, 1);
       mark(MP_KC_GREEN_Z, 0);
-      MP_CK(ctx, launch_green_z<R>(r->L, c, st));
+      MP_CK(ctx, launch_green_z<R>(L, c, st));
       mark(MP_KC_GREEN_Z, 1);
       mark(MP_KC_FFT_Y_INV, 0);
-      MP_CK(ctx, launch_fft_y<R>(r->L, c, +1, st));
+      MP_CK(ctx, launch_fft_y<R>(L, c, +1, st));
       mark(MP_KC_FFT_Y_INV, 1);
     }
     mark(MP_KC_PASS_A, 0);
-    MP_CK(ctx, launch_pass_a_iter<R>(r->L, c, parts, st));
+    MP_CK(ctx, launch_pass_a_iter<R>(L, c, parts, st));
     mark(MP_KC_PASS_A, 1);
     mark(MP_KC_REDUCE, 0);
-    MP_CK(ctx, launch_reduce_err<R>(r->L, c, parts, r->err_kind, eout, st));
+    MP_CK(ctx, launch_reduce_err<R>(L, c, parts, r->err_kind, eout, st));
     mark(MP_KC_REDUCE, 1);
     MP_CK(ctx, cudaMemcpyAsync(r->err_host, r->errout.ptr, sizeof(double) * 6, cudaMemcpyDeviceToHost, st));
     MP_CK(ctx, cudaStreamSynchronize(st));
-    if (fused) {
-      r->launches[MP_KC_SPECTRAL]++;
-    } else {
-      if (ydo) {
-        r->launches[MP_KC_FFT_Y_FWD]++;
-        r->launches[MP_KC_FFT_Y_INV]++;
-      }
-      r->launches[MP_KC_GREEN_Z]++;
-    }
-    r->launches[MP_KC_PASS_A]++;
-    r->launches[MP_KC_REDUCE]++;
+    count(1);
     if (prof) {
       const int ks[6] = {MP_KC_FFT_Y_FWD, MP_KC_GREEN_Z, MP_KC_FFT_Y_INV, MP_KC_PASS_A, MP_KC_REDUCE,
                          MP_KC_SPECTRAL};
@@ -651,21 +748,120 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
       }
     }
     err = r->err_host[0];
+    o.it += 1;
+    o.err = err;
     if (r->tracing) {
-      const double rec[7] = {(double)s, (double)(it + 1), r->err_host[0], r->err_host[1], r->err_host[2],
+      const double rec[7] = {(double)s, (double)(it0 + o.it), r->err_host[0], r->err_host[1], r->err_host[2],
                              r->err_host[3], r->err_host[4]};
       r->trace.insert(r->trace.end(), rec, rec + 7);
     }
-    ++it;
-    if (r->err_host[5] != 0.0) {
-      status = MP_E_TIMEOUT;
-      break;
-    }
-    if (!std::isfinite(err) || err > r->div_limit) {
-      status = MP_E_DIVERGED;
+    classify(r->err_host);
+    if (o.status != MP_OK) break;
+    // the stagnation watch, as on the device
+    if (target < 0 && stag > 0 && err > r->tol && o.it < budget &&
+        stall_step(err, o.it, stag, adapt, ref_err, it_ref, gap)) {
+      o.stalled = true;
       break;
     }
   }
+  return MP_OK;
+}
+
+// Moves the state of an FP32-mixed cell in the middle of increment s to its
+// FP64 copy (records, predictor and the current polarization spectrum
+// widened on the device; p, q and the cell scalars are shared).
+mp_status escalate_to_fp64(mp_rve* r, cudaStream_t st) {
+  mp_ctx* ctx = r->ctx;
+  mp_status s = twin_setup(r, st);
+  if (s != MP_OK) return s;
+  const long long nv = r->nvox;
+  const int nsm = ctx->nsm;
+  const CellDev<float>& f = r->cf;
+  CellDev<double>& d = r->cd;
+  MP_CK(ctx, (launch_convert<float, double>(f.prev, d.prev, 20 * nv, nsm, st)));
+  MP_CK(ctx, (launch_convert<float, double>(f.hist, d.hist, 20 * nv, nsm, st)));
+  MP_CK(ctx, (launch_convert<float, double>(f.elast, d.elast, 18 * nv, nsm, st)));
+  MP_CK(ctx, (launch_convert<float, double>(reinterpret_cast<const float*>(f.spec), reinterpret_cast<double*>(d.spec),
+                                           36 * f.nspec, nsm, st)));
+  return MP_OK;
+}
+
+// Back to FP32 after an increment committed in FP64 (the next increment's
+// predictor is in the iterate record).
+mp_status demote_from_fp64(mp_rve* r, cudaStream_t st) {
+  mp_ctx* ctx = r->ctx;
+  const long long nv = r->nvox;
+  const int nsm = ctx->nsm;
+  const CellDev<double>& d = r->cd;
+  CellDev<float>& f = r->cf;
+  MP_CK(ctx, (launch_convert<double, float>(d.prev, f.prev, 20 * nv, nsm, st)));
+  MP_CK(ctx, (launch_convert<double, float>(d.hist, f.hist, 20 * nv, nsm, st)));
+  MP_CK(ctx, (launch_convert<double, float>(d.elast, f.elast, 18 * nv, nsm, st)));
+  return MP_OK;
+}
+
+// One load increment s (1-based): predictor, fixed-point loop, commit.
+// An FP32-mixed cell (precision 1, no prescribed schedule, no manufactured
+// source) whose error sets no new low in kStallIters iterations while above
+// the tolerance continues the increment in the increment form (the first
+// iteration writes tau(e^i) - tau(e^{i-1}), the next ones also transform the
+// change of e); if that sets no new low in kStallItersDelta iterations (or
+// twice the longest gap between the increment's earlier lows), the
+// increment finishes in FP64 (still in the increment form), is committed there
+// and the state returns to FP32 for the next increment.
+template <class R>
+mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
+  mp_ctx* ctx = r->ctx;
+  CellDev<R>& c = cell_of<R>(r);
+  set_load(c, r, s);
+  c.src = r->src.ptr ? reinterpret_cast<const R*>(r->src.ptr) + (size_t)(s - 1) * (size_t)r->nvox * 18 : nullptr;
+  c.delta_in = c.delta_out = 0;
+  const bool prof_step = r->profiling;
+  if (prof_step) cudaEventRecord(r->ev[2 * MP_KC_START], st);
+  MP_CK(ctx, launch_start<R>(r->L, c, s == 1 ? 1 : 0, st));
+  if (prof_step) cudaEventRecord(r->ev[2 * MP_KC_START + 1], st);
+  r->launches[MP_KC_START] += (s == 1) ? 2 : 1;
+  const int target = r->lockstep.empty() ? -1 : r->lockstep[s - 1];
+  const bool watch = sizeof(R) == 4 && r->precision == 1 && target < 0 && !r->src.ptr;
+  LoopOut o;
+  int it = 0, it64 = 0, gap = 0;
+  bool in_fp64 = false;
+  MP_CK_ST(run_loop<R>(r, c, s, st, target, target >= 0 ? target : r->max_iter, watch ? kStallIters : 0, false, gap,
+                       0, o));
+  it += o.it;
+  if constexpr (sizeof(R) == 4) {
+    if (o.stalled) {
+      // the increment form: one iteration that writes the first increment of
+      // the polarization, then iterations on the increments
+      ++r->delta_switches;
+      c.delta_in = 0;
+      c.delta_out = 1;
+      MP_CK_ST(run_loop<R>(r, c, s, st, -1, std::min(1, r->max_iter - it), 0, false, gap, it, o));
+      it += o.it;
+      if (o.status == MP_OK && o.err > r->tol) {
+        c.delta_in = 1;
+        MP_CK_ST(run_loop<R>(r, c, s, st, -1, r->max_iter - it, kStallItersDelta, true, gap, it, o));
+        it += o.it;
+      }
+      if (o.stalled) {
+        ++r->escalations;
+        MP_CK_ST(escalate_to_fp64(r, st));
+        CellDev<double>& d = r->cd;
+        set_load(d, r, s);
+        d.src = nullptr;
+        d.delta_in = 1;
+        d.delta_out = 1;
+        MP_CK_ST(run_loop<double>(r, d, s, st, -1, r->max_iter - it, 0, false, gap, it, o));
+        it += o.it;
+        it64 = o.it;
+        in_fp64 = true;
+      }
+      c.delta_in = c.delta_out = 0;
+    }
+  }
+  const double err = o.err;
+  mp_status status = o.status;
+  if (status == MP_OK && o.stalled) status = MP_E_NOT_CONVERGED;  // a stall with no later stage
   r->total_iters += it;
   if (status == MP_E_TIMEOUT) {
     r->failed_step = s;
@@ -675,12 +871,20 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
   const bool predict = (status == MP_OK) && (s < r->n_steps);
   const double ratio =
       predict ? (r->time[s + 1] - r->time[s]) / (r->time[s] - r->time[s - 1]) : 0.0;
-  c.predict = predict ? 1 : 0;
-  c.ratio = ratio;
+  double* row = reinterpret_cast<double*>(r->steprows.ptr) + (size_t)kAvgPartials * (s - 1);
   if (prof_step) cudaEventRecord(r->ev[2 * MP_KC_COMMIT], st);
-  MP_CK(ctx, launch_commit<R>(r->L, c, reinterpret_cast<double*>(r->avgpart.ptr),
-                              reinterpret_cast<double*>(r->steprows.ptr) + (size_t)kAvgPartials * (s - 1),
-                              st));
+  if (in_fp64) {
+    CellDev<double>& d = r->cd;
+    d.predict = predict ? 1 : 0;
+    d.ratio = ratio;
+    d.delta_in = d.delta_out = 0;
+    MP_CK(ctx, launch_commit<double>(r->L64, d, avgpart_of<double>(r), row, st));
+    MP_CK_ST(demote_from_fp64(r, st));
+  } else {
+    c.predict = predict ? 1 : 0;
+    c.ratio = ratio;
+    MP_CK(ctx, launch_commit<R>(r->L, c, avgpart_of<R>(r), row, st));
+  }
   r->launches[MP_KC_COMMIT] += 2;
   if (prof_step) {
     // once per increment: the start and commit launches' times (the commit
@@ -694,12 +898,11 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
   }
   r->err_steps.push_back(err);
   r->iters_steps.push_back(it);
+  r->iters64_steps.push_back(r->precision == 0 ? it : it64);
   r->steps_done = s;
   r->predicted = predict;
   if (status != MP_OK) {
     r->failed_step = s;
-    if (status == MP_E_TIMEOUT)
-      return set_error(ctx, status, "load increment %d: a bounded device wait expired", s);
     return set_error(ctx, status, "load increment %d %s after %d iterations (err %.3e)", s,
                      status == MP_E_DIVERGED ? "diverged" : "did not converge", it, err);
   }
@@ -744,7 +947,7 @@ uint64_t problem_digest(const mp_problem* p, const double ref[6]) {
 
 // Checkpoint image: header, then the device arrays in this order.
 struct CkptHeader {
-  char magic[8];  // "MPCKPT1\0"
+  char magic[8];  // "MPCKPT2\0"
   int32_t precision, n[3], n_steps, steps_done, predicted, failed_step;
   int64_t total_iters;
   uint64_t digest;
@@ -755,7 +958,9 @@ void rve_free(mp_rve* r) {
   mp_ctx* ctx = r->ctx;
   DevBuf* bufs[] = {&r->spec, &r->prev, &r->hist, &r->pq, &r->elast, &r->phase, &r->phases,
                     &r->twx, &r->twy, &r->twz, &r->partials, &r->avgpart, &r->errout, &r->steprows,
-                    &r->status, &r->tmean, &r->ctl, &r->src};
+                    &r->status, &r->tmean, &r->ctl, &r->src, &r->spec64, &r->prev64, &r->hist64,
+                    &r->elast64, &r->phases64, &r->twx64, &r->twy64, &r->twz64, &r->partials64,
+                    &r->avgpart64};
   for (DevBuf* b : bufs) dfree(ctx, *b);
   if (r->err_host) cudaFreeHost(r->err_host);
   r->err_host = nullptr;
@@ -840,13 +1045,14 @@ mp_status mp_rve_create(mp_ctx* ctx, const mp_problem* p, mp_rve** out, void* st
   if (p->lockstep_iters) r->lockstep.assign(p->lockstep_iters, p->lockstep_iters + p->n_steps);
   r->div_limit = p->div_limit > 0 ? p->div_limit : 1e6;
   for (int i = 0; i < 6; ++i) r->ref[i] = ref[i];
-  cudaError_t e = cudaMallocHost(&r->err_host, sizeof(double) * 8);
+  cudaError_t e = cudaMallocHost(&r->err_host, sizeof(double) * 16);
   if (e != cudaSuccess) {
     r->err_host = nullptr;
     delete r;
     return set_error(ctx, MP_E_CUDA, "cudaMallocHost: %s", cudaGetErrorString(e));
   }
-  for (int i = 0; i < 8; ++i) r->err_host[i] = 0.0;
+  for (int i = 0; i < 16; ++i) r->err_host[i] = 0.0;
+  r->phases_host.assign(p->phases, p->phases + p->n_phases);
   r->digest = problem_digest(p, ref);
   st = (r->precision == 0) ? rve_setup<double>(r, p, cs) : rve_setup<float>(r, p, cs);
   if (st == MP_OK && ctx->autotune)
@@ -874,13 +1080,14 @@ mp_status mp_rve_reset(mp_rve* r, void* stream) {
   r->failed_step = 0;
   r->err_steps.clear();
   r->iters_steps.clear();
+  r->iters64_steps.clear();
   return MP_OK;
 }
 
 mp_status mp_checkpoint(mp_rve* r, void* host_buf, size_t* bytes, void* stream) {
   if (!r || !bytes) return set_error(r ? r->ctx : nullptr, MP_E_INVALID_ARG, "NULL argument");
   CkptHeader h{};
-  std::memcpy(h.magic, "MPCKPT1", 8);
+  std::memcpy(h.magic, "MPCKPT2", 8);
   h.precision = r->precision;
   for (int j = 0; j < 3; ++j) h.n[j] = r->n[j];
   h.n_steps = r->n_steps;
@@ -895,7 +1102,7 @@ mp_status mp_checkpoint(mp_rve* r, void* host_buf, size_t* bytes, void* stream) 
   h.bytes_elast = r->elast.bytes;
   h.bytes_tmean = r->tmean.bytes;
   h.bytes_rows = r->steprows.bytes;
-  const size_t host_bytes = sizeof(double) * r->err_steps.size() + sizeof(int32_t) * r->iters_steps.size();
+  const size_t host_bytes = sizeof(double) * r->err_steps.size() + 2 * sizeof(int32_t) * r->iters_steps.size();
   const size_t need = sizeof(h) + h.bytes_prev + h.bytes_hist + h.bytes_pq + h.bytes_elast + h.bytes_tmean +
                       h.bytes_rows + host_bytes;
   if (!host_buf) {
@@ -927,6 +1134,11 @@ mp_status mp_checkpoint(mp_rve* r, void* host_buf, size_t* bytes, void* stream) 
     std::memcpy(out + o, &it, sizeof(int32_t));
     o += sizeof(int32_t);
   }
+  for (size_t k = 0; k < r->iters64_steps.size(); ++k) {
+    const int32_t it = r->iters64_steps[k];
+    std::memcpy(out + o, &it, sizeof(int32_t));
+    o += sizeof(int32_t);
+  }
   *bytes = o;
   return MP_OK;
 }
@@ -936,7 +1148,7 @@ mp_status mp_resume(mp_rve* r, const void* host_buf, size_t bytes, void* stream)
   CkptHeader h;
   if (bytes < sizeof(h)) return set_error(r->ctx, MP_E_INVALID_ARG, "checkpoint truncated");
   std::memcpy(&h, host_buf, sizeof(h));
-  if (std::memcmp(h.magic, "MPCKPT1", 8) != 0)
+  if (std::memcmp(h.magic, "MPCKPT2", 8) != 0)
     return set_error(r->ctx, MP_E_INVALID_ARG, "not a checkpoint of this library");
   if (h.digest != r->digest || h.precision != r->precision || h.n_steps != r->n_steps ||
       h.n[0] != r->n[0] || h.n[1] != r->n[1] || h.n[2] != r->n[2])
@@ -947,7 +1159,7 @@ mp_status mp_resume(mp_rve* r, const void* host_buf, size_t bytes, void* stream)
     return set_error(r->ctx, MP_E_INVALID_ARG, "checkpoint layout does not match the cell");
   const size_t nst = (size_t)h.steps_done;
   const size_t need = sizeof(h) + h.bytes_prev + h.bytes_hist + h.bytes_pq + h.bytes_elast + h.bytes_tmean +
-                      h.bytes_rows + nst * (sizeof(double) + sizeof(int32_t));
+                      h.bytes_rows + nst * (sizeof(double) + 2 * sizeof(int32_t));
   if (bytes < need) return set_error(r->ctx, MP_E_INVALID_ARG, "checkpoint truncated");
   MP_DEVICE_SCOPE(r->ctx);
   mp_status st = MP_OK;
@@ -971,6 +1183,13 @@ mp_status mp_resume(mp_rve* r, const void* host_buf, size_t bytes, void* stream)
     int32_t it;
     std::memcpy(&it, in + o, sizeof(int32_t));
     r->iters_steps[k] = it;
+    o += sizeof(int32_t);
+  }
+  r->iters64_steps.assign(nst, 0);
+  for (size_t k = 0; k < nst; ++k) {
+    int32_t it;
+    std::memcpy(&it, in + o, sizeof(int32_t));
+    r->iters64_steps[k] = it;
     o += sizeof(int32_t);
   }
   r->steps_done = h.steps_done;
@@ -1112,7 +1331,7 @@ mp_status mp_rve_results(mp_rve* r, mp_result* res, void* stream) {
     if (res->Meq) res->Meq[s] = row[39];
     if (res->err) res->err[s] = r->err_steps[s];
     if (res->iters) res->iters[s] = r->iters_steps[s];
-    if (res->iters_fp64) res->iters_fp64[s] = r->precision == 0 ? r->iters_steps[s] : 0;
+    if (res->iters_fp64) res->iters_fp64[s] = r->iters64_steps[s];
   }
   res->steps_done = ns;
   res->failed_step = r->failed_step;

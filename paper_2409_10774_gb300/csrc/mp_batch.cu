@@ -210,15 +210,16 @@ struct Progress {
   std::vector<double> err_steps;
   std::vector<int> iters_steps, iters64_steps;
   int it64 = 0;             // iterations of the current increment run in FP64
-  double ref_err = 0.0;     // stagnation watch (FP32): error level and iteration
-  int it_ref = 0;           //   of its last significant new low
+  double ref_err = 0.0;     // stagnation watch (FP32, stall_step): error level and
+  int it_ref = 0;           //   iteration of its last new low, and the longest
+  int gap = 0;              //   gap between lows in the increment
   int delta = 0;            // increment form: 0 off, 1 switching on this round, 2 on
   bool escalate = false;    // FP32 iteration stagnated: finish the increment in FP64
   bool demote = false;      // FP64-finished increment committed: next one in FP32
 };
 
-// An FP32-mixed cell whose error has set no new low (a drop by kStagnationDrop)
-// in kStagnationIters iterations while still above the tolerance has met the
+// An FP32-mixed cell whose error has set no new low (a drop below kStallDrop times
+// the last low) in kStallIters iterations while still above the tolerance has met the
 // rounding floor of its FP32 transforms, which for strongly heterogeneous
 // plastic cells can sit above the tolerance of the local error measure (a
 // slowly but steadily converging cell keeps setting new lows and stays as it
@@ -228,12 +229,11 @@ struct Progress {
 // stresses that enter the local error measure (a voxel's stress rounds at
 // ~6e-8 of its own magnitude, which at stress concentrations can reach the
 // tolerance relative to the mean): a cell that sets no new low for
-// kStagnationItersDelta iterations there finishes the increment in FP64, which
-// then takes a few to a few hundred iterations.  (Cells that converge in the
-// increment form set a new low every few iterations.)
-constexpr int kStagnationIters = 64;
-constexpr int kStagnationItersDelta = 128;
-constexpr double kStagnationDrop = 0.01;
+// kStallItersDelta iterations there (or twice the longest gap between its
+// earlier lows, so that a slow but steady contraction keeps going in FP32)
+// finishes the increment in FP64.
+// (The thresholds, kStallIters, kStallItersDelta and kStallDrop, are the
+// single-cell solver's.)
 
 // Iteration rounds per window: a window's launches run back to back on the
 // device, each cell's loop test is taken there (RoundCtl) and the host
@@ -366,6 +366,7 @@ class Engine {
         g.err = 2.0 * q.tol;
         g.ref_err = 0.0;
         g.it_ref = 0;
+        g.gap = 0;
       }
       if (g.state == Progress::kIter) {
         c.delta_in = g.delta == 2 ? 1 : 0;
@@ -391,13 +392,14 @@ class Engine {
       rc.tol = q.tol;
       rc.div_limit = q.div_limit;
       rc.ref_err = g.ref_err;
-      rc.drop = 1.0 - kStagnationDrop;
       rc.rows = derr + (size_t)8 * kRoundWindow * i;
       rc.it = g.it;
       rc.target = target;
       rc.max_iter = q.max_iter;
       rc.it_ref = g.it_ref;
-      rc.stag_iters = (!kFp64 && target < 0) ? (g.delta ? kStagnationItersDelta : kStagnationIters) : 0;
+      rc.stag_iters = (!kFp64 && target < 0) ? (g.delta ? kStallItersDelta : kStallIters) : 0;
+      rc.adapt = g.delta != 0 ? 1 : 0;
+      rc.gap = g.gap;
       // the first round of the increment form changes the next round's inputs
       rc.max_rounds = (g.delta == 1) ? 1 : K;
       sl.c.rctl = dctl + i;
@@ -481,10 +483,8 @@ class Engine {
     if (!leave) {
       // FP32 stagnation watch (not under a prescribed iteration schedule)
       if (!kFp64 && target < 0) {
-        if (g.it_ref == 0 || g.err < (1.0 - kStagnationDrop) * g.ref_err) {
-          g.ref_err = g.err;
-          g.it_ref = g.it;
-        } else if (g.it - g.it_ref >= (g.delta ? kStagnationItersDelta : kStagnationIters)) {
+        if (stall_step(g.err, g.it, g.delta ? kStallItersDelta : kStallIters, g.delta != 0, g.ref_err, g.it_ref,
+                       g.gap)) {
           if (g.delta == 0) {
             g.delta = 1;
             g.ref_err = g.err;

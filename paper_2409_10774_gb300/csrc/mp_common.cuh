@@ -83,14 +83,15 @@ struct AxisPlan {
 // through the same test.
 struct RoundCtl {
   double tol, div_limit;
-  double ref_err;    // stagnation watch: error at the last significant new low
-  double drop;       // a significant new low: err < drop * ref_err
+  double ref_err;    // stagnation watch (stall_step): error at the last new low
   double* rows;      // [max_rounds][8] the window's error rows
   int it;            // iterations of the current increment so far
   int target;        // prescribed iteration count of the increment, or -1
   int max_iter;
   int it_ref;        // iteration of the last significant new low (0: none yet)
   int stag_iters;    // iterations without a new low that stop the window (0: no watch)
+  int adapt;         // 1: the window widens to twice the longest gap between lows (stall_step)
+  int gap;           // longest gap between lows in the increment so far
   int max_rounds;    // rounds the window may run for this cell
   int rounds;        // rounds run (device-written)
   int stop;          // 1: no further round in this window (device-written)
@@ -174,6 +175,33 @@ struct Work {
   const long long* pre;
   int n_act;
 };
+
+// Stagnation watch of an FP32-mixed iteration (single cells and batches): a
+// new low is an error below kStallDrop times the last low; kStallIters
+// iterations without one end the full-form stage, kStallItersDelta the
+// increment-form stage (the increment then finishes in FP64).
+constexpr double kStallDrop = 0.99;
+constexpr int kStallIters = 64;
+constexpr int kStallItersDelta = 128;
+
+// One step of the stagnation watch after iteration `it` with error `err`
+// (above the tolerance), shared by the host and device loop tests: a new low
+// (the first error, or one below kStallDrop times the last low) records its
+// iteration and the longest gap between consecutive lows; returns true once
+// no new low came for `window` iterations or, with adapt, for max(window,
+// 2 x that longest gap): a slowly but steadily converging iteration keeps its
+// pace between lows, while at a rounding floor the gaps grow without bound.
+__host__ __device__ inline bool stall_step(double err, int it, int window, bool adapt, double& ref_err, int& it_ref,
+                                           int& gap) {
+  if (it_ref == 0 || err < kStallDrop * ref_err) {
+    if (it_ref > 0 && it - it_ref > gap) gap = it - it_ref;
+    ref_err = err;
+    it_ref = it;
+    return false;
+  }
+  const int w = (adapt && 2 * gap > window) ? 2 * gap : window;
+  return it - it_ref >= w;
+}
 
 // Number of doubles in one block partial of the iteration error reduction:
 // 4 maxima of |delta a|, 4 sums of |delta a|, 36 sums of e, t, gamma, m.

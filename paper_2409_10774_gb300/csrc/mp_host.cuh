@@ -86,6 +86,13 @@ struct DeviceScope {
                              "%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__, __LINE__); \
   } while (0)
 
+// Returns the mp_status of `call` when it is not MP_OK (its error already set).
+#define MP_CK_ST(call)                \
+  do {                                \
+    const mp_status _s = (call);      \
+    if (_s != MP_OK) return _s;       \
+  } while (0)
+
 namespace mp {
 
 // Per-phase constants of Algorithm 1, prepared in FP64.  ret32 (FP32 fields

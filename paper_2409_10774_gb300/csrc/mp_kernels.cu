@@ -1132,13 +1132,16 @@ __global__ void __launch_bounds__(256) k_reduce_err(CellDev<R> c, const double* 
 
 // The same reduction, deciding the fixed-point loop on the device (Algorithm 2's
 // while test) for a launch inside a conditional WHILE node: out[6] counts the
-// iterations of the increment; the loop continues while no failure is
-// recorded, err is finite, err <= div_limit, err > tol and fewer than
-// max_iter iterations ran.
+// iterations of the loop; the loop continues while no failure is recorded,
+// err is finite, err <= div_limit, err > tol, fewer than max_iter iterations
+// ran and (stag > 0) the stagnation watch (stall_step with window stag) has
+// not tripped: out[7], out[8] hold the last low and its iteration, out[10]
+// the longest gap between lows, out[9] = 1 records a stop by the watch.
 template <class R>
 __global__ void __launch_bounds__(256) k_reduce_err_loop(CellDev<R> c, const double* partials, int nparts,
                                                          int err_kind, double* out, double tol, int max_iter,
-                                                         double div_limit, cudaGraphConditionalHandle handle) {
+                                                         double div_limit, int stag, int adapt,
+                                                         cudaGraphConditionalHandle handle) {
   __shared__ double s[kErrPartials];
   __shared__ double wred[8][kErrPartials];
   fold_partials(partials, nparts, s, wred);
@@ -1147,7 +1150,18 @@ __global__ void __launch_bounds__(256) k_reduce_err_loop(CellDev<R> c, const dou
     const int it = (int)out[6] + 1;
     out[6] = (double)it;
     const double err = out[0];
-    const bool go = out[5] == 0.0 && isfinite(err) && err <= div_limit && err > tol && it < max_iter;
+    bool go = out[5] == 0.0 && isfinite(err) && err <= div_limit && err > tol && it < max_iter;
+    if (go && stag > 0) {
+      double ref_err = out[7];
+      int it_ref = (int)out[8], gap = (int)out[10];
+      if (stall_step(err, it, stag, adapt != 0, ref_err, it_ref, gap)) {
+        go = false;
+        out[9] = 1.0;
+      }
+      out[7] = ref_err;
+      out[8] = (double)it_ref;
+      out[10] = (double)gap;
+    }
     cudaGraphSetConditional(handle, go ? 1u : 0u);
   }
 }
@@ -1173,12 +1187,8 @@ __device__ void round_decide(RoundCtl& rc, const double* e) {
     } else if (rc.target < 0 && rc.it >= rc.max_iter) {
       stop = true;  // not converged
     } else if (rc.stag_iters > 0) {
-      if (rc.it_ref == 0 || err < rc.drop * rc.ref_err) {
-        rc.ref_err = err;
-        rc.it_ref = rc.it;
-      } else if (rc.it - rc.it_ref >= rc.stag_iters) {
-        stop = true;  // the host switches the schedule here
-      }
+      // the host switches the schedule where the watch trips
+      if (stall_step(err, rc.it, rc.stag_iters, rc.adapt != 0, rc.ref_err, rc.it_ref, rc.gap)) stop = true;
     }
   }
   if (rc.rounds >= rc.max_rounds) stop = true;
@@ -1613,10 +1623,10 @@ cudaError_t launch_reduce_err(const LaunchCfg& L, const CellDev<R>& c, const dou
 
 template <class R>
 cudaError_t launch_reduce_err_loop(const LaunchCfg& L, const CellDev<R>& c, const double* partials, int err_kind,
-                                   double* err_out, double tol, int max_iter, double div_limit,
-                                   cudaGraphConditionalHandle handle, cudaStream_t st) {
+                                   double* err_out, double tol, int max_iter, double div_limit, int stag,
+                                   int adapt, cudaGraphConditionalHandle handle, cudaStream_t st) {
   k_reduce_err_loop<R><<<1, 256, 0, st>>>(c, partials, L.grid_a, err_kind, err_out, tol, max_iter, div_limit,
-                                          handle);
+                                          stag, adapt, handle);
   return cudaGetLastError();
 }
 
@@ -1802,7 +1812,7 @@ bool sizes_fit(int n1, int n2, int n3) {
   template cudaError_t launch_green_z<R>(const LaunchCfg&, const CellDev<R>&, cudaStream_t);          \
   template cudaError_t launch_pass_a_iter<R>(const LaunchCfg&, const CellDev<R>&, double*, cudaStream_t); \
   template cudaError_t launch_reduce_err_loop<R>(const LaunchCfg&, const CellDev<R>&, const double*, int, \
-                                                 double*, double, int, double,                       \
+                                                 double*, double, int, double, int, int,             \
                                                  cudaGraphConditionalHandle, cudaStream_t);          \
   template cudaError_t launch_reduce_err<R>(const LaunchCfg&, const CellDev<R>&, const double*, int,  \
                                             double*, cudaStream_t);                                  \

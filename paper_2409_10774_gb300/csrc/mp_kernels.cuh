@@ -34,11 +34,14 @@ cudaError_t launch_reduce_err(const LaunchCfg& L, const CellDev<R>& c, const dou
 // The error reduction of a loop decided on the device: additionally counts
 // the iteration in err_out[6] (zeroed before the loop) and sets `handle` (a
 // conditional WHILE node's) to continue while err > tol, err finite and
-// <= div_limit, no failure recorded and fewer than max_iter iterations ran.
+// <= div_limit, no failure recorded, fewer than max_iter iterations ran and
+// (stag > 0) the stagnation watch (stall_step, window stag, widening when
+// adapt) has not tripped (err_out[6..10]: loop iterations, last low, its
+// iteration, stopped by the watch, longest gap between lows).
 template <class R>
 cudaError_t launch_reduce_err_loop(const LaunchCfg& L, const CellDev<R>& c, const double* partials, int err_kind,
-                                   double* err_out, double tol, int max_iter, double div_limit,
-                                   cudaGraphConditionalHandle handle, cudaStream_t st);
+                                   double* err_out, double tol, int max_iter, double div_limit, int stag,
+                                   int adapt, cudaGraphConditionalHandle handle, cudaStream_t st);
 // One fixed-point iteration; writes err and the four per-field errors to err_out[0..4].
 template <class R>
 cudaError_t launch_iteration(const LaunchCfg& L, const CellDev<R>& c, double* partials,

@@ -9,8 +9,9 @@ point by about tol rho / (1 - rho) (rho the contraction factor), whatever its
 arithmetic.  So the precision contract (homogenized results within 1e-6 of
 their size, fields within 1e-5 relative L2 over the stored sample of voxels,
 each with its partner floor as in parity_helpers) is checked on FP32-field
-runs taken to 1e-8 (the batched engine gets there by continuing a stalled
-FP32 increment in the increment form and, past that, in FP64), and the runs
+runs taken to 1e-8 (a stalled FP32 increment continues in the increment form
+and, past that, in FP64, in the single-cell solver and the batched engine
+alike), and the runs
 at the configuration's tolerance 1e-6 are held to that early-stopping level
 (5e-6 homogenized, 1e-4 fields).  The plain FP64 path run to 1e-10 agrees to
 1e-8.
@@ -89,7 +90,7 @@ def _check(res, ref, prob, hom_tol, field_tol, label):
         assert v <= field_tol, (label, k, v)
 
 
-@pytest.mark.parametrize("name", ["rsa64", "voronoi64"])
+@pytest.mark.parametrize("name", ["rsa64", "voronoi64", "request0"])
 def test_fp32_single_cell_free_running(ctx, name):
     import paper_2409_10774_gb300 as M
     ref = _ref(name)

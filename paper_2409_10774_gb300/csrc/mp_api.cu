@@ -836,8 +836,13 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
       ++r->delta_switches;
       c.delta_in = 0;
       c.delta_out = 1;
-      MP_CK_ST(run_loop<R>(r, c, s, st, -1, std::min(1, r->max_iter - it), 0, false, gap, it, o));
-      it += o.it;
+      if (it < r->max_iter) {
+        MP_CK_ST(run_loop<R>(r, c, s, st, 1, 1, 0, false, gap, it, o));  // exactly one iteration
+        it += o.it;
+      } else {
+        o.stalled = false;
+        o.status = MP_E_NOT_CONVERGED;
+      }
       if (o.status == MP_OK && o.err > r->tol) {
         c.delta_in = 1;
         MP_CK_ST(run_loop<R>(r, c, s, st, -1, r->max_iter - it, kStallItersDelta, true, gap, it, o));

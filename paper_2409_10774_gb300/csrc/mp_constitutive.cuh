@@ -125,9 +125,11 @@ __device__ __forceinline__ R scaled_t(R ttr, bool diag, R vol, R ft) {
 // A level whose trial value q2 (FP32 fields) lies clearly inside the yield
 // surface of radius Y + H p_n, judged in single precision with a margin well
 // above its rounding, is elastic without the FP64 test; the other voxels take
-// the FP64 test, whose outcome this screen never contradicts.
+// the FP64 test, whose outcome this screen never contradicts.  p_n is
+// narrowed toward zero with integer operations (H >= 0, so the radius can
+// only come out smaller: the screen stays on the safe side).
 __device__ __forceinline__ bool surely_elastic_f32(float q2, float Yf, float Hf, double pn) {
-  const float Rn = fmaf(Hf, (float)pn, Yf);
+  const float Rn = fmaf(Hf, float_rz(pn), Yf);
   return q2 < 0.999996f * (Rn * Rn);
 }
 

@@ -150,13 +150,19 @@ def test_green_apply_fused_spectral_pass(ctx, n):
     assert np.abs(g - g_ref).max() <= 2e-5 * np.abs(g_ref).max()
 
 
-def test_lockstep_solve_on_fused_spectral_pass(ctx):
+def test_lockstep_solve_on_fused_spectral_pass():
     import paper_2409_10774_gb300 as M
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
     n = (2, 256, 256)
     prob = _thin_problem(n, seed=7)
     # ten iterations on both sides (the oracle needs ~2 s for each on this cell)
     ref = OS.solve(prob, lockstep_iters=[10])
     assert ref["status"] == "ok" and ref["P"][0] > 0.0
+    # the default schedule (the autotuner may time the separate passes faster
+    # on a cell of a single kx plane)
+    ctx = M.Context(0)
+    ctx.set_autotune(False)
     rve = M.Rve(ctx, prob, precision=1, lockstep_iters=ref["iters"])
     rve.profile(True)
     assert rve.run(len(ref["iters"])) == 0

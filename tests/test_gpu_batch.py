@@ -135,6 +135,9 @@ def test_batch_failures_stay_per_item(ctx):
     assert res[2]["failed_step"] == single["failed_step"] == 1
     assert res[2]["steps_done"] == single["steps_done"] == 1
     assert list(res[2]["iters"]) == list(single["iters"]) == [3]
+    # same iterate sequence, but the batched and the single-cell kernels are
+    # separately compiled and sum their FP64 reductions in another order, and
+    # the FP32 fields carry that difference: agreement to FP32 rounding
     assert _rel(res[2]["T"], single["T"]) <= 1e-6
     alone = M.mp_batch_solve(ctx, [probs[0]], precision=1)[0]
     _assert_identical(res[0], alone, fields=False)

@@ -271,6 +271,8 @@ class Engine {
     for (Slot<R>& s : slots_) release(s);
     slots_.clear();
     free_meta();
+    if (gexec_) cudaGraphExecDestroy(gexec_);
+    if (capture_) cudaStreamDestroy(capture_);
   }
 
   bool idle() const { return slots_.empty(); }
@@ -712,7 +714,7 @@ class Engine {
       e = cudaMemcpyAsync(db + meta_.ctl, hb + meta_.ctl, sizeof(RoundCtl) * n, cudaMemcpyHostToDevice, st_);
     if (e == cudaSuccess && !l_commit.empty()) e = launch_multi_commit<R>(m, st_);
     if (e == cudaSuccess && !l_start.empty()) e = launch_multi_start<R>(m, st_);
-    for (int r = 0; e == cudaSuccess && !l_iter.empty() && r < rounds; ++r) e = launch_multi_iteration<R>(m, st_);
+    if (e == cudaSuccess && !l_iter.empty()) e = launch_rounds(m, rounds);
     if (e == cudaSuccess && !l_iter.empty())
       e = cudaMemcpyAsync(h_err_, db + meta_.err, sizeof(double) * 8 * kRoundWindow * n, cudaMemcpyDeviceToHost,
                           st_);
@@ -800,9 +802,73 @@ class Engine {
     return st;
   }
 
+  // The window's iteration rounds as one CUDA graph: captured for a launch
+  // configuration (work lists, item counts, grids, shared memory, rounds) and
+  // replayed while the configuration stays the same (the resident cells keep
+  // iterating); the work lists' contents live in the metadata block, which
+  // every window uploads before the launch.
+  struct RoundsKey {
+    Work<R> wy, wz, wa;
+    long long items_y, items_z, items_a;
+    size_t smem_y, smem_z, smem_a;
+    int grid_y, grid_z, grid_a, rounds;
+  };
+  static RoundsKey rounds_key(const MultiCfg<R>& m, int rounds) {
+    RoundsKey k;
+    std::memset(&k, 0, sizeof(k));  // padding compares equal
+    k.wy = m.wy;
+    k.wz = m.wz;
+    k.wa = m.wa;
+    k.items_y = m.items_y;
+    k.items_z = m.items_z;
+    k.items_a = m.items_a;
+    k.smem_y = m.smem_y;
+    k.smem_z = m.smem_z;
+    k.smem_a = m.smem_a;
+    k.grid_y = m.grid_y;
+    k.grid_z = m.grid_z;
+    k.grid_a = m.grid_a;
+    k.rounds = rounds;
+    return k;
+  }
+  cudaError_t launch_rounds(const MultiCfg<R>& m, int rounds) {
+    if (rounds <= 1) return launch_multi_iteration<R>(m, st_);
+    const RoundsKey k = rounds_key(m, rounds);
+    if (!(gexec_ && std::memcmp(&k, &gkey_, sizeof(k)) == 0)) {
+      if (gexec_) cudaGraphExecDestroy(gexec_);
+      gexec_ = nullptr;
+      if (!capture_ && cudaStreamCreateWithFlags(&capture_, cudaStreamNonBlocking) != cudaSuccess) capture_ = nullptr;
+      cudaGraph_t g = nullptr;
+      cudaError_t e = capture_ ? cudaStreamBeginCapture(capture_, cudaStreamCaptureModeRelaxed)
+                               : cudaErrorNotSupported;
+      if (e == cudaSuccess) {
+        cudaError_t el = cudaSuccess;
+        for (int r = 0; r < rounds && el == cudaSuccess; ++r) el = launch_multi_iteration<R>(m, capture_);
+        e = cudaStreamEndCapture(capture_, &g);
+        if (e == cudaSuccess) e = el;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec_, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        // no graph: the same launches one by one
+        cudaGetLastError();
+        if (gexec_) cudaGraphExecDestroy(gexec_);
+        gexec_ = nullptr;
+        cudaError_t el = cudaSuccess;
+        for (int r = 0; r < rounds && el == cudaSuccess; ++r) el = launch_multi_iteration<R>(m, st_);
+        return el;
+      }
+      gkey_ = k;
+    }
+    return cudaGraphLaunch(gexec_, st_);
+  }
+
   mp_ctx* ctx_;
   Pool* pool_;
   cudaStream_t st_;
+  cudaStream_t capture_ = nullptr;
+  cudaGraphExec_t gexec_ = nullptr;
+  RoundsKey gkey_{};
   std::vector<Slot<R>> slots_;
   size_t resident_ = 0;
   int64_t voxel_iters_ = 0, rounds_ = 0, delta_switches_ = 0;

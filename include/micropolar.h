@@ -33,8 +33,9 @@
  *         rounding floor) continues in the increment form e^{i+1} = e^i -
  *         Gamma0 * (tau^i - tau^{i-1}); one that stalls there for 128
  *         iterations (or, if longer, twice the longest gap between its
- *         earlier lows) finishes in FP64 (an FP64 copy of the cell's state,
- *         allocated at the first such increment) and returns to FP32 for
+ *         earlier lows) finishes in FP64 in the full form restarted from
+ *         the current iterate (an FP64 copy of the cell's state, allocated
+ *         at the first such increment) and returns to FP32 for
  *         the next increment; iters_fp64 counts those FP64 iterations;
  *     2 = as 1, but the level return's radius, square root, multiplier
  *         increment and scale factor are formed in FP32 (the trial
@@ -275,8 +276,8 @@ mp_status mp_rve_profile_read(const mp_rve* rve, double* ms, int64_t* launches, 
  * tau^{i-1}), whose transforms round relative to the change of the
  * polarization; if that sets no new low for 128 iterations (or twice the
  * longest gap between its earlier lows, if longer), it finishes the
- * increment in FP64 (iters_fp64).  A prescribed iteration schedule disables
- * both. */
+ * increment in FP64 (iters_fp64), in the full form restarted from its
+ * current iterate.  A prescribed iteration schedule disables both. */
 typedef struct mp_batch_stats {
   int64_t rounds;              /* iteration rounds of the FP32 and of the FP64 engine       */
   int64_t rounds_fp64;

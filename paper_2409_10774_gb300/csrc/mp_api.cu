@@ -768,8 +768,8 @@ mp_status run_loop(mp_rve* r, CellDev<R>& c, int s, cudaStream_t st, int target,
 }
 
 // Moves the state of an FP32-mixed cell in the middle of increment s to its
-// FP64 copy (records, predictor and the current polarization spectrum
-// widened on the device; p, q and the cell scalars are shared).
+// FP64 copy (records and predictor widened on the device; p, q and the cell
+// scalars are shared; the polarization is formed anew there).
 mp_status escalate_to_fp64(mp_rve* r, cudaStream_t st) {
   mp_ctx* ctx = r->ctx;
   mp_status s = twin_setup(r, st);
@@ -781,8 +781,6 @@ mp_status escalate_to_fp64(mp_rve* r, cudaStream_t st) {
   MP_CK(ctx, (launch_convert<float, double>(f.prev, d.prev, 20 * nv, nsm, st)));
   MP_CK(ctx, (launch_convert<float, double>(f.hist, d.hist, 20 * nv, nsm, st)));
   MP_CK(ctx, (launch_convert<float, double>(f.elast, d.elast, 18 * nv, nsm, st)));
-  MP_CK(ctx, (launch_convert<float, double>(reinterpret_cast<const float*>(f.spec), reinterpret_cast<double*>(d.spec),
-                                           36 * f.nspec, nsm, st)));
   return MP_OK;
 }
 
@@ -807,8 +805,9 @@ mp_status demote_from_fp64(mp_rve* r, cudaStream_t st) {
 // iteration writes tau(e^i) - tau(e^{i-1}), the next ones also transform the
 // change of e); if that sets no new low in kStallItersDelta iterations (or
 // twice the longest gap between the increment's earlier lows), the
-// increment finishes in FP64 (still in the increment form), is committed there
-// and the state returns to FP32 for the next increment.
+// increment finishes in FP64 in the full form (restarted from the current
+// iterate), is committed there and the state returns to FP32 for the next
+// increment.
 template <class R>
 mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
   mp_ctx* ctx = r->ctx;
@@ -854,8 +853,13 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
         CellDev<double>& d = r->cd;
         set_load(d, r, s);
         d.src = nullptr;
-        d.delta_in = 1;
-        d.delta_out = 1;
+        // FP64 restarts the full form from the current iterate: the start
+        // pass forms its polarization, so the rounding the increment form
+        // carried is damped by the iteration instead of kept
+        d.delta_in = 0;
+        d.delta_out = 0;
+        MP_CK(ctx, launch_start<double>(r->L64, d, 0, st));
+        r->launches[MP_KC_START] += 1;
         MP_CK_ST(run_loop<double>(r, d, s, st, -1, r->max_iter - it, 0, false, gap, it, o));
         it += o.it;
         it64 = o.it;

@@ -216,6 +216,8 @@ struct Progress {
   int delta = 0;            // increment form: 0 off, 1 switching on this round, 2 on
   bool escalate = false;    // FP32 iteration stagnated: finish the increment in FP64
   bool demote = false;      // FP64-finished increment committed: next one in FP32
+  bool restart = false;     // escalated: recompute the polarization of the current
+                            // iterate and continue in the full form (in FP64)
 };
 
 // An FP32-mixed cell whose error has set no new low (a drop below kStallDrop times
@@ -369,6 +371,13 @@ class Engine {
         g.ref_err = 0.0;
         g.it_ref = 0;
         g.gap = 0;
+      }
+      if (g.state == Progress::kIter && g.restart) {
+        // an escalated increment continues in FP64 in the full form: the
+        // start pass forms the polarization of the current iterate (the
+        // increment form's carried rounding is then damped, not kept)
+        l_start.push_back(i);
+        g.restart = false;
       }
       if (g.state == Progress::kIter) {
         c.delta_in = g.delta == 2 ? 1 : 0;
@@ -898,6 +907,10 @@ int migrate(Engine<RA>& from, Engine<RB>& to) {
     }
     Slot<RB> dst;
     dst.g = src.g;
+    if (src.g.escalate && src.g.state == Progress::kIter) {
+      dst.g.delta = 0;
+      dst.g.restart = true;
+    }
     dst.g.escalate = dst.g.demote = false;
     if (to.build_slot(dst, false) != MP_OK) {
       src.g.escalate = src.g.demote = false;
@@ -912,7 +925,7 @@ int migrate(Engine<RA>& from, Engine<RB>& to) {
     cudaError_t e = launch_convert<RA, RB>(src.c.prev, dst.c.prev, 20 * nv, nsm, st);
     if (e == cudaSuccess) e = launch_convert<RA, RB>(src.c.hist, dst.c.hist, 20 * nv, nsm, st);
     if (e == cudaSuccess) e = launch_convert<RA, RB>(src.c.elast, dst.c.elast, 18 * nv, nsm, st);
-    if (e == cudaSuccess && src.g.state == Progress::kIter)
+    if (e == cudaSuccess && src.g.state == Progress::kIter && !dst.g.restart)
       e = launch_convert<RA, RB>(reinterpret_cast<const RA*>(src.c.spec), reinterpret_cast<RB*>(dst.c.spec),
                                  36 * src.c.nspec, nsm, st);
     if (e == cudaSuccess)

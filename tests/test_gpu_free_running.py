@@ -10,8 +10,8 @@ arithmetic.  So the precision contract (homogenized results within 1e-6 of
 their size, fields within 1e-5 relative L2 over the stored sample of voxels,
 each with its partner floor as in parity_helpers) is checked on FP32-field
 runs taken to 1e-8 (a stalled FP32 increment continues in the increment form
-and, past that, in FP64, in the single-cell solver and the batched engine
-alike), and the runs
+and, past that, in FP64 in the full form, in the single-cell solver and the
+batched engine alike), and the runs
 at the configuration's tolerance 1e-6 are held to that early-stopping level
 (5e-6 homogenized, 1e-4 fields).  The plain FP64 path run to 1e-10 agrees to
 1e-8.
@@ -127,13 +127,14 @@ def _check_contract(res, ref, prob, field_tol, label):
         assert v <= field_tol, (label, k, v)
 
 
-@pytest.mark.parametrize("name,field_tol", [("rsa64", 1e-5), ("voronoi64", 1e-5), ("request0", 1e-4)])
+@pytest.mark.parametrize("name,field_tol", [("rsa64", 1e-5), ("voronoi64", 1e-5), ("request0", 1e-5)])
 def test_fp32_precision_contract(ctx, name, field_tol):
     """FP32 fields with the FP64 scalar solve and reductions, run to 1e-8,
-    against the converged oracle.  The strongly plastic request cell with
-    stiff inclusions finishes its increments in the increment form, whose
-    rounding is carried rather than damped: its fields keep ~1e-4 of FP32
-    rounding while its homogenized stress meets 1e-6."""
+    against the converged oracle.  The plastic cells with stiff inclusions
+    (rsa64, request0) stall at the FP32 floor in every increment; the FP64
+    stage then restarts the full form from the current iterate, whose
+    contraction removes the rounding the FP32 and increment-form iterations
+    left (measured: fields within 3e-8 there)."""
     import paper_2409_10774_gb300 as M
     ref = _ref(name)
     prob = dict(FC.problem(name), tol=1e-8)

@@ -342,7 +342,8 @@ __device__ __forceinline__ void stage_first_inv_packed(const cpx<R>* __restrict_
     }
     if constexpr (RADIX == 3) dft3<R, +1>(v);
     else if constexpr (RADIX == 4) dft4<R, +1>(v);
-    else dft8<R, +1>(v);
+    else if constexpr (RADIX == 8) dft8<R, +1>(v);
+    else dft16<R, +1>(v);
     cpx<R>* dst = out + rr * rs + c + (j * RADIX) * 18;
 #pragma unroll
     for (int r = 0; r < RADIX; ++r) dst[r * 18] = v[r];
@@ -366,10 +367,9 @@ __device__ cpx<R>* tile_fft_x_inv_packed(cpx<R>* b0, cpx<R>* b1, int rows, const
       stage_fixed<R, +1, 8, 8, 256, 2>(b0, b1, rows, tw); sync_swap();
       stage_fixed<R, +1, 4, 64, 256, 2>(b0, b1, rows, tw); sync_swap();
       return b0;
-    case 128:
-      stage_first_inv_packed<R, 8, 128>(b0, b1, rows, tw); sync_swap();
-      stage_fixed<R, +1, 4, 8, 128, 2>(b0, b1, rows, tw); sync_swap();
-      stage_fixed<R, +1, 4, 32, 128, 2>(b0, b1, rows, tw); sync_swap();
+    case 128:  // 16 x 8, as the forward transform
+      stage_first_inv_packed<R, 16, 128>(b0, b1, rows, tw); sync_swap();
+      stage_fixed<R, +1, 8, 16, 128, 2>(b0, b1, rows, tw); sync_swap();
       return b0;
     case 64:
       stage_first_inv_packed<R, 8, 64>(b0, b1, rows, tw); sync_swap();

@@ -419,6 +419,57 @@ __device__ __forceinline__ void x_forward_post(const cpx<R>* Z, cpx<R>* X, int r
   }
 }
 
+// Length 128 (N1 = 256): the last forward Stockham stage (radix 8, Ns = 16)
+// fused with the packed-real post-step.  Output k = j + 16 r of butterfly j is
+// paired with output 128 - k, which butterfly 16 - j (mod 16) produces at
+// r' = 7 - r (j = 0: 8 - r): one thread takes butterflies j and 16 - j of a
+// line (j = 0 and 8 pair with themselves), so both partners are in its
+// registers and X goes straight to shared memory, without the Z pass.
+template <class R>
+__device__ __forceinline__ void x_forward_last_post_128(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ X,
+                                                        int rows, const cpx<R>* __restrict__ tw) {
+  constexpr int M = 128, NB = 16, LN = 18, RS = M * LN;
+  const int total = rows * 9 * LN;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int c = idx % LN;
+    const int q = idx / LN;
+    const int rr = q / 9, u = q - rr * 9;
+    const cpx<R>* src = in + rr * RS + c;
+    cpx<R>* dst = X + rr * RS + c;
+    // butterfly j of the stage (as stage_fixed<R, -1, 8, 16, 128, 2>)
+    auto butterfly = [&](int j, cpx<R>(&v)[8]) {
+      v[0] = src[j * LN];
+#pragma unroll
+      for (int r = 1; r < 8; ++r) v[r] = cmul(src[(j + r * NB) * LN], twiddle<R, -1>(tw, 2 * r * j));
+      dft8<R, -1>(v);
+    };
+    // X[k] = (s - i W_N1^k d) / 2, s = Z[k] + conj(Z[M - k]), d = Z[k] - conj(Z[M - k])
+    auto post = [&](int k, cpx<R> a, cpx<R> zp) {
+      const cpx<R> b = cconj(zp);
+      const cpx<R> sm = cadd(a, b), df = csub(a, b);
+      const cpx<R> wd = cmul(tw[k], df);
+      dst[k * LN] = cmake<R>(R(0.5) * (sm.x + wd.y), R(0.5) * (sm.y - wd.x));
+    };
+    cpx<R> v[8];
+    butterfly(u, v);
+    if (u == 0) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) post(16 * r, v[r], v[(8 - r) & 7]);
+    } else if (u == 8) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) post(8 + 16 * r, v[r], v[7 - r]);
+    } else {
+      cpx<R> w[8];
+      butterfly(16 - u, w);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        post(u + 16 * r, v[r], w[7 - r]);
+        post(16 - u + 16 * r, w[r], v[7 - r]);
+      }
+    }
+  }
+}
+
 enum PassMode { kIter = 0, kStart = 1, kXFwd = 2, kXInv = 3 };
 
 // Shared-memory plan of pass A: a fixed header (barriers, reduction scratch,
@@ -847,7 +898,14 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
   }
   // ---------------------------------------------------------- forward x
   cpx<R>* X;
-  if (packed) {
+  if (packed && M == 128) {
+    // radix 16, then the radix-8 stage fused with the post-step
+    cpx<R>* other = (zbuf == b0) ? b1 : b0;
+    stage_fixed<R, -1, 16, 1, 128, 2>(zbuf, other, nr, tws);
+    __syncthreads();
+    x_forward_last_post_128<R>(other, zbuf, nr, tws);
+    X = zbuf;
+  } else if (packed) {
     cpx<R>* other = (zbuf == b0) ? b1 : b0;
     cpx<R>* Z = tile_fft_x<R, -1>(zbuf, other, nr, c.px, tws);
     cpx<R>* dst = (Z == b0) ? b1 : b0;
@@ -880,9 +938,9 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
         }
       }
     } else {
-#pragma unroll
       R* cmx = reinterpret_cast<R*>(smem_raw + L.carry_off);
       double* csm = reinterpret_cast<double*>(cmx + 4 * kThreads);
+#pragma unroll
       for (int a = 0; a < 4; ++a) {
         R& m = cmx[a * kThreads + threadIdx.x];
         m = max(m, dmax[a]);

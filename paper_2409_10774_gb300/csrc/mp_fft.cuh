@@ -233,8 +233,8 @@ __device__ cpx<R>* tile_fft(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R>&
 
 // The x-axis transform inside pass A (twiddle stride 2: the table holds the
 // N1 = 2 M roots).  Common lengths are unrolled at compile time (radix <= 8,
-// radix 3 last, except 16 x 8 for M = 128); others take tile_fft with the
-// host's radix plan.
+// radix 3 last, except 16 x 8 for M = 128 in FP32); others take tile_fft with
+// the host's radix plan.
 template <class R, int DIR>
 __device__ cpx<R>* tile_fft_x(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R>& p, const cpx<R>* tw) {
   auto sync_swap = [&]() {
@@ -249,9 +249,17 @@ __device__ cpx<R>* tile_fft_x(cpx<R>* b0, cpx<R>* b1, int rows, const AxisPlan<R
       stage_fixed<R, DIR, 8, 8, 256, 2>(b0, b1, rows, tw); sync_swap();
       stage_fixed<R, DIR, 4, 64, 256, 2>(b0, b1, rows, tw); sync_swap();
       return b0;
-    case 128:  // two stages (16 x 8): one shared-memory pass and one barrier fewer
-      stage_fixed<R, DIR, 16, 1, 128, 2>(b0, b1, rows, tw); sync_swap();
-      stage_fixed<R, DIR, 8, 16, 128, 2>(b0, b1, rows, tw); sync_swap();
+    case 128:
+      if constexpr (sizeof(R) == 4) {
+        // two stages (16 x 8): one shared-memory pass and one barrier fewer
+        // (FP64 keeps three: its radix-16 butterfly costs more than it saves)
+        stage_fixed<R, DIR, 16, 1, 128, 2>(b0, b1, rows, tw); sync_swap();
+        stage_fixed<R, DIR, 8, 16, 128, 2>(b0, b1, rows, tw); sync_swap();
+      } else {
+        stage_fixed<R, DIR, 8, 1, 128, 2>(b0, b1, rows, tw); sync_swap();
+        stage_fixed<R, DIR, 4, 8, 128, 2>(b0, b1, rows, tw); sync_swap();
+        stage_fixed<R, DIR, 4, 32, 128, 2>(b0, b1, rows, tw); sync_swap();
+      }
       return b0;
     case 64:
       stage_fixed<R, DIR, 8, 1, 64, 2>(b0, b1, rows, tw); sync_swap();

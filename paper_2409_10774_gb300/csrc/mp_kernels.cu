@@ -367,9 +367,15 @@ __device__ cpx<R>* tile_fft_x_inv_packed(cpx<R>* b0, cpx<R>* b1, int rows, const
       stage_fixed<R, +1, 8, 8, 256, 2>(b0, b1, rows, tw); sync_swap();
       stage_fixed<R, +1, 4, 64, 256, 2>(b0, b1, rows, tw); sync_swap();
       return b0;
-    case 128:  // 16 x 8, as the forward transform
-      stage_first_inv_packed<R, 16, 128>(b0, b1, rows, tw); sync_swap();
-      stage_fixed<R, +1, 8, 16, 128, 2>(b0, b1, rows, tw); sync_swap();
+    case 128:  // as the forward transform: 16 x 8 in FP32, 8 x 4 x 4 in FP64
+      if constexpr (sizeof(R) == 4) {
+        stage_first_inv_packed<R, 16, 128>(b0, b1, rows, tw); sync_swap();
+        stage_fixed<R, +1, 8, 16, 128, 2>(b0, b1, rows, tw); sync_swap();
+      } else {
+        stage_first_inv_packed<R, 8, 128>(b0, b1, rows, tw); sync_swap();
+        stage_fixed<R, +1, 4, 8, 128, 2>(b0, b1, rows, tw); sync_swap();
+        stage_fixed<R, +1, 4, 32, 128, 2>(b0, b1, rows, tw); sync_swap();
+      }
       return b0;
     case 64:
       stage_first_inv_packed<R, 8, 64>(b0, b1, rows, tw); sync_swap();
@@ -419,29 +425,31 @@ __device__ __forceinline__ void x_forward_post(const cpx<R>* Z, cpx<R>* X, int r
   }
 }
 
-// Length 128 (N1 = 256): the last forward Stockham stage (radix 8, Ns = 16)
-// fused with the packed-real post-step.  Output k = j + 16 r of butterfly j is
-// paired with output 128 - k, which butterfly 16 - j (mod 16) produces at
-// r' = 7 - r (j = 0: 8 - r): one thread takes butterflies j and 16 - j of a
-// line (j = 0 and 8 pair with themselves), so both partners are in its
-// registers and X goes straight to shared memory, without the Z pass.
-template <class R>
-__device__ __forceinline__ void x_forward_last_post_128(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ X,
-                                                        int rows, const cpx<R>* __restrict__ tw) {
-  constexpr int M = 128, NB = 16, LN = 18, RS = M * LN;
-  const int total = rows * 9 * LN;
+// The last forward Stockham stage of a length-M transform (radix RADIX,
+// Ns = M / RADIX, twiddle stride 2) fused with the packed-real post-step.
+// Output k = j + Ns r of butterfly j pairs with output M - k, which butterfly
+// Ns - j produces at r' = RADIX - 1 - r (butterfly 0: r' = RADIX - r mod
+// RADIX; butterfly Ns / 2 pairs with itself): one thread takes butterflies j
+// and Ns - j of a line, so both partners are in its registers and X goes
+// straight to shared memory, without a separate post pass.
+template <class R, int M, int RADIX>
+__device__ __forceinline__ void x_forward_last_post(const cpx<R>* __restrict__ in, cpx<R>* __restrict__ X,
+                                                    int rows, const cpx<R>* __restrict__ tw) {
+  constexpr int NS = M / RADIX, UNITS = NS / 2 + 1, LN = 18, RS = M * LN;
+  const int total = rows * UNITS * LN;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int c = idx % LN;
     const int q = idx / LN;
-    const int rr = q / 9, u = q - rr * 9;
+    const int rr = q / UNITS, u = q - rr * UNITS;
     const cpx<R>* src = in + rr * RS + c;
     cpx<R>* dst = X + rr * RS + c;
-    // butterfly j of the stage (as stage_fixed<R, -1, 8, 16, 128, 2>)
-    auto butterfly = [&](int j, cpx<R>(&v)[8]) {
+    // butterfly j of the stage (as stage_fixed<R, -1, RADIX, NS, M, 2>)
+    auto butterfly = [&](int j, cpx<R>(&v)[RADIX]) {
       v[0] = src[j * LN];
 #pragma unroll
-      for (int r = 1; r < 8; ++r) v[r] = cmul(src[(j + r * NB) * LN], twiddle<R, -1>(tw, 2 * r * j));
-      dft8<R, -1>(v);
+      for (int r = 1; r < RADIX; ++r) v[r] = cmul(src[(j + r * NS) * LN], twiddle<R, -1>(tw, 2 * r * j));
+      if constexpr (RADIX == 4) dft4<R, -1>(v);
+      else dft8<R, -1>(v);
     };
     // X[k] = (s - i W_N1^k d) / 2, s = Z[k] + conj(Z[M - k]), d = Z[k] - conj(Z[M - k])
     auto post = [&](int k, cpx<R> a, cpx<R> zp) {
@@ -450,21 +458,21 @@ __device__ __forceinline__ void x_forward_last_post_128(const cpx<R>* __restrict
       const cpx<R> wd = cmul(tw[k], df);
       dst[k * LN] = cmake<R>(R(0.5) * (sm.x + wd.y), R(0.5) * (sm.y - wd.x));
     };
-    cpx<R> v[8];
+    cpx<R> v[RADIX];
     butterfly(u, v);
     if (u == 0) {
 #pragma unroll
-      for (int r = 0; r < 8; ++r) post(16 * r, v[r], v[(8 - r) & 7]);
-    } else if (u == 8) {
+      for (int r = 0; r < RADIX; ++r) post(NS * r, v[r], v[(RADIX - r) % RADIX]);
+    } else if (u == NS / 2) {
 #pragma unroll
-      for (int r = 0; r < 8; ++r) post(8 + 16 * r, v[r], v[7 - r]);
+      for (int r = 0; r < RADIX; ++r) post(NS / 2 + NS * r, v[r], v[RADIX - 1 - r]);
     } else {
-      cpx<R> w[8];
-      butterfly(16 - u, w);
+      cpx<R> w[RADIX];
+      butterfly(NS - u, w);
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        post(u + 16 * r, v[r], w[7 - r]);
-        post(16 - u + 16 * r, w[r], v[7 - r]);
+      for (int r = 0; r < RADIX; ++r) {
+        post(u + NS * r, v[r], w[RADIX - 1 - r]);
+        post(NS - u + NS * r, w[r], v[RADIX - 1 - r]);
       }
     }
   }
@@ -898,12 +906,17 @@ __device__ __forceinline__ bool pass_a_item(const CellDev<R>& c, long long item,
   }
   // ---------------------------------------------------------- forward x
   cpx<R>* X;
-  if (packed && M == 128) {
-    // radix 16, then the radix-8 stage fused with the post-step
+  if (sizeof(R) == 4 && packed && (M == 128 || M == 64 || M == 32)) {
+    // FP32: the first stage of the compile-time plan, then its last stage
+    // fused with the post-step (128: 16 x 8, 64: 8 x 8, 32: 8 x 4)
     cpx<R>* other = (zbuf == b0) ? b1 : b0;
-    stage_fixed<R, -1, 16, 1, 128, 2>(zbuf, other, nr, tws);
+    if (M == 128) stage_fixed<R, -1, 16, 1, 128, 2>(zbuf, other, nr, tws);
+    else if (M == 64) stage_fixed<R, -1, 8, 1, 64, 2>(zbuf, other, nr, tws);
+    else stage_fixed<R, -1, 8, 1, 32, 2>(zbuf, other, nr, tws);
     __syncthreads();
-    x_forward_last_post_128<R>(other, zbuf, nr, tws);
+    if (M == 128) x_forward_last_post<R, 128, 8>(other, zbuf, nr, tws);
+    else if (M == 64) x_forward_last_post<R, 64, 8>(other, zbuf, nr, tws);
+    else x_forward_last_post<R, 32, 4>(other, zbuf, nr, tws);
     X = zbuf;
   } else if (packed) {
     cpx<R>* other = (zbuf == b0) ? b1 : b0;

@@ -56,3 +56,16 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_profiling_shape_names_its_workload_and_drops_traffic():
+    """--shape runs a box-shaped regeneration under its own workload name; the
+    committed per-launch traffic belongs to the 256^3 workload only."""
+    import argparse
+    import bench
+    a = argparse.Namespace(n=256, cells=200, shape="256,128,128", gpus=1)
+    cfg = bench._config(a)
+    assert cfg["workload"] == "voronoi200-256x128x128" and cfg["n"] == [256, 128, 128]
+    assert bench._traffic("pass_a", cfg["workload"]) is None
+    b = argparse.Namespace(n=256, cells=200, shape=None, gpus=1)
+    assert bench._config(b)["workload"] == "voronoi200-256^3"

@@ -87,3 +87,25 @@ def test_ramp_path_is_linear_from_zero():
     assert np.array_equal(E[0], np.zeros((3, 3))) and np.allclose(E[-1], Ef)
     assert np.allclose(E[2], 0.5 * Ef)
     assert np.count_nonzero(Gm) == 0
+
+
+def test_box_shaped_voronoi_regenerations():
+    """A box-shaped grid maps the same seed box onto each axis with its own
+    scale: the cubic shape reproduces the cubic generator, and a box shape
+    keeps the grain table and every grain that the scaled seeds reach."""
+    cube = W.workload_voronoi(n=16)
+    box = W.workload_voronoi(shape=(16, 16, 16))
+    assert np.array_equal(cube["phase"], box["phase"])
+    assert box["name"] == "voronoi200-16x16x16"
+    thin = W.workload_voronoi(shape=(32, 8, 16))
+    assert thin["n"] == (32, 8, 16) and thin["phase"].shape == (16, 8, 32)
+    assert len(thin["phases"]) == len(cube["phases"])
+    # nearest-seed check at a few voxels, seeds scaled per axis
+    seeds = G.voronoi_seeds(200, 256, G.seed_for(2)) * (np.array([32, 8, 16]) / 256.0)
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        z, y, x = (int(rng.integers(16)), int(rng.integers(8)), int(rng.integers(32)))
+        c = np.array([x + 0.5, y + 0.5, z + 0.5])
+        d = c[None, :] - seeds
+        d -= np.array([32, 8, 16]) * np.round(d / np.array([32, 8, 16]))
+        assert thin["phase"][z, y, x] == int(np.argmin((d * d).sum(axis=1)))

@@ -1192,6 +1192,36 @@ __device__ __forceinline__ void fold_partials(const double* partials, long long 
   __syncthreads();
 }
 
+// The same fold for a batched cell's per-item records (tens to hundreds of
+// items): thread (q, g) folds value q over the g-th of kFoldGroups contiguous
+// item ranges in item order (neighbouring q read neighbouring doubles), then
+// thread q folds the groups in order: a fixed order, like the tree above,
+// without its 44 shuffle trees per warp.
+constexpr int kFoldGroups = 5;  // 5 x 44 = 220 of the 256 threads
+__device__ __forceinline__ void fold_items(const double* partials, long long nparts, double* s,
+                                           double (*part)[kErrPartials]) {
+  const int t = threadIdx.x;
+  if (t < kFoldGroups * kErrPartials) {
+    const int q = t % kErrPartials, g = t / kErrPartials;
+    const long long per = (nparts + kFoldGroups - 1) / kFoldGroups;
+    const long long b0 = (long long)g * per;
+    const long long b1 = (b0 + per < nparts) ? b0 + per : nparts;
+    double v = 0.0;
+    for (long long b = b0; b < b1; ++b) {
+      const double x = partials[b * kErrPartials + q];
+      v = (q < 4) ? fmax(v, x) : v + x;
+    }
+    part[g][q] = v;
+  }
+  __syncthreads();
+  if (t < kErrPartials) {
+    double v = part[0][t];
+    for (int g = 1; g < kFoldGroups; ++g) v = (t < 4) ? fmax(v, part[g][t]) : v + part[g][t];
+    s[t] = v;
+  }
+  __syncthreads();
+}
+
 template <class R>
 __global__ void __launch_bounds__(256) k_reduce_err(CellDev<R> c, const double* partials, int nparts,
                                                     int err_kind, double* out) {
@@ -1269,13 +1299,13 @@ __device__ void round_decide(RoundCtl& rc, const double* e) {
 template <class R>
 __global__ void __launch_bounds__(256) k_reduce_err_multi(Work<R> w) {
   __shared__ double s[kErrPartials];
-  __shared__ double wred[8][kErrPartials];
+  __shared__ double part[kFoldGroups][kErrPartials];
   __shared__ CellDev<R> cs;
   load_cell(cs, w.cells + w.act[blockIdx.x]);
   __syncthreads();
   RoundCtl* rc = cs.rctl;
   if (rc != nullptr && __ldcg(&rc->stop) != 0) return;  // uniform: one flag per block
-  fold_partials(cs.ipart, cs.items_a, s, wred);
+  fold_items(cs.ipart, cs.items_a, s, part);
   if (threadIdx.x == 0) {
     if (rc != nullptr) {
       double* out = rc->rows + 8 * rc->rounds;

@@ -1165,38 +1165,11 @@ __device__ void finish_err(const CellDev<R>& c, const double* s, int err_kind, d
 }
 
 // Fixed-order FP64 fold of `nparts` partial records (max for the first four
-// entries, sums for the rest) by one block; the total lands in s[].
-__device__ __forceinline__ void fold_partials(const double* partials, long long nparts, double* s,
-                                              double (*wred)[kErrPartials]) {
-  double a[kErrPartials];
-#pragma unroll
-  for (int q = 0; q < kErrPartials; ++q) a[q] = 0.0;
-  for (long long b = threadIdx.x; b < nparts; b += blockDim.x) {
-    const double* src = partials + b * kErrPartials;
-#pragma unroll
-    for (int q = 0; q < kErrPartials; ++q) a[q] = (q < 4) ? fmax(a[q], src[q]) : a[q] + src[q];
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < kErrPartials; ++q) {
-    const double v = (q < 4) ? shfl_max(a[q]) : shfl_sum(a[q]);
-    if (lane == 0) wred[warp][q] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < kErrPartials) {
-    const int q = threadIdx.x;
-    double v = wred[0][q];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = (q < 4) ? fmax(v, wred[w][q]) : v + wred[w][q];
-    s[q] = v;
-  }
-  __syncthreads();
-}
-
-// The same fold for a batched cell's per-item records (tens to hundreds of
-// items): thread (q, g) folds value q over the g-th of kFoldGroups contiguous
-// item ranges in item order (neighbouring q read neighbouring doubles), then
-// thread q folds the groups in order: a fixed order, like the tree above,
-// without its 44 shuffle trees per warp.
+// entries, sums for the rest; the block partials of a single cell, or a
+// batched cell's per-item records) by one block; the total lands in s[].
+// Thread (q, g) folds value q over the g-th of kFoldGroups contiguous record
+// ranges in record order (neighbouring q read neighbouring doubles), then
+// thread q folds the groups in order.
 constexpr int kFoldGroups = 5;  // 5 x 44 = 220 of the 256 threads
 __device__ __forceinline__ void fold_items(const double* partials, long long nparts, double* s,
                                            double (*part)[kErrPartials]) {
@@ -1226,8 +1199,8 @@ template <class R>
 __global__ void __launch_bounds__(256) k_reduce_err(CellDev<R> c, const double* partials, int nparts,
                                                     int err_kind, double* out) {
   __shared__ double s[kErrPartials];
-  __shared__ double wred[8][kErrPartials];
-  fold_partials(partials, nparts, s, wred);
+  __shared__ double part[kFoldGroups][kErrPartials];
+  fold_items(partials, nparts, s, part);
   if (threadIdx.x == 0) finish_err<R>(c, s, err_kind, out);
 }
 
@@ -1244,8 +1217,8 @@ __global__ void __launch_bounds__(256) k_reduce_err_loop(CellDev<R> c, const dou
                                                          double div_limit, int stag, int adapt,
                                                          cudaGraphConditionalHandle handle) {
   __shared__ double s[kErrPartials];
-  __shared__ double wred[8][kErrPartials];
-  fold_partials(partials, nparts, s, wred);
+  __shared__ double part[kFoldGroups][kErrPartials];
+  fold_items(partials, nparts, s, part);
   if (threadIdx.x == 0) {
     finish_err<R>(c, s, err_kind, out);
     const int it = (int)out[6] + 1;

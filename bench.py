@@ -255,7 +255,7 @@ def _config(args):
     name = f"voronoi{args.cells}-" + ("x".join(map(str, shape)) if shape else f"{args.n}^3")
     return {"workload": name, "n": list(shape) if shape else args.n, "cells": args.cells,
             "increments": 20, "load": "E11 to 1%", "tol": 1e-6, "err": "local",
-            "ref_medium": "mean", "fields": "fp32", "scalars": "fp64 p, q, totals",
+            "ref_medium": "mean", "fields": "fp32", "scalars": "fp64 scalar return, p, q, error sums; averages in compensated fp32 pairs folded in fp64",
             "l2": "no flush: the cell's device state (~5.3 GB) exceeds L2",
             "parallelism": f"replicas x{args.gpus}"}
 

@@ -26,8 +26,9 @@
  *         accumulated plastic strains p, q in FP64, the error measure's sums,
  *         means and ratios (eq. err) in FP64 (the per-voxel norms of FP32
  *         field differences are FP32 quantities and their maxima are exact),
- *         and the homogenized averages summed in FP64.  Without a
- *         prescribed iteration schedule or a manufactured source, an
+ *         and the homogenized averages accumulated in compensated FP32
+ *         pairs (per thread) and folded in FP64 (p, q summed in FP64).
+ *         Without a prescribed iteration schedule or a manufactured source, an
  *         increment whose error sets no new low (below 0.99 times the last
  *         one) in 64 iterations while above the tolerance (the FP32
  *         rounding floor) continues in the increment form e^{i+1} = e^i -
@@ -39,8 +40,8 @@
  *         the next increment; iters_fp64 counts those FP64 iterations;
  *     2 = as 1, but the level return's radius, square root, multiplier
  *         increment and scale factor are formed in FP32 (the trial
- *         equivalent stress is itself an FP32 quantity); p, q and every sum
- *         stay FP64.
+ *         equivalent stress is itself an FP32 quantity); p, q and the sums
+ *         as in 1.
  *   - Status codes only; nothing throws or aborts across this boundary.  The
  *     message of the last failure is available from mp_last_error().
  *   - Host pointers are read during the call and not retained.  Output host

@@ -37,7 +37,9 @@
  *         earlier lows) finishes in FP64 in the full form restarted from
  *         the current iterate (an FP64 copy of the cell's state, allocated
  *         at the first such increment) and returns to FP32 for
- *         the next increment; iters_fp64 counts those FP64 iterations;
+ *         the next increment (once the increment form has stalled in a
+ *         solve, later full-form stalls go to FP64 directly); iters_fp64
+ *         counts those FP64 iterations;
  *     2 = as 1, but the level return's radius, square root, multiplier
  *         increment and scale factor are formed in FP32 (the trial
  *         equivalent stress is itself an FP32 quantity); p, q and the sums
@@ -278,7 +280,9 @@ mp_status mp_rve_profile_read(const mp_rve* rve, double* ms, int64_t* launches, 
  * polarization; if that sets no new low for 128 iterations (or twice the
  * longest gap between its earlier lows, if longer), it finishes the
  * increment in FP64 (iters_fp64), in the full form restarted from its
- * current iterate.  A prescribed iteration schedule disables both. */
+ * current iterate; once that has happened in a cell's solve, its later
+ * full-form stalls go to FP64 directly.  A prescribed iteration schedule
+ * disables both. */
 typedef struct mp_batch_stats {
   int64_t rounds;              /* iteration rounds of the FP32 and of the FP64 engine       */
   int64_t rounds_fp64;

@@ -313,6 +313,7 @@ struct mp_rve {
   bool twin = false;
   std::vector<int> iters64_steps;  // iterations of each increment run in FP64
   long long delta_switches = 0, escalations = 0;
+  bool skip_delta = false;  // the increment form stalled once: later stalls go to FP64 directly
 };
 
 namespace {
@@ -829,7 +830,7 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
                        0, o));
   it += o.it;
   if constexpr (sizeof(R) == 4) {
-    if (o.stalled) {
+    if (o.stalled && !r->skip_delta) {
       // the increment form: one iteration that writes the first increment of
       // the polarization, then iterations on the increments
       ++r->delta_switches;
@@ -847,26 +848,27 @@ mp_status run_step(mp_rve* r, int s, cudaStream_t st) {
         MP_CK_ST(run_loop<R>(r, c, s, st, -1, r->max_iter - it, kStallItersDelta, true, gap, it, o));
         it += o.it;
       }
-      if (o.stalled) {
-        ++r->escalations;
-        MP_CK_ST(escalate_to_fp64(r, st));
-        CellDev<double>& d = r->cd;
-        set_load(d, r, s);
-        d.src = nullptr;
-        // FP64 restarts the full form from the current iterate: the start
-        // pass forms its polarization, so the rounding the increment form
-        // carried is damped by the iteration instead of kept
-        d.delta_in = 0;
-        d.delta_out = 0;
-        MP_CK(ctx, launch_start<double>(r->L64, d, 0, st));
-        r->launches[MP_KC_START] += 1;
-        MP_CK_ST(run_loop<double>(r, d, s, st, -1, r->max_iter - it, 0, false, gap, it, o));
-        it += o.it;
-        it64 = o.it;
-        in_fp64 = true;
-      }
-      c.delta_in = c.delta_out = 0;
+      if (o.stalled) r->skip_delta = true;  // it stalled here too: later stalls skip it
     }
+    if (o.stalled) {
+      ++r->escalations;
+      MP_CK_ST(escalate_to_fp64(r, st));
+      CellDev<double>& d = r->cd;
+      set_load(d, r, s);
+      d.src = nullptr;
+      // FP64 restarts the full form from the current iterate: the start
+      // pass forms its polarization, so the rounding the increment form
+      // carried is damped by the iteration instead of kept
+      d.delta_in = 0;
+      d.delta_out = 0;
+      MP_CK(ctx, launch_start<double>(r->L64, d, 0, st));
+      r->launches[MP_KC_START] += 1;
+      MP_CK_ST(run_loop<double>(r, d, s, st, -1, r->max_iter - it, 0, false, gap, it, o));
+      it += o.it;
+      it64 = o.it;
+      in_fp64 = true;
+    }
+    c.delta_in = c.delta_out = 0;
   }
   const double err = o.err;
   mp_status status = o.status;
@@ -957,7 +959,7 @@ uint64_t problem_digest(const mp_problem* p, const double ref[6]) {
 // Checkpoint image: header, then the device arrays in this order.
 struct CkptHeader {
   char magic[8];  // "MPCKPT2\0"
-  int32_t precision, n[3], n_steps, steps_done, predicted, failed_step;
+  int32_t precision, n[3], n_steps, steps_done, predicted, failed_step, skip_delta, reserved;
   int64_t total_iters;
   uint64_t digest;
   uint64_t bytes_prev, bytes_hist, bytes_pq, bytes_elast, bytes_tmean, bytes_rows;
@@ -1090,6 +1092,7 @@ mp_status mp_rve_reset(mp_rve* r, void* stream) {
   r->err_steps.clear();
   r->iters_steps.clear();
   r->iters64_steps.clear();
+  r->skip_delta = false;
   return MP_OK;
 }
 
@@ -1103,6 +1106,7 @@ mp_status mp_checkpoint(mp_rve* r, void* host_buf, size_t* bytes, void* stream) 
   h.steps_done = r->steps_done;
   h.predicted = r->predicted ? 1 : 0;
   h.failed_step = r->failed_step;
+  h.skip_delta = r->skip_delta ? 1 : 0;
   h.total_iters = r->total_iters;
   h.digest = r->digest;
   h.bytes_prev = r->prev.bytes;
@@ -1204,6 +1208,7 @@ mp_status mp_resume(mp_rve* r, const void* host_buf, size_t bytes, void* stream)
   r->steps_done = h.steps_done;
   r->predicted = h.predicted != 0;
   r->failed_step = h.failed_step;
+  r->skip_delta = h.skip_delta != 0;
   r->total_iters = h.total_iters;
   return MP_OK;
 }

@@ -218,6 +218,8 @@ struct Progress {
   bool demote = false;      // FP64-finished increment committed: next one in FP32
   bool restart = false;     // escalated: recompute the polarization of the current
                             // iterate and continue in the full form (in FP64)
+  bool skip_delta = false;  // the increment form stalled once in this solve: later
+                            // full-form stalls go to FP64 directly
 };
 
 // An FP32-mixed cell whose error has set no new low (a drop below kStallDrop times
@@ -496,12 +498,13 @@ class Engine {
       if (!kFp64 && target < 0) {
         if (stall_step(g.err, g.it, g.delta ? kStallItersDelta : kStallIters, g.delta != 0, g.ref_err, g.it_ref,
                        g.gap)) {
-          if (g.delta == 0) {
+          if (g.delta == 0 && !g.skip_delta) {
             g.delta = 1;
             g.ref_err = g.err;
             g.it_ref = g.it;
             ++delta_switches_;
           } else {
+            if (g.delta != 0) g.skip_delta = true;
             g.escalate = true;
           }
           return false;

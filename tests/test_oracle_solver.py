@@ -365,3 +365,25 @@ def test_mean_reference_diverges_on_centred_sphere_midrange_converges():
     p["ref_kind"] = "midrange"
     res = solver.solve(p, max_steps=2)
     assert res["status"] == "ok"
+
+
+def test_centred_sphere_symmetry_under_uniaxial_strain():
+    """P13: a sphere centred in the cell (voxel centres at i + 1/2) under E11
+    alone.  The phase map is invariant under the reflections x_j -> L - x_j
+    and under swapping y and z, and so is the load: <t22> = <t33>, the
+    off-diagonal averages vanish, and so does the mean couple stress (no
+    curvature load), to rounding; the plastic strain never decreases."""
+    p = W.workload_centered_sphere(n=8, radius=2.5, n_steps=3, tol=1e-10, ref_kind="midrange")
+    assert np.array_equal(p["phase"], np.transpose(p["phase"], (1, 0, 2)))   # z <-> y
+    assert np.array_equal(p["phase"], p["phase"][::-1, ::-1, ::-1])
+    res = solver.solve(p)
+    assert res["status"] == "ok" and res["P"][-1] > 0.0
+    T, M = res["T"], res["M"]
+    scale = np.abs(T).max()
+    np.testing.assert_allclose(T[:, 1, 1], T[:, 2, 2], rtol=0, atol=1e-12 * scale)
+    off = T.copy()
+    for k in range(3):
+        off[:, k, k] = 0.0
+    assert np.abs(off).max() <= 1e-12 * scale
+    assert np.abs(M).max() <= 1e-12 * scale * p["h"]
+    assert np.all(np.diff(res["P"]) >= 0) and np.all(np.diff(res["Q"]) >= 0)

@@ -190,9 +190,11 @@ __device__ __forceinline__ void fft_y_tile_any(const CellDev<R>& c, long long ti
 }
 
 // NF > 0: compiled for one column length (its transform plan unrolled);
-// NF = 0: any length, dispatched per tile (multi-cell launches).
+// NF = 0: any length, dispatched per tile (multi-cell launches; every plan is
+// compiled into the one kernel, so it is given the registers of two blocks
+// per SM rather than spilling at three).
 template <class R, int DIR, bool MULTI, int NF>
-__global__ void __launch_bounds__(kThreadsYZ, 3) k_fft_y(CellDev<R> c0, Work<R> w) {
+__global__ void __launch_bounds__(kThreadsYZ, NF > 0 ? 3 : 2) k_fft_y(CellDev<R> c0, Work<R> w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ CellDev<R> cs;
   for_items<R, MULTI>(c0, tiles_y(c0), w, cs, [&](const CellDev<R>& c, long long t) {
